@@ -1,0 +1,359 @@
+"""Benchmark: dof-updates/s of the sparse-tiled DG elastic time step on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config large] [--tile-size 1024] [--no-untiled] [--no-cpu]
+
+One step = one full time step of the DG elastic chain (seventeen loops: velocity sub-chain then
+stress sub-chain) over the whole mesh.  The default workload is the 1000x500-square mesh of the
+300x150 domain (1.0M triangles, P2, FP64, three layers, Ricker source), executed sparse-tiled
+with the seed tile size given, fusion scheme {velocity, stress}.  Inputs are resident in HBM and
+larger than L2 (no flush needed).  The JSON line carries the tiled throughput (value), the plain
+untiled chain on the same GPU, the inspection time, the roofline of the dominant kernel, the
+oracle timed on the host cores (cpu_baseline) and an end-to-end number through the C ABI with
+host buffers (e2e).  --impl reference times the oracle itself on the host cores.
+
+Multi-GPU: the workload does not shard in this library; --gpus N runs N independent replicas
+(one per rank, launched by torchrun) and reports the sum over ranks / the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dof-updates/s per timestep, tiled vs untiled, % HBM roofline; adjoint/fwd time"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max SM clock
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def flops_per_step(Np, Nfp, nc, nfi, nfe):
+    """FP64 flops the executor's kernels perform in one time step (an FMA counts 2).
+
+    Per cell: volB 8Np^2+10Np+4, hookeB 8Np^2+17Np+6 (twice), volD 8Np^2+9Np (three times),
+    updV 8Np, updS 19Np+2; per cell side of an interior facet: intB 4NpNfp+9Nfp+4 and intD
+    4NpNfp+6Np+2Nfp+3 (three loops each); per exterior facet: extB 4NpNfp+6Nfp+3 (three loops);
+    final increments 2Np (intB, extB) and 3Np (intD) per cell and facet loop."""
+    cell = (8 * Np * Np + 10 * Np + 4) + 2 * (8 * Np * Np + 17 * Np + 6) + 3 * (8 * Np * Np + 9 * Np) \
+        + 8 * Np + 19 * Np + 2 + 3 * 2 * Np + 3 * 3 * Np
+    side_b = 4 * Np * Nfp + 9 * Nfp + 4
+    side_d = 4 * Np * Nfp + 6 * Np + 2 * Nfp + 3
+    ext = 4 * Np * Nfp + 6 * Nfp + 3 + 2 * Np
+    return nc * cell + 2 * nfi * 3 * (side_b + side_d) + nfe * 3 * ext
+
+
+def bytes_per_step(Np, nc, tiled):
+    """Algorithmic DRAM bytes of one time step.  Tiled (ideal): the prognostic fields v, sigma
+    read and written once plus per-cell geometry, material and neighbours read once
+    (80 Np + 140 B per cell).  Untiled: every loop streams its operand and result fields and
+    the metadata it needs (808 Np + 808 B per cell, counted loop by loop in the design doc)."""
+    if tiled:
+        return nc * (80 * Np + 140)
+    return nc * (808 * Np + 808)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("exec.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1708_03183_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel source; otherwise None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+        if e.get("source_hash") != kernel_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons while active."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=2)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for k, n in enumerate(names):
+                    if r[4 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_rate(cfg_name, nsteps, scale=4):
+    """The oracle on the host cores: `nsteps` time steps of the same workload generator with the
+    mesh reduced by `scale` in each direction (single BLAS thread).  Returns dof-updates/s."""
+    code = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, %r)
+import synth
+from oracle.dg import ElasticDG
+c = synth.CONFIGS[%r]
+cfg = synth.build_config(%r, nx=c["nx"] // %d, ny=c["ny"] // %d, nsteps=%d)
+dg = ElasticDG(cfg["mesh"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"])
+nc, Np = dg.nc, dg.Np
+v, s = np.zeros((nc, 2, Np)), np.zeros((nc, 3, Np))
+t = time.perf_counter()
+dg.run(v, s, cfg["dt"], %d, cfg["ricker"], cfg["src"])
+t = time.perf_counter() - t
+print(json.dumps({"t": t, "nc": nc, "Np": Np}))
+""" % (ROOT, cfg_name, cfg_name, scale, scale, nsteps, nsteps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return 5 * d["Np"] * d["nc"] * nsteps / d["t"], d
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import synth
+    c = synth.CONFIGS[args.config]
+    scale = 4
+    for _ in range(args.warmup):
+        oracle_sample_rate(args.config, 1, scale)
+    tot_t, tot_units = 0.0, 0.0
+    for _ in range(args.steps):
+        rate, d = oracle_sample_rate(args.config, 1, scale)
+        tot_t += d["t"]
+        tot_units += 5 * d["Np"] * d["nc"]
+    value = tot_units / tot_t
+    sample = "one time step per step of the %dx%d-square mesh (%d cells, P%d) from the same generator" % (
+        c["nx"] // scale, c["ny"] // scale, d["nc"], c["p"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "dof-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "dof-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "dof-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_name(args):
+    import synth
+    c = synth.CONFIGS[args.config]
+    sc = getattr(args, "scale", 1)
+    nx, ny = c["nx"] // sc, c["ny"] // sc
+    return ("%s: %dx%d squares on %gx%g, %d triangles, DG P%d FP64, %s material, Ricker f0=%g, "
+            "sparse-tiled ts=%d, fusion {velocity, stress}" % (
+                args.config, nx, ny, c["Lx"], c["Ly"], 2 * nx * ny, c["p"], c["material"],
+                c["f0"], args.tile_size))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large")
+    ap.add_argument("--tile-size", type=int, default=1024)
+    ap.add_argument("--no-untiled", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--scale", type=int, default=1, help="divide nx, ny of the workload (small profiling cases)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_03183_gb300 as slt
+    import synth
+
+    c0 = synth.CONFIGS[args.config]
+    cfg = synth.build_config(args.config, nsteps=args.warmup + args.steps + args.e2e_steps,
+                             nx=c0["nx"] // args.scale, ny=c0["ny"] // args.scale)
+    m = cfg["mesh"]
+    nc = m["cell2vert"].shape[0]
+    p = cfg["p"]
+    Np, Nfp = (p + 1) * (p + 2) // 2, p + 1
+    stream = torch.cuda.current_stream()
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], p, cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
+    info = slt.slt_mesh_info(mesh)
+    chain = slt.slt_mesh_chain(mesh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,))
+    inspect_s = time.perf_counter() - t0
+    subs = [slt.slt_schedule_info(sched, k) for k in range(2)]
+
+    ricker = torch.tensor(cfg["ricker"], device="cuda")
+    units_per_step = 5 * Np * nc
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(schedule, K, W):
+        v = torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda")
+        s = torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda")
+        slt.slt_execute(mesh, schedule, v, s, ricker, cfg["dt"], W)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            e0.record(stream)
+            prof = slt.slt_execute_profiled(mesh, schedule, v, s, ricker[W:], cfg["dt"], K)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, clk.summary()
+
+    ms, prof, clocks = timed(sched, args.steps, args.warmup)
+    value = units_per_step * args.steps * world / (ms * 1e-3)
+    flops = flops_per_step(Np, Nfp, nc, info["nfi"], info["nfe"])
+    kern_s = prof["chain_ms"] * 1e-3
+    achieved = flops * args.steps / kern_s / 1e12
+    hbm_peak, hbm_kind = peaks()
+    traffic = ncu_traffic("k_tiled<2>", args.config)
+    tiled_bytes = bytes_per_step(Np, nc, True)
+
+    out = {"metric": METRIC, "value": value, "unit": "dof-updates/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args), "ncell": nc, "degree": p, "tile_size": args.tile_size,
+                      "dofs": units_per_step, "l2": "inputs larger than L2 (%.2f GB resident per step)" % (
+                          (20 * Np + 33) * nc * 8 / 1e9),
+                      "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "tiles": [s["ntiles"] for s in subs], "colours": [s["ncolours"] for s in subs],
+                      "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_PEAK_TFLOPS,
+                        "traffic": traffic, "kernel": "k_tiled<2>",
+                        "peak_kind": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal unit counts)",
+                        "launch_ms_avg": prof["chain_ms"] / max(prof["chain_launches"], 1),
+                        "flops_per_step": flops},
+           "hbm": {"algorithmic_bytes_per_step": tiled_bytes,
+                   "achieved_gbs": tiled_bytes * args.steps / kern_s / 1e9, "peak_gbs": hbm_peak,
+                   "frac": tiled_bytes * args.steps / kern_s / 1e9 / hbm_peak, "peak_kind": hbm_kind},
+           "clocks": clocks,
+           "gpu_launches": prof["chain_launches"] + prof["layout_launches"]}
+
+    if not args.no_untiled:
+        K = max(args.steps // 4, 10)
+        ums, uprof, uclk = timed(None, K, args.warmup)
+        ub = bytes_per_step(Np, nc, False)
+        uk = uprof["chain_ms"] * 1e-3
+        out["untiled"] = {"value": units_per_step * K * world / (ums * 1e-3), "ms_per_step": ums / K, "steps": K,
+                          "roofline_frac_fp64": flops * K / uk / 1e12 / FP64_PEAK_TFLOPS,
+                          "hbm_frac": ub * K / uk / 1e9 / hbm_peak, "algorithmic_bytes_per_step": ub,
+                          "launches_per_step": uprof["chain_launches"] / K, "clocks": uclk}
+
+    # end to end through the C ABI with pinned host buffers: every step copies the state in,
+    # runs one step and copies the state out
+    hv = torch.zeros((nc, 2, Np), dtype=torch.float64).pin_memory()
+    hs = torch.zeros((nc, 3, Np), dtype=torch.float64).pin_memory()
+    hr = torch.tensor(cfg["ricker"], dtype=torch.float64).pin_memory()
+    for n in range(3):
+        slt.slt_execute_host(mesh, sched, hv, hs, hr[n:n + 1], cfg["dt"], 1)
+    barrier()
+    t0 = time.perf_counter()
+    for n in range(args.e2e_steps):
+        slt.slt_execute_host(mesh, sched, hv, hs, hr[n:n + 1], cfg["dt"], 1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    out["e2e"] = {"value": units_per_step * args.e2e_steps * world / e2e_s, "unit": "dof-updates/s",
+                  "h2d_bytes_per_step": 5 * Np * nc * 8 + 8, "d2h_bytes_per_step": 5 * Np * nc * 8,
+                  "steps": args.e2e_steps}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, d = oracle_sample_rate(args.config, 10)
+        out["cpu_baseline"] = {"value": rate, "unit": "dof-updates/s", "cores": 1, "kind": "oracle",
+                               "sample": "10 time steps of the same generator's mesh reduced 4x per direction "
+                                         "(%d cells, P%d), single BLAS thread, %.1f s" % (d["nc"], p, d["t"])}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

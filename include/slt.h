@@ -1,0 +1,176 @@
+/* slt.h - sparse-tiled DG elastic-wave time stepping on one GB300 (sm_103a).
+ *
+ * C ABI of libslt.so.  Plain pointers and sizes only; every entry point returns an slt_status
+ * (0 on success) and never throws or aborts.  slt_last_error() returns a thread-local message
+ * describing the last failure of the calling thread.
+ *
+ * Conventions
+ *  - "host" pointers are read (or written) during the call only and never retained;
+ *    "device" pointers are CUDA global-memory pointers borrowed for the duration of the call.
+ *  - Objects (chain, mesh, schedule) are owned by the library and freed by their destroy call.
+ *  - Calls taking a `stream` (a cudaStream_t, NULL = legacy default stream) enqueue their GPU
+ *    work on it; slt_inspect, slt_mesh_create and the slt_schedule_* queries synchronise the
+ *    stream before returning.  Arguments are validated on the host before any launch:
+ *    invalid input returns SLT_ERR_ARG with nothing launched.
+ *  - Integers that index sets are int32; sizes are int64 (each set holds < 2^31 elements).
+ *
+ * Section and algorithm numbers refer to Luporini et al., "Automated Tiling of Unstructured
+ * Mesh Computations with Application to Seismological Modelling" (arXiv:1708.03183).
+ */
+#ifndef SLT_H
+#define SLT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SLT_OK = 0,
+  SLT_ERR_ARG = -1,          /* invalid argument (checked before any GPU work) */
+  SLT_ERR_OOM = -2,          /* device or host allocation failed */
+  SLT_ERR_CUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+  SLT_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+  SLT_ERR_CONFLICT_CAP = -5, /* conflict buffer of the inspector overflowed */
+  SLT_ERR_UNSUPPORTED = -6,  /* valid request outside what this build implements */
+  SLT_ERR_STATE = -7         /* object used in the wrong state (e.g. schedule of another mesh) */
+} slt_status;
+
+typedef struct slt_chain_s* slt_chain;       /* loop chain description (host) */
+typedef struct slt_schedule_s* slt_schedule; /* inspector output (device resident) */
+typedef struct slt_mesh_s* slt_mesh;         /* DG elastic mesh (device resident) */
+
+const char* slt_last_error(void);
+/* Library version and the compute capability it was built for (e.g. 103). */
+int slt_version(int32_t* major, int32_t* minor, int32_t* arch);
+
+/* ------------------------------------------------------------------ loop chain (Section 2)
+ * A loop chain is an ordered list of loops; each loop iterates over a set (iteration space)
+ * and carries descriptors <map or direct, mode in {r, w, i}> (Section 2, Figure 2 right).
+ * The order of slt_loop calls is the order of the chain.  Maps are flat arrays
+ * values[i * arity + k], copied at the call. */
+int slt_chain_create(slt_chain* out);
+int slt_chain_destroy(slt_chain chain);
+/* Declare a set of `size` >= 0 elements; returns its id (0, 1, ...). */
+int slt_set(slt_chain chain, int64_t size, int32_t* set_id);
+/* Declare a map from_set -> to_set^arity from host values (each in [0, size(to_set))).
+   SLT_ERR_ARG for arity < 1, unknown sets or out-of-range values. */
+int slt_map(slt_chain chain, int32_t from_set, int32_t to_set, int32_t arity,
+            const int32_t* host_values, int32_t* map_id);
+/* Append a loop over set_id with ndesc >= 1 descriptors: map_ids[d] (-1 = direct access)
+   and modes[d] in {'r', 'w', 'i'}.  An indirect descriptor's map must start at set_id. */
+int slt_loop(slt_chain chain, int32_t set_id, int32_t ndesc, const int32_t* map_ids,
+             const char* modes, int32_t* loop_id);
+/* Attach a 2-D point (host, [size][2] doubles) to every element of a set; the Hilbert
+   renumbering of the seed partition uses the points of the seed set. */
+int slt_set_points(slt_chain chain, int32_t set_id, const double* host_xy);
+int slt_chain_info(slt_chain chain, int32_t* nsets, int32_t* nmaps, int32_t* nloops);
+
+/* ------------------------------------------------------------------ inspector (Section 5.1)
+ * slt_inspect runs Algorithm 1 (with Algorithms 2 and 3) as GPU kernels on every sub-chain
+ * [split_k, split_{k+1}) of the chain (a fusion scheme: sub-chains are tiled independently and
+ * executed one after the other).  The seed loop of a sub-chain is its first loop.
+ *
+ *  partition  : seed iterations ranked by identity (renumber = 0) or by a stable sort of the
+ *               order-16 Hilbert index of their points quantised on a 65536^2 grid over the
+ *               bounding box (renumber = 1); iteration of rank r goes to tile r / tile_size.
+ *  adjacency  : through the first map of the sub-chain touching the seed set, plus fake edges.
+ *  colouring  : colouring = 0: Jones-Plassmann with priorities splitmix64(tile ^ prio_seed),
+ *               each tile taking the smallest colour unused by higher-priority neighbours;
+ *               colouring = 1: tile t gets colour t.
+ *  projection : MAX colour, previous projection kept on ties, all descriptors projected.
+ *  conflicts  : two distinct same-colour tiles touching one element; they become fake edges and
+ *               the sub-chain is re-coloured, up to max_rounds times, then colouring falls
+ *               back to sequential.
+ * The output is bit-identical to a sequential execution of the same rules. */
+typedef struct {
+  int32_t tile_size;     /* seed tile size ts >= 1 */
+  int32_t colouring;     /* 0 = Jones-Plassmann greedy, 1 = sequential */
+  int32_t renumber;      /* 0 = identity, 1 = Hilbert (needs points on the seed set) */
+  int32_t max_rounds;    /* restarts before the sequential fallback (>= 0) */
+  uint64_t prio_seed;    /* colouring priority seed */
+  int32_t nsplit;        /* number of split points (0 = one sub-chain) */
+  int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
+} slt_options;
+
+/* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
+   no split. */
+int slt_options_default(slt_options* opt);
+int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
+int slt_schedule_destroy(slt_schedule sched);
+/* Per sub-chain statistics: info[0..7] = ntiles, ncolours, restarts, fell_back_to_sequential,
+   conflict pairs in the last conflicting round, iterations with no projected element (sent to
+   tile 0), first loop, number of loops. */
+int slt_schedule_info(slt_schedule sched, int32_t subchain, int64_t info[8]);
+/* Copy one integer array of the schedule to host memory.  Call with host_out = NULL to get
+   the length in *n.  kind:
+     0 rank of every seed element            (loop, desc ignored)
+     1 colour of every tile                  (loop, desc ignored)
+     2 tiling function sigma_j               (loop = j, chain-global index)
+     3 iteration-list offsets [ntiles + 1]   (loop)
+     4 iteration lists, ascending per tile   (loop)
+     5 local-map footprint offsets [ntiles+1](loop, desc = indirect descriptor index)
+     6 local-map footprints (sorted targets per tile)
+     7 local maps: position of map[i*arity+k] in the footprint of tile sigma_j[i]
+   The sub-chain is the one containing `loop` (kinds 0, 1: the sub-chain index in `loop`). */
+int slt_schedule_export(slt_schedule sched, int32_t kind, int32_t loop, int32_t desc,
+                        int32_t* host_out, int64_t* n);
+
+/* ------------------------------------------------------------------ DG elastic mesh
+ * Velocity-stress elastic waves in 2-D (Section 7.1): DG P_degree on affine triangles with
+ * centered fluxes, free surface on every exterior facet, explicit fourth-order staggered
+ * Taylor leapfrog.  Fields are nodal values on the equispaced points (i/p, j/p) of the
+ * reference triangle (0,0),(1,0),(0,1), j outer, i inner; the local vertex order of each cell
+ * defines its reference map.  Field layouts (host or device): v [ncell][2][Np] (vx, vy),
+ * sigma [ncell][3][Np] (sxx, syy, sxy), Np = (p+1)(p+2)/2, cells in the caller's numbering.
+ *
+ * cell2vert [ncell][3] vertex ids (topology: two cells sharing two vertex ids share a facet),
+ * cellxy [ncell][3][2] vertex coordinates per cell (periodic meshes: unwrapped per cell),
+ * rho, lam, mu [ncell] material; src_xy [2] explosive point source position (NULL: none).
+ * All host arrays, copied.  degree in 1..4.  The work layout on the device follows the
+ * Hilbert order of the cell centroids. */
+int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t ncell, int32_t degree,
+                    const double* rho, const double* lam, const double* mu, const double* src_xy,
+                    void* stream, slt_mesh* out);
+int slt_mesh_destroy(slt_mesh mesh);
+/* info[0..7] = ncell, degree, Np, interior facets, exterior facets, source cell (-1: none),
+   number of chain loops (17), velocity/stress split loop (9). */
+int slt_mesh_info(slt_mesh mesh, int64_t info[8]);
+/* The seventeen-loop chain of one time step over the sets cells (0), interior facets (1),
+   exterior facets (2), with maps facet->cell (arity 2, map 0) and exterior facet->cell
+   (arity 1, map 1); points: cell centroids ((x0 + x1) + x2) / 3 on set 0, facet midpoints
+   (xa + xb) * 0.5 on sets 1 and 2 (endpoints taken from the facet's first cell).  Facets are numbered by
+   (min vertex id, max vertex id); an interior facet lists its smaller cell id first.
+   Loops: volB intB extB volD intD hookeB intB extB updV | volD intD hookeB intB extB volD intD updS. */
+int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
+
+/* ------------------------------------------------------------------ executor (Section 5.2)
+ * nsteps time steps on device fields v, sigma (layout above, updated in place).
+ * ricker: device array [nsteps] of the source time function at t_{n+1/2} (NULL: no source).
+ * sched = NULL runs the plain untiled chain (one launch per loop, seventeen per step);
+ * otherwise the schedule must come from slt_inspect on slt_mesh_chain(mesh) and the tiled
+ * executor runs every sub-chain colour by colour, one CTA per tile, each tile executing its
+ * slice of every loop in chain order (Algorithm 4, shared-memory mode).  Library-owned work
+ * buffers are allocated at the first call for a mesh. */
+int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
+                double dt, int64_t nsteps, void* stream);
+/* slt_execute that also times every kernel launch with CUDA events recorded on `stream` and
+   synchronises before returning.  profile[0] = total ms of the chain kernels, [1] their number
+   of launches, [2] ms of the layout kernels (caller <-> work layout), [3] their launches,
+   [4] longest and [5] shortest chain-kernel launch in ms, [6..7] zero.  Not thread-safe:
+   one profiled call at a time per process. */
+int slt_execute_profiled(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
+                         double dt, int64_t nsteps, void* stream, double profile[8]);
+/* The same with HOST fields and source series: copies in, runs, copies out, synchronises. */
+int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* host_sigma,
+                     const double* host_ricker, double dt, int64_t nsteps, void* stream);
+/* Apply one operator once (for tests): op 0 = A (stress -> velocity rate, device
+   in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
+   out [ncell][3][Np]).  Runs the untiled loops of that operator. */
+int slt_apply_operator(slt_mesh mesh, int32_t op, const double* in, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -82,6 +82,7 @@ class Chain:
     def sub(self, start, stop):
         c = Chain()
         c.set_size, c.set_name, c.maps = self.set_size, self.set_name, self.maps
+        c.points = getattr(self, "points", {})
         c.loops = self.loops[start:stop]
         return c
 
@@ -123,7 +124,16 @@ def elastic_chain(mesh):
             ch.loop(sets[sname], [(m, "r"), (m, "i")], kname)
     X = np.asarray(mesh["cellxy"], dtype=np.float64)
     xy = np.stack([((X[:, 0, 0] + X[:, 1, 0]) + X[:, 2, 0]) / 3.0, ((X[:, 0, 1] + X[:, 1, 1]) + X[:, 2, 1]) / 3.0], 1)
+    ch.points = {C: np.ascontiguousarray(xy),
+                 F: _midpoints(X, inter[:, 0], inter[:, 1]), E: _midpoints(X, exter[:, 0], exter[:, 1])}
     return ch, np.ascontiguousarray(xy), inter, exter
+
+
+def _midpoints(X, cells, faces):
+    """(x_a + x_b) * 0.5 of local face f (vertices f, f+1) of each given cell."""
+    a = X[cells, faces]
+    b = X[cells, (faces + 1) % 3]
+    return np.ascontiguousarray((a + b) * 0.5)
 
 
 def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=None, max_rounds=16):

@@ -1,0 +1,302 @@
+"""Python binding of libslt.so: sparse-tiled DG elastic-wave time stepping on GB300.
+
+Argument marshalling only: every step of the inspector and executor runs in the CUDA library.
+The functions keep the names of the C entry points (include/slt.h).  Device arrays are torch
+CUDA tensors (float64 / int32, contiguous); host arrays are numpy arrays.  Importing this
+package loads the in-tree library and raises ImportError if it has not been built
+(python paper_1708_03183_gb300/build.py, or __graft_entry__.build()); there is no fallback
+implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+_LIB_PATH = _build_mod.LIB
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("libslt.so is not built (%s); run python paper_1708_03183_gb300/build.py" % _LIB_PATH)
+lib = ctypes.CDLL(_LIB_PATH)
+
+P = ctypes.c_void_p
+I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class slt_options(ctypes.Structure):
+    _fields_ = [("tile_size", I32), ("colouring", I32), ("renumber", I32), ("max_rounds", I32),
+                ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15)]
+
+
+_SIGS = {
+    "slt_last_error": (ctypes.c_char_p, []),
+    "slt_version": (ctypes.c_int, [P, P, P]),
+    "slt_chain_create": (ctypes.c_int, [P]),
+    "slt_chain_destroy": (ctypes.c_int, [P]),
+    "slt_set": (ctypes.c_int, [P, I64, P]),
+    "slt_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
+    "slt_loop": (ctypes.c_int, [P, I32, I32, P, P, P]),
+    "slt_set_points": (ctypes.c_int, [P, I32, P]),
+    "slt_chain_info": (ctypes.c_int, [P, P, P, P]),
+    "slt_options_default": (ctypes.c_int, [P]),
+    "slt_inspect": (ctypes.c_int, [P, P, P, P]),
+    "slt_schedule_destroy": (ctypes.c_int, [P]),
+    "slt_schedule_info": (ctypes.c_int, [P, I32, P]),
+    "slt_schedule_export": (ctypes.c_int, [P, I32, I32, I32, P, P]),
+    "slt_mesh_create": (ctypes.c_int, [P, P, I64, I32, P, P, P, P, P, P]),
+    "slt_mesh_destroy": (ctypes.c_int, [P]),
+    "slt_mesh_info": (ctypes.c_int, [P, P]),
+    "slt_mesh_chain": (ctypes.c_int, [P, P]),
+    "slt_execute": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
+    "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
+    "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
+    "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype, _f.argtypes = _res, _args
+
+STATUS = {0: "SLT_OK", -1: "SLT_ERR_ARG", -2: "SLT_ERR_OOM", -3: "SLT_ERR_CUDA", -4: "SLT_ERR_TIMEOUT",
+          -5: "SLT_ERR_CONFLICT_CAP", -6: "SLT_ERR_UNSUPPORTED", -7: "SLT_ERR_STATE"}
+
+
+class SltError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc != 0:
+        raise SltError(rc, lib.slt_last_error().decode(errors="replace"))
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev(t, dtype_name):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch." + dtype_name):
+        raise ValueError("expected a contiguous CUDA %s tensor" % dtype_name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    """A cudaStream_t: the given handle, torch's current stream, or NULL (legacy default)."""
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream)) if int(stream) else None
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(lib, self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chain(_Handle):
+    _destroy = "slt_chain_destroy"
+
+
+class Schedule(_Handle):
+    _destroy = "slt_schedule_destroy"
+
+
+class Mesh(_Handle):
+    _destroy = "slt_mesh_destroy"
+
+
+# ------------------------------------------------------------------ loop chain
+def slt_chain_create():
+    h = ctypes.c_void_p()
+    _check(lib.slt_chain_create(ctypes.byref(h)))
+    return Chain(h)
+
+
+def slt_set(chain, size):
+    i = I32()
+    _check(lib.slt_set(chain.ptr, int(size), ctypes.byref(i)))
+    return i.value
+
+
+def slt_map(chain, from_set, to_set, arity, values):
+    v, vp = _host(np.asarray(values).ravel(), np.int32)
+    i = I32()
+    _check(lib.slt_map(chain.ptr, from_set, to_set, arity, vp, ctypes.byref(i)))
+    return i.value
+
+
+def slt_loop(chain, set_id, descs):
+    """descs: list of (map id or -1, mode char)."""
+    ids, idp = _host([d[0] for d in descs], np.int32)
+    modes = ctypes.create_string_buffer("".join(d[1] for d in descs).encode())
+    i = I32()
+    _check(lib.slt_loop(chain.ptr, set_id, len(descs), idp, modes, ctypes.byref(i)))
+    return i.value
+
+
+def slt_set_points(chain, set_id, xy):
+    a, ap = _host(xy, np.float64)
+    _check(lib.slt_set_points(chain.ptr, set_id, ap))
+
+
+def slt_chain_info(chain):
+    a, b, c = I32(), I32(), I32()
+    _check(lib.slt_chain_info(chain.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------ inspector
+def slt_options_default(**kw):
+    o = slt_options()
+    _check(lib.slt_options_default(ctypes.byref(o)))
+    split = kw.pop("split", ())
+    for k, v in kw.items():
+        setattr(o, k, v)
+    o.nsplit = len(split)
+    for i, s in enumerate(split):
+        o.split[i] = s
+    return o
+
+
+def slt_inspect(chain, opts=None, stream=None, **kw):
+    if opts is None:
+        opts = slt_options_default(**kw)
+    h = ctypes.c_void_p()
+    _check(lib.slt_inspect(chain.ptr, ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return Schedule(h)
+
+
+def slt_schedule_info(sched, sub):
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib.slt_schedule_info(sched.ptr, sub, ctypes.c_void_p(info.ctypes.data)))
+    keys = ["ntiles", "ncolours", "restarts", "fell_back", "conflicts", "unprojected", "first", "nloops"]
+    return dict(zip(keys, (int(x) for x in info)))
+
+
+EXPORT_KINDS = {"rank": 0, "colour": 1, "sigma": 2, "list_ptr": 3, "list": 4, "fp_ptr": 5, "fp": 6, "lmap": 7}
+
+
+def slt_schedule_export(sched, kind, loop, desc=0):
+    k = EXPORT_KINDS.get(kind, kind)
+    n = I64()
+    _check(lib.slt_schedule_export(sched.ptr, k, loop, desc, None, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(lib.slt_schedule_export(sched.ptr, k, loop, desc, ctypes.c_void_p(out.ctypes.data), ctypes.byref(n)))
+    return out[:n.value]
+
+
+# ------------------------------------------------------------------ mesh and executor
+def slt_mesh_create(cell2vert, cellxy, degree, rho, lam, mu, src_xy=None, stream=None):
+    c2v, c2vp = _host(cell2vert, np.int32)
+    xy, xyp = _host(cellxy, np.float64)
+    r, rp = _host(rho, np.float64)
+    l, lp = _host(lam, np.float64)
+    m, mp = _host(mu, np.float64)
+    sp = None
+    if src_xy is not None:
+        s, sp = _host(src_xy, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.slt_mesh_create(c2vp, xyp, c2v.shape[0], degree, rp, lp, mp, sp, _stream(stream), ctypes.byref(h)))
+    return Mesh(h)
+
+
+def slt_mesh_info(mesh):
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib.slt_mesh_info(mesh.ptr, ctypes.c_void_p(info.ctypes.data)))
+    keys = ["ncell", "degree", "Np", "nfi", "nfe", "src_cell", "nloops", "split"]
+    return dict(zip(keys, (int(x) for x in info)))
+
+
+def slt_mesh_chain(mesh):
+    h = ctypes.c_void_p()
+    _check(lib.slt_mesh_chain(mesh.ptr, ctypes.byref(h)))
+    return Chain(h)
+
+
+def _check_fields(mesh, v, sigma, ricker, nsteps):
+    info = slt_mesh_info(mesh)
+    nv, ns = info["ncell"] * 2 * info["Np"], info["ncell"] * 3 * info["Np"]
+    if v.numel() != nv or sigma.numel() != ns:
+        raise ValueError("v needs %d and sigma %d float64 values" % (nv, ns))
+    if ricker is not None and ricker.numel() < nsteps:
+        raise ValueError("the source series is shorter than nsteps")
+
+
+def slt_execute(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None):
+    """v [ncell, 2, Np], sigma [ncell, 3, Np]: CUDA float64 tensors, updated in place;
+    ricker: CUDA float64 [nsteps] or None; sched None = plain untiled chain."""
+    _check_fields(mesh, v, sigma, ricker, nsteps)
+    _check(lib.slt_execute(mesh.ptr, sched.ptr if sched is not None else None, _dev(v, "float64"),
+                           _dev(sigma, "float64"), _dev(ricker, "float64"), float(dt), int(nsteps), _stream(stream)))
+
+
+def slt_execute_profiled(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None):
+    """slt_execute with per-launch CUDA-event timing; returns a dict of kernel times."""
+    _check_fields(mesh, v, sigma, ricker, nsteps)
+    prof = np.zeros(8, dtype=np.float64)
+    _check(lib.slt_execute_profiled(mesh.ptr, sched.ptr if sched is not None else None, _dev(v, "float64"),
+                                    _dev(sigma, "float64"), _dev(ricker, "float64"), float(dt), int(nsteps),
+                                    _stream(stream), ctypes.c_void_p(prof.ctypes.data)))
+    return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
+                max_launch_ms=prof[4], min_launch_ms=prof[5])
+
+
+def slt_execute_host(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None):
+    """Host (numpy or pinned CPU torch) fields, updated in place; returns when done."""
+    def ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("expected a contiguous CPU tensor")
+            return ctypes.c_void_p(a.data_ptr())
+        if not (a.flags["C_CONTIGUOUS"] and a.dtype == np.float64):
+            raise ValueError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(a.ctypes.data)
+    _check_fields(mesh, v if hasattr(v, "numel") else _np_numel(v), sigma if hasattr(sigma, "numel") else _np_numel(sigma),
+                  None if ricker is None else (ricker if hasattr(ricker, "numel") else _np_numel(ricker)), nsteps)
+    _check(lib.slt_execute_host(mesh.ptr, sched.ptr if sched is not None else None, ptr(v), ptr(sigma),
+                                ptr(ricker), float(dt), int(nsteps), _stream(stream)))
+
+
+class _np_numel:
+    def __init__(self, a):
+        self.n = int(np.asarray(a).size)
+
+    def numel(self):
+        return self.n
+
+
+def slt_apply_operator(mesh, op, x, out, stream=None):
+    info = slt_mesh_info(mesh)
+    rin, rout = (3, 2) if op == 0 else (2, 3)
+    if x.numel() != info["ncell"] * rin * info["Np"] or out.numel() != info["ncell"] * rout * info["Np"]:
+        raise ValueError("operator input/output sizes do not match the mesh")
+    _check(lib.slt_apply_operator(mesh.ptr, op, _dev(x, "float64"), _dev(out, "float64"), _stream(stream)))
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/slt.h."""
+    import re
+    hdr = open(os.path.join(_build_mod.ROOT, "include", "slt.h")).read()
+    return sorted(set(re.findall(r"\b(slt_[a-z_]+)\s*\(", hdr)))

@@ -1,0 +1,516 @@
+// C ABI of libslt.so: argument validation, object lifetimes, mesh set-up and the elastic chain.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace slt {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    fail(SLT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+}  // namespace slt
+
+using namespace slt;
+
+#define API_BEGIN try {
+#define API_END                                             \
+  }                                                         \
+  catch (const slt::Error& e) {                             \
+    slt::set_error(e.msg);                                  \
+    return e.code;                                          \
+  }                                                         \
+  catch (const std::bad_alloc&) {                           \
+    slt::set_error("host allocation failed");               \
+    return SLT_ERR_OOM;                                     \
+  }                                                         \
+  catch (...) {                                             \
+    slt::set_error("unexpected exception");                 \
+    return SLT_ERR_CUDA;                                    \
+  }                                                         \
+  return SLT_OK;
+
+#define REQUIRE(cond, msg) \
+  do {                     \
+    if (!(cond)) fail(SLT_ERR_ARG, msg); \
+  } while (0)
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+const char* slt_last_error(void) { return g_err.c_str(); }
+
+int slt_version(int32_t* major, int32_t* minor, int32_t* arch) {
+  API_BEGIN
+  if (major) *major = 1;
+  if (minor) *minor = 0;
+  if (arch) *arch = 103;
+  API_END
+}
+
+// ------------------------------------------------------------------ loop chain
+int slt_chain_create(slt_chain* out) {
+  API_BEGIN
+  REQUIRE(out, "out is null");
+  *out = new slt_chain_s();
+  API_END
+}
+
+int slt_chain_destroy(slt_chain chain) {
+  API_BEGIN
+  delete chain;
+  API_END
+}
+
+int slt_set(slt_chain c, int64_t size, int32_t* set_id) {
+  API_BEGIN
+  REQUIRE(c && set_id, "null argument");
+  REQUIRE(size >= 0 && size < (int64_t(1) << 31), "set size must be in [0, 2^31)");
+  c->set_size.push_back(size);
+  c->points.emplace_back();
+  *set_id = (int32_t)c->set_size.size() - 1;
+  API_END
+}
+
+int slt_map(slt_chain c, int32_t from_set, int32_t to_set, int32_t arity, const int32_t* host_values, int32_t* map_id) {
+  API_BEGIN
+  REQUIRE(c && map_id, "null argument");
+  const int32_t ns = (int32_t)c->set_size.size();
+  REQUIRE(from_set >= 0 && from_set < ns && to_set >= 0 && to_set < ns, "unknown set");
+  REQUIRE(arity >= 1 && arity <= 64, "arity must be in 1..64");
+  const int64_t n = c->set_size[from_set] * (int64_t)arity;
+  REQUIRE(n < (int64_t(1) << 31), "map too large");
+  REQUIRE(host_values || n == 0, "values are null");
+  MapH M{from_set, to_set, arity, std::vector<int32_t>(host_values, host_values + n)};
+  for (int32_t v : M.values) REQUIRE(v >= 0 && v < c->set_size[to_set], "map value outside the target set");
+  c->maps.push_back(std::move(M));
+  *map_id = (int32_t)c->maps.size() - 1;
+  API_END
+}
+
+int slt_loop(slt_chain c, int32_t set_id, int32_t ndesc, const int32_t* map_ids, const char* modes, int32_t* loop_id) {
+  API_BEGIN
+  REQUIRE(c && loop_id && map_ids && modes, "null argument");
+  REQUIRE(set_id >= 0 && set_id < (int32_t)c->set_size.size(), "unknown set");
+  REQUIRE(ndesc >= 1 && ndesc <= 8, "ndesc must be in 1..8");
+  LoopH L{set_id, {}, -1};
+  for (int d = 0; d < ndesc; ++d) {
+    REQUIRE(modes[d] == 'r' || modes[d] == 'w' || modes[d] == 'i', "mode must be r, w or i");
+    REQUIRE(map_ids[d] >= -1 && map_ids[d] < (int32_t)c->maps.size(), "unknown map");
+    if (map_ids[d] >= 0) REQUIRE(c->maps[map_ids[d]].from == set_id, "map does not start at the loop's set");
+    L.descs.push_back({map_ids[d], modes[d]});
+  }
+  c->loops.push_back(std::move(L));
+  *loop_id = (int32_t)c->loops.size() - 1;
+  API_END
+}
+
+int slt_set_points(slt_chain c, int32_t set_id, const double* xy) {
+  API_BEGIN
+  REQUIRE(c && xy, "null argument");
+  REQUIRE(set_id >= 0 && set_id < (int32_t)c->set_size.size(), "unknown set");
+  const int64_t n = c->set_size[set_id];
+  for (int64_t i = 0; i < 2 * n; ++i) REQUIRE(std::isfinite(xy[i]), "points must be finite");
+  c->points[set_id].assign(xy, xy + 2 * n);
+  API_END
+}
+
+int slt_chain_info(slt_chain c, int32_t* nsets, int32_t* nmaps, int32_t* nloops) {
+  API_BEGIN
+  REQUIRE(c, "null chain");
+  if (nsets) *nsets = (int32_t)c->set_size.size();
+  if (nmaps) *nmaps = (int32_t)c->maps.size();
+  if (nloops) *nloops = (int32_t)c->loops.size();
+  API_END
+}
+
+// ------------------------------------------------------------------ inspector
+int slt_options_default(slt_options* o) {
+  API_BEGIN
+  REQUIRE(o, "null options");
+  std::memset(o, 0, sizeof(*o));
+  o->tile_size = 1024;
+  o->colouring = 0;
+  o->renumber = 1;
+  o->max_rounds = 16;
+  o->prio_seed = 0x5EED;
+  o->nsplit = 0;
+  API_END
+}
+
+int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule* out) {
+  API_BEGIN
+  REQUIRE(c && opt && out, "null argument");
+  *out = nullptr;
+  REQUIRE(!c->loops.empty(), "the chain has no loop");
+  REQUIRE(opt->tile_size >= 1, "tile_size must be >= 1");
+  REQUIRE(opt->colouring == 0 || opt->colouring == 1, "colouring must be 0 or 1");
+  REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
+  REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
+  REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
+  const int nl = (int)c->loops.size();
+  int prev = 0;
+  for (int k = 0; k < opt->nsplit; ++k) {
+    REQUIRE(opt->split[k] > prev && opt->split[k] < nl, "split points must increase strictly inside (0, nloops)");
+    prev = opt->split[k];
+  }
+  std::vector<int> starts = {0};
+  for (int k = 0; k < opt->nsplit; ++k) starts.push_back(opt->split[k]);
+  for (int st : starts) {
+    int seed_set = c->loops[st].set;
+    if (opt->renumber)
+      REQUIRE((int64_t)c->points[seed_set].size() == 2 * c->set_size[seed_set],
+              "renumber = 1 needs points on the seed set");
+  }
+  std::unique_ptr<slt_schedule_s> s(new slt_schedule_s());
+  s->loops = c->loops;
+  for (const MapH& M : c->maps) s->maps_meta.push_back({M.from, M.to, M.arity, {}});
+  s->set_size = c->set_size;
+  s->mesh = c->mesh;
+  inspect_chain(c, *opt, as_stream(stream), s.get());
+  *out = s.release();
+  API_END
+}
+
+int slt_schedule_destroy(slt_schedule s) {
+  API_BEGIN
+  delete s;
+  API_END
+}
+
+int slt_schedule_info(slt_schedule s, int32_t sub, int64_t info[8]) {
+  API_BEGIN
+  REQUIRE(s && info, "null argument");
+  REQUIRE(sub >= 0 && sub < (int32_t)s->subs.size(), "unknown sub-chain");
+  const SubSched& S = s->subs[sub];
+  info[0] = S.m;
+  info[1] = S.ncolours;
+  info[2] = S.restarts;
+  info[3] = S.fell_back;
+  info[4] = S.conflicts;
+  info[5] = S.unprojected;
+  info[6] = S.first;
+  info[7] = S.last - S.first;
+  API_END
+}
+
+int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc, int32_t* host_out, int64_t* n) {
+  API_BEGIN
+  REQUIRE(s && n, "null argument");
+  REQUIRE(kind >= 0 && kind <= 7, "unknown kind");
+  const SubSched* S = nullptr;
+  int jj = 0;
+  if (kind <= 1) {
+    REQUIRE(loop >= 0 && loop < (int32_t)s->subs.size(), "unknown sub-chain");
+    S = &s->subs[loop];
+  } else {
+    REQUIRE(loop >= 0 && loop < (int32_t)s->loops.size(), "unknown loop");
+    for (const SubSched& x : s->subs)
+      if (loop >= x.first && loop < x.last) { S = &x; jj = loop - x.first; }
+    REQUIRE(S, "loop not inspected");
+  }
+  const int32_t* src = nullptr;
+  int64_t len = 0;
+  const LoopH* L = kind >= 2 ? &s->loops[loop] : nullptr;
+  switch (kind) {
+    case 0: src = S->rank.p; len = s->set_size[s->loops[S->first].set]; break;
+    case 1: src = S->colour.p; len = S->m; break;
+    case 2: src = S->sigma[jj].p; len = s->set_size[L->set]; break;
+    case 3: src = S->list_ptr[jj].p; len = S->m + 1; break;
+    case 4: src = S->list[jj].p; len = s->set_size[L->set]; break;
+    default: {
+      REQUIRE(desc >= 0 && desc < (int32_t)L->descs.size() && L->descs[desc].map >= 0,
+              "desc must name an indirect descriptor");
+      const LocalMap& lm = S->lmaps[jj][desc];
+      if (kind == 5) { src = lm.fp_ptr.p; len = S->m + 1; }
+      else if (kind == 6) {
+        int32_t tot = 0;
+        SLT_CUDA(cudaMemcpy(&tot, lm.fp_ptr.p + S->m, 4, cudaMemcpyDeviceToHost));
+        src = lm.fp.p;
+        len = tot;
+      } else { src = lm.lmap.p; len = s->set_size[L->set] * (int64_t)s->maps_meta[L->descs[desc].map].arity; }
+    }
+  }
+  *n = len;
+  if (host_out && len) SLT_CUDA(cudaMemcpy(host_out, src, len * 4, cudaMemcpyDeviceToHost));
+  API_END
+}
+
+// ------------------------------------------------------------------ mesh
+int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, int32_t degree, const double* rho,
+                    const double* lam, const double* mu, const double* src_xy, void* stream, slt_mesh* out) {
+  API_BEGIN
+  REQUIRE(out, "out is null");
+  *out = nullptr;
+  REQUIRE(cell2vert && cellxy && rho && lam && mu, "null argument");
+  REQUIRE(nc >= 1 && nc < (int64_t(1) << 28), "ncell must be in [1, 2^28)");
+  REQUIRE(degree >= 1 && degree <= 4, "degree must be in 1..4");
+  cudaStream_t s = as_stream(stream);
+  std::unique_ptr<slt_mesh_s> m(new slt_mesh_s());
+  m->nc = nc;
+  m->ncp = (nc + 63) / 64 * 64;
+  m->p = degree;
+  m->ref = make_refelem(degree);
+  m->Np = m->ref.Np;
+  m->Nfp = m->ref.Nfp;
+  for (int64_t i = 0; i < 3 * nc; ++i) REQUIRE(cell2vert[i] >= 0, "negative vertex id");
+  for (int64_t i = 0; i < 6 * nc; ++i) REQUIRE(std::isfinite(cellxy[i]), "coordinates must be finite");
+  for (int64_t c = 0; c < nc; ++c) {
+    REQUIRE(std::isfinite(rho[c]) && rho[c] > 0, "rho must be finite and positive");
+    REQUIRE(std::isfinite(lam[c]) && std::isfinite(mu[c]), "lambda and mu must be finite");
+  }
+  // facets: (min vertex, max vertex, cell, local face, start vertex), sorted by key then cell
+  struct Ent { int32_t lo, hi, cell, face, start; };
+  std::vector<Ent> ent(3 * nc);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int f = 0; f < 3; ++f) {
+      int32_t a = cell2vert[3 * c + f], b = cell2vert[3 * c + (f + 1) % 3];
+      REQUIRE(a != b, "a cell repeats a vertex");
+      ent[3 * c + f] = {std::min(a, b), std::max(a, b), (int32_t)c, f, a};
+    }
+  std::sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y) {
+    if (x.lo != y.lo) return x.lo < y.lo;
+    if (x.hi != y.hi) return x.hi < y.hi;
+    return x.cell < y.cell;
+  });
+  std::vector<std::array<int32_t, 3>> nbr_c(nc, {-1, -1, -1});   // neighbour cell, caller numbering
+  std::vector<std::array<int8_t, 3>> nbr_f(nc), nbr_flip(nc);
+  for (size_t i = 0; i < ent.size();) {
+    size_t j = i + 1;
+    while (j < ent.size() && ent[j].lo == ent[i].lo && ent[j].hi == ent[i].hi) ++j;
+    REQUIRE(j - i <= 2, "an edge is shared by more than two cells");
+    if (j - i == 2) {
+      const Ent &A = ent[i], &B = ent[i + 1];
+      REQUIRE(A.cell != B.cell, "a cell touches the same edge twice");
+      int8_t flip = A.start != B.start;
+      m->f2c.push_back(A.cell);
+      m->f2c.push_back(B.cell);
+      m->f2f.push_back((int8_t)A.face);
+      m->f2f.push_back((int8_t)B.face);
+      nbr_c[A.cell][A.face] = B.cell; nbr_f[A.cell][A.face] = (int8_t)B.face; nbr_flip[A.cell][A.face] = flip;
+      nbr_c[B.cell][B.face] = A.cell; nbr_f[B.cell][B.face] = (int8_t)A.face; nbr_flip[B.cell][B.face] = flip;
+    } else {
+      m->e2c.push_back(ent[i].cell);
+      m->e2f.push_back((int8_t)ent[i].face);
+    }
+    i = j;
+  }
+  // facet midpoints (x_a + x_b) * 0.5 from the first listed cell, points of the facet sets
+  auto midpoint = [&](int32_t c, int f, std::vector<double>& out) {
+    const double* X = cellxy + 6 * (int64_t)c;
+    out.push_back((X[2 * f] + X[2 * ((f + 1) % 3)]) * 0.5);
+    out.push_back((X[2 * f + 1] + X[2 * ((f + 1) % 3) + 1]) * 0.5);
+  };
+  for (size_t k = 0; k < m->f2c.size() / 2; ++k) midpoint(m->f2c[2 * k], m->f2f[2 * k], m->fmid);
+  for (size_t k = 0; k < m->e2c.size(); ++k) midpoint(m->e2c[k], m->e2f[k], m->emid);
+  m->nfi = (int64_t)m->f2c.size() / 2;
+  m->nfe = (int64_t)m->e2c.size();
+  // geometry (caller numbering)
+  std::vector<double> rx(nc), ry(nc), sx(nc), sy(nc), adet(nc), fg(9 * nc);
+  m->centroid.resize(2 * nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    const double* X = cellxy + 6 * c;
+    double j11 = X[2] - X[0], j21 = X[3] - X[1], j12 = X[4] - X[0], j22 = X[5] - X[1];
+    double det = j11 * j22 - j12 * j21;
+    REQUIRE(det != 0.0 && std::isfinite(det), "degenerate cell");
+    rx[c] = j22 / det; ry[c] = -j12 / det; sx[c] = -j21 / det; sy[c] = j11 / det;
+    adet[c] = std::fabs(det);
+    for (int f = 0; f < 3; ++f) {
+      const double *P = X + 2 * f, *Q = X + 2 * ((f + 1) % 3), *O = X + 2 * ((f + 2) % 3);
+      double tx = Q[0] - P[0], ty = Q[1] - P[1];
+      double len = std::hypot(tx, ty);
+      double nx = ty / len, ny = -tx / len;
+      if (nx * (O[0] - P[0]) + ny * (O[1] - P[1]) > 0) { nx = -nx; ny = -ny; }
+      fg[9 * c + 3 * f] = nx;
+      fg[9 * c + 3 * f + 1] = ny;
+      fg[9 * c + 3 * f + 2] = len / adet[c];
+    }
+    m->centroid[2 * c] = ((X[0] + X[2]) + X[4]) / 3.0;
+    m->centroid[2 * c + 1] = ((X[1] + X[3]) + X[5]) / 3.0;
+  }
+  // work order: Hilbert order of the centroids
+  {
+    DevBuf<double> xy(2 * nc);
+    xy.upload(m->centroid.data(), 2 * nc, s);
+    DevBuf<int32_t> rank(nc);
+    seed_rank(xy.p, nc, 1, rank.p, s);
+    m->iperm = rank.download(s);
+    m->perm.assign(nc, 0);
+    for (int64_t c = 0; c < nc; ++c) m->perm[m->iperm[c]] = (int32_t)c;
+  }
+  const int64_t ncp = m->ncp;
+  std::vector<double> hgeo(4 * ncp, 0.0), hfgeo(9 * ncp, 0.0), hmat(3 * ncp, 0.0);
+  std::vector<int32_t> hnbr(3 * ncp, -1);
+  for (int64_t w = 0; w < nc; ++w) {
+    int64_t c = m->perm[w];
+    hgeo[w] = rx[c]; hgeo[ncp + w] = ry[c]; hgeo[2 * ncp + w] = sx[c]; hgeo[3 * ncp + w] = sy[c];
+    for (int q = 0; q < 9; ++q) hfgeo[q * ncp + w] = fg[9 * c + q];
+    hmat[w] = 1.0 / rho[c]; hmat[ncp + w] = lam[c]; hmat[2 * ncp + w] = mu[c];
+    for (int f = 0; f < 3; ++f)
+      if (nbr_c[c][f] >= 0)
+        hnbr[f * ncp + w] = (m->iperm[nbr_c[c][f]] << 3) | (nbr_f[c][f] << 1) | nbr_flip[c][f];
+  }
+  m->geo.alloc(4 * ncp); m->geo.upload(hgeo.data(), 4 * ncp, s);
+  m->fgeo.alloc(9 * ncp); m->fgeo.upload(hfgeo.data(), 9 * ncp, s);
+  m->mat.alloc(3 * ncp); m->mat.upload(hmat.data(), 3 * ncp, s);
+  m->nbr.alloc(3 * ncp); m->nbr.upload(hnbr.data(), 3 * ncp, s);
+  m->d_perm.alloc(nc); m->d_perm.upload(m->perm.data(), nc, s);
+  m->d_iperm.alloc(nc); m->d_iperm.upload(m->iperm.data(), nc, s);
+  // point source: smallest cell id whose barycentric coordinates are all >= -1e-12
+  std::vector<double> hsrc(m->Np, 0.0);
+  if (src_xy) {
+    REQUIRE(std::isfinite(src_xy[0]) && std::isfinite(src_xy[1]), "source position must be finite");
+    for (int64_t c = 0; c < nc && m->src_cell < 0; ++c) {
+      const double* X = cellxy + 6 * c;
+      double dx = src_xy[0] - X[0], dy = src_xy[1] - X[1];
+      double r = rx[c] * dx + ry[c] * dy, t = sx[c] * dx + sy[c] * dy;
+      if (r >= -1e-12 && t >= -1e-12 && 1.0 - r - t >= -1e-12) {
+        m->src_cell = c;
+        std::vector<double> phi = m->ref.eval(r, t);
+        for (int i = 0; i < m->Np; ++i) {
+          double acc = 0.0;
+          for (int j = 0; j < m->Np; ++j) acc += m->ref.Minv[i * m->Np + j] * phi[j];
+          hsrc[i] = acc / adet[c];
+        }
+      }
+    }
+    REQUIRE(m->src_cell >= 0, "the source lies outside the mesh");
+    m->src_w = m->iperm[m->src_cell];
+  }
+  m->src.alloc(m->Np);
+  m->src.upload(hsrc.data(), m->Np, s);
+  upload_constants(m->ref);
+  m->work.alloc(15 * (int64_t)m->Np * ncp);
+  SLT_CUDA(cudaMemsetAsync(m->work.p, 0, 15 * (int64_t)m->Np * ncp * sizeof(double), s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  *out = m.release();
+  API_END
+}
+
+int slt_mesh_destroy(slt_mesh m) {
+  API_BEGIN
+  delete m;
+  API_END
+}
+
+int slt_mesh_info(slt_mesh m, int64_t info[8]) {
+  API_BEGIN
+  REQUIRE(m && info, "null argument");
+  info[0] = m->nc;
+  info[1] = m->p;
+  info[2] = m->Np;
+  info[3] = m->nfi;
+  info[4] = m->nfe;
+  info[5] = m->src_cell;
+  info[6] = 17;
+  info[7] = 9;
+  API_END
+}
+
+int slt_mesh_chain(slt_mesh m, slt_chain* out) {
+  API_BEGIN
+  REQUIRE(m && out, "null argument");
+  std::unique_ptr<slt_chain_s> c(new slt_chain_s());
+  c->set_size = {m->nc, m->nfi, m->nfe};
+  c->points.resize(3);
+  c->points[0] = m->centroid;
+  c->points[1] = m->fmid;
+  c->points[2] = m->emid;
+  c->maps.push_back({1, 0, 2, m->f2c});
+  c->maps.push_back({2, 0, 1, m->e2c});
+  // (set, kernel) of the seventeen loops; cell loops: direct read + direct write (updates:
+  // increment); facet loops: read and increment cells through their facet->cell map
+  static const int32_t sets[17] = {0, 1, 2, 0, 1, 0, 1, 2, 0, 0, 1, 0, 1, 2, 0, 1, 0};
+  static const int32_t kern[17] = {K_VOLB, K_INTB, K_EXTB, K_VOLD, K_INTD, K_HOOKEB, K_INTB, K_EXTB, K_UPDV,
+                                   K_VOLD, K_INTD, K_HOOKEB, K_INTB, K_EXTB, K_VOLD, K_INTD, K_UPDS};
+  for (int j = 0; j < 17; ++j) {
+    LoopH L{sets[j], {}, kern[j]};
+    if (sets[j] == 0) {
+      L.descs.push_back({-1, 'r'});
+      L.descs.push_back({-1, (kern[j] == K_UPDV || kern[j] == K_UPDS) ? 'i' : 'w'});
+    } else {
+      int mid = sets[j] == 1 ? 0 : 1;
+      L.descs.push_back({mid, 'r'});
+      L.descs.push_back({mid, 'i'});
+    }
+    c->loops.push_back(L);
+  }
+  c->mesh = m;
+  *out = c.release();
+  API_END
+}
+
+// ------------------------------------------------------------------ executor
+int slt_execute(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
+                int64_t nsteps, void* stream) {
+  API_BEGIN
+  REQUIRE(m && v && sigma, "null argument");
+  REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  REQUIRE(std::isfinite(dt), "dt must be finite");
+  if (sched) {
+    if (sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  }
+  exec_run(m, sched, v, sigma, ricker, dt, nsteps, as_stream(stream));
+  API_END
+}
+
+int slt_execute_profiled(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
+                         int64_t nsteps, void* stream, double profile[8]) {
+  API_BEGIN
+  REQUIRE(m && v && sigma && profile, "null argument");
+  REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  REQUIRE(std::isfinite(dt), "dt must be finite");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  exec_run(m, sched, v, sigma, ricker, dt, nsteps, as_stream(stream), profile);
+  API_END
+}
+
+int slt_execute_host(slt_mesh m, slt_schedule sched, double* hv, double* hs, const double* hr, double dt,
+                     int64_t nsteps, void* stream) {
+  API_BEGIN
+  REQUIRE(m && hv && hs, "null argument");
+  REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  REQUIRE(std::isfinite(dt), "dt must be finite");
+  if (sched) {
+    if (sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  }
+  cudaStream_t s = as_stream(stream);
+  const int64_t nv = m->nc * 2 * m->Np, ns = m->nc * 3 * m->Np;
+  if (m->io_v.n < (size_t)nv) m->io_v.alloc(nv);
+  if (m->io_s.n < (size_t)ns) m->io_s.alloc(ns);
+  if (hr && m->ricker_buf.n < (size_t)std::max<int64_t>(nsteps, 1)) m->ricker_buf.alloc(std::max<int64_t>(nsteps, 1));
+  m->io_v.upload(hv, nv, s);
+  m->io_s.upload(hs, ns, s);
+  if (hr) m->ricker_buf.upload(hr, nsteps, s);
+  exec_run(m, sched, m->io_v.p, m->io_s.p, hr ? m->ricker_buf.p : nullptr, dt, nsteps, s);
+  SLT_CUDA(cudaMemcpyAsync(hv, m->io_v.p, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaMemcpyAsync(hs, m->io_s.p, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+int slt_apply_operator(slt_mesh m, int32_t op, const double* in, double* out, void* stream) {
+  API_BEGIN
+  REQUIRE(m && in && out, "null argument");
+  REQUIRE(op == 0 || op == 1, "op must be 0 (A) or 1 (B)");
+  exec_apply(m, op, in, out, as_stream(stream));
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,685 @@
+// Sparse-tiling inspector on the GPU (Section 5.1: Algorithm 1 with Algorithms 2 and 3).
+//
+// Every step is a data-parallel kernel whose result does not depend on thread scheduling, so
+// the integer output equals a sequential execution of the same rules:
+//   partition   rank / ts, ranks from a stable radix sort of Hilbert keys (sort.cu)
+//   adjacency   tile pairs through the seed map plus fake edges, sorted and de-duplicated
+//   colouring   Jones-Plassmann rounds: a tile is coloured once all higher-priority neighbours
+//               are; it takes the smallest colour none of them has (= greedy in priority order)
+//   projection  one thread per element of the projected set walks its inverse-map row in
+//               ascending (iteration, slot) order; strictly larger colour replaces; equal
+//               colours of distinct tiles among the candidates are recorded as conflicts
+//   tiling      one thread per iteration, descriptors and slots in order, strict maximum
+//   lists       stable radix sort of iterations by tile
+//   local maps  stable sorts of slots by (tile, target), de-duplicated per tile
+// Conflict pairs (few) are de-duplicated on the host and become fake edges for the next round.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace slt {
+
+namespace {
+
+inline int grid_for(int64_t n, int threads = 256) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return g < 1 ? 1 : (int)g;
+}
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_div(const int32_t* __restrict__ rank, int64_t n, int32_t ts, int32_t* __restrict__ sig) {
+  GRID_STRIDE(e, n) sig[e] = rank[e] / ts;
+}
+__global__ void k_fill(int32_t* __restrict__ a, int64_t n, int32_t v) {
+  GRID_STRIDE(e, n) a[e] = v;
+}
+__global__ void k_fill_u(uint32_t* __restrict__ a, int64_t n, uint32_t v) {
+  GRID_STRIDE(e, n) a[e] = v;
+}
+__global__ void k_iota_u(uint32_t* __restrict__ a, int64_t n) {
+  GRID_STRIDE(e, n) a[e] = (uint32_t)e;
+}
+__global__ void k_copy_i2u(const int32_t* __restrict__ a, int64_t n, uint32_t* __restrict__ b) {
+  GRID_STRIDE(e, n) b[e] = (uint32_t)a[e];
+}
+// b[e] = src[idx[e] / div]
+__global__ void k_gather_div(const int32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n, int div,
+                             uint32_t* __restrict__ b) {
+  GRID_STRIDE(e, n) b[e] = (uint32_t)src[idx[e] / div];
+}
+
+// pairs of distinct slot tiles of every element of a map that targets the seed set
+__global__ void k_pairs_target(const int32_t* __restrict__ map, int64_t nsrc, int a, const int32_t* __restrict__ sig0,
+                               uint32_t m, uint32_t* __restrict__ pa, uint32_t* __restrict__ pb) {
+  GRID_STRIDE(e, nsrc) {
+    for (int x = 0; x < a; ++x)
+      for (int y = 0; y < a; ++y) {
+        uint32_t ta = (uint32_t)sig0[map[e * a + x]], tb = (uint32_t)sig0[map[e * a + y]];
+        int64_t o = (e * a + x) * a + y;
+        pa[o] = ta != tb ? ta : m;
+        pb[o] = ta != tb ? tb : m;
+      }
+  }
+}
+// count deg^2 of every target element of a map leaving the seed set
+__global__ void k_pairs_count(const int32_t* __restrict__ ioff, int64_t ntgt, int32_t* __restrict__ cnt) {
+  GRID_STRIDE(e, ntgt) {
+    int32_t d = ioff[e + 1] - ioff[e];
+    cnt[e] = d * d;
+  }
+}
+__global__ void k_pairs_source(const int32_t* __restrict__ ioff, const uint32_t* __restrict__ islot, int64_t ntgt,
+                               int a, const int32_t* __restrict__ cntoff, const int32_t* __restrict__ sig0, uint32_t m,
+                               uint32_t* __restrict__ pa, uint32_t* __restrict__ pb) {
+  GRID_STRIDE(e, ntgt) {
+    int32_t b = ioff[e], d = ioff[e + 1] - b;
+    int64_t o = cntoff[e];
+    for (int x = 0; x < d; ++x)
+      for (int y = 0; y < d; ++y) {
+        uint32_t ta = (uint32_t)sig0[islot[b + x] / a], tb = (uint32_t)sig0[islot[b + y] / a];
+        pa[o] = ta != tb ? ta : m;
+        pb[o] = ta != tb ? tb : m;
+        ++o;
+      }
+  }
+}
+// first occurrence of each distinct (a, b) with a < m in a sequence sorted by (a, b)
+__global__ void k_unique_flags(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, int64_t n, uint32_t m,
+                               int32_t* __restrict__ flag) {
+  GRID_STRIDE(p, n) flag[p] = (a[p] < m) && (p == 0 || a[p] != a[p - 1] || b[p] != b[p - 1]);
+}
+__global__ void k_compact2(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, const int32_t* __restrict__ flag,
+                           const int32_t* __restrict__ pos, int64_t n, uint32_t* __restrict__ oa, int32_t* __restrict__ ob) {
+  GRID_STRIDE(p, n) if (flag[p]) {
+    oa[pos[p]] = a[p];
+    ob[pos[p]] = (int32_t)b[p];
+  }
+}
+
+__global__ void k_priorities(int32_t m, uint64_t seed, uint64_t* __restrict__ prio) {
+  GRID_STRIDE(t, m) prio[t] = splitmix64((uint64_t)t ^ seed);
+}
+__global__ void k_jp_round(int32_t m, const int32_t* __restrict__ aoff, const int32_t* __restrict__ adj,
+                           const uint64_t* __restrict__ prio, int32_t* col, int32_t* __restrict__ remaining) {
+  GRID_STRIDE(t, m) {
+    if (((volatile int32_t*)col)[t] >= 0) continue;
+    const uint64_t pt = prio[t];
+    bool ready = true;
+    for (int32_t k = aoff[t]; k < aoff[t + 1] && ready; ++k) {
+      int32_t u = adj[k];
+      if (prio[u] > pt || (prio[u] == pt && u < t)) ready = ((volatile int32_t*)col)[u] >= 0;
+    }
+    if (!ready) {
+      atomicAdd(remaining, 1);
+      continue;
+    }
+    int32_t c = 0;
+    for (;;) {
+      bool used = false;
+      for (int32_t k = aoff[t]; k < aoff[t + 1]; ++k) {
+        int32_t u = adj[k];
+        if ((prio[u] > pt || (prio[u] == pt && u < t)) && ((volatile int32_t*)col)[u] == c) { used = true; break; }
+      }
+      if (!used) break;
+      ++c;
+    }
+    ((volatile int32_t*)col)[t] = c;
+  }
+}
+
+__device__ __forceinline__ void push_conflict(int32_t x, int32_t y, int2* buf, int32_t* cnt, int32_t cap) {
+  int32_t i = atomicAdd(cnt, 1);
+  if (i < cap) buf[i] = make_int2(x < y ? x : y, x < y ? y : x);
+}
+
+__global__ void k_project_direct(int64_t n, const int32_t* __restrict__ sig, const int32_t* __restrict__ col,
+                                 int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap) {
+  GRID_STRIDE(e, n) {
+    int32_t old = phi[e], t = sig[e];
+    if (old < 0 || col[t] > col[old]) phi[e] = t;
+    else if (t != old && col[t] == col[old]) push_conflict(old, t, cbuf, ccnt, cap);
+  }
+}
+__global__ void k_project_indirect(int64_t n, const int32_t* __restrict__ ioff, const uint32_t* __restrict__ islot,
+                                   int a, const int32_t* __restrict__ sig, const int32_t* __restrict__ col,
+                                   int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap) {
+  GRID_STRIDE(e, n) {
+    const int32_t b = ioff[e], d = ioff[e + 1] - b;
+    const int32_t old = phi[e];
+    int32_t cur = old;
+    for (int k = 0; k < d; ++k) {
+      int32_t t = sig[islot[b + k] / a];
+      if (cur < 0 || col[t] > col[cur]) cur = t;
+    }
+    phi[e] = cur;
+    // conflicts: distinct same-colour tiles among {old} + touching iterations' tiles
+    const int ncand = d + (old >= 0 ? 1 : 0);
+    for (int x = 0; x < ncand; ++x) {
+      int32_t tx = (old >= 0) ? (x == 0 ? old : sig[islot[b + x - 1] / a]) : sig[islot[b + x] / a];
+      for (int y = x + 1; y < ncand; ++y) {
+        int32_t ty = (old >= 0) ? (y == 0 ? old : sig[islot[b + y - 1] / a]) : sig[islot[b + y] / a];
+        if (tx != ty && col[tx] == col[ty]) push_conflict(tx, ty, cbuf, ccnt, cap);
+      }
+    }
+  }
+}
+
+constexpr int MAXD = 8;
+struct TileDescs {
+  int nd;
+  const int32_t* map[MAXD];  // null for direct
+  int arity[MAXD];
+  const int32_t* phi[MAXD];  // projection of the target set (null: none yet)
+};
+__global__ void k_tile(int64_t n, TileDescs D, const int32_t* __restrict__ col, int32_t* __restrict__ sig,
+                       int32_t* __restrict__ nbottom) {
+  GRID_STRIDE(e, n) {
+    int32_t cur = -1;
+    for (int d = 0; d < D.nd; ++d) {
+      const int32_t* p = D.phi[d];
+      if (!p) continue;
+      if (!D.map[d]) {
+        int32_t t = p[e];
+        if (t >= 0 && (cur < 0 || col[t] > col[cur])) cur = t;
+      } else {
+        const int a = D.arity[d];
+        for (int k = 0; k < a; ++k) {
+          int32_t t = p[D.map[d][e * a + k]];
+          if (t >= 0 && (cur < 0 || col[t] > col[cur])) cur = t;
+        }
+      }
+    }
+    if (cur < 0) {
+      cur = 0;
+      atomicAdd(nbottom, 1);
+    }
+    sig[e] = cur;
+  }
+}
+
+// local maps: p-th entry of the sequence sorted by (tile, target)
+__global__ void k_lm_flags(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ slot,
+                           const int32_t* __restrict__ map, int64_t n, int32_t* __restrict__ flag) {
+  GRID_STRIDE(p, n) flag[p] = (p == 0 || tile[p] != tile[p - 1] || map[slot[p]] != map[slot[p - 1]]);
+}
+__global__ void k_lm_emit(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ slot,
+                          const int32_t* __restrict__ map, const int32_t* __restrict__ flag,
+                          const int32_t* __restrict__ pos, int64_t n, int32_t* __restrict__ fp,
+                          uint32_t* __restrict__ utile) {
+  GRID_STRIDE(p, n) if (flag[p]) {
+    fp[pos[p]] = map[slot[p]];
+    utile[pos[p]] = tile[p];
+  }
+}
+__global__ void k_lm_local(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ slot,
+                           const int32_t* __restrict__ pos, const int32_t* __restrict__ fp_ptr, int64_t n,
+                           int32_t* __restrict__ lmap) {
+  GRID_STRIDE(p, n) lmap[slot[p]] = pos[p + 1] - 1 - fp_ptr[tile[p]];
+}
+
+// executor plan of a facet loop: entries (tile, work id, face bit), sorted, OR-reduced per cell
+__global__ void k_plan_facet_keys(const int32_t* __restrict__ map, const int8_t* __restrict__ face, int64_t nslot,
+                                  const int32_t* __restrict__ iperm, uint32_t* __restrict__ wid, uint32_t* __restrict__ slot) {
+  GRID_STRIDE(s, nslot) {
+    wid[s] = (uint32_t)iperm[map[s]];
+    slot[s] = (uint32_t)s;
+  }
+}
+__global__ void k_plan_facet_flags(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid, int64_t n,
+                                   int32_t* __restrict__ flag) {
+  GRID_STRIDE(p, n) flag[p] = (p == 0 || tile[p] != tile[p - 1] || wid[p] != wid[p - 1]);
+}
+__global__ void k_plan_facet_emit(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid,
+                                  const uint32_t* __restrict__ slot, const int8_t* __restrict__ face,
+                                  const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
+                                  int32_t* __restrict__ items, uint32_t* __restrict__ utile) {
+  GRID_STRIDE(p, n) if (flag[p]) {
+    int mask = 0;
+    for (int64_t q = p; q < n && tile[q] == tile[p] && wid[q] == wid[p]; ++q) mask |= 1 << face[slot[q]];
+    items[pos[p]] = (int32_t)((wid[p] << 3) | (uint32_t)mask);
+    utile[pos[p]] = tile[p];
+  }
+}
+__global__ void k_gather_iperm(const int32_t* __restrict__ iperm, const uint32_t* __restrict__ e, int64_t n,
+                               int32_t* __restrict__ out) {
+  GRID_STRIDE(p, n) out[p] = iperm[e[p]];
+}
+
+struct InverseMap {
+  DevBuf<int32_t> off;   // [ntgt + 1]
+  DevBuf<uint32_t> slot; // [nsrc * arity], slots sorted by target (stable)
+};
+
+void build_inverse(const int32_t* d_map, int64_t nslot, int64_t ntgt, InverseMap& inv, cudaStream_t s) {
+  DevBuf<uint32_t> k(nslot), tk(nslot), tv(nslot);
+  inv.slot.alloc(nslot);
+  inv.off.alloc(ntgt + 1);
+  if (nslot) {
+    k_copy_i2u<<<grid_for(nslot), 256, 0, s>>>(d_map, nslot, k.p);
+    k_iota_u<<<grid_for(nslot), 256, 0, s>>>(inv.slot.p, nslot);
+    radix_sort_pairs(k.p, inv.slot.p, nslot, bits_for(std::max<int64_t>(ntgt - 1, 1)), tk.p, tv.p, s);
+  }
+  lower_bound_offsets(k.p, nslot, ntgt, inv.off.p, s);
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+// stable sort of n values by two keys: primary k1 (bits1), secondary k2 (bits2); returns the
+// permutation (positions into the original sequence) and the sorted primary keys.
+void sort_by_two(DevBuf<uint32_t>& k1, int bits1, DevBuf<uint32_t>& k2, int bits2, int64_t n, DevBuf<uint32_t>& order,
+                 cudaStream_t s) {
+  DevBuf<uint32_t> tk(n), tv(n), key(n);
+  order.alloc(n);
+  k_iota_u<<<grid_for(n), 256, 0, s>>>(order.p, n);
+  SLT_CUDA(cudaMemcpyAsync(key.p, k2.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  radix_sort_pairs(key.p, order.p, n, bits2, tk.p, tv.p, s);
+  // gather primary keys in the secondary order, then stable sort by them
+  k_gather_div<<<grid_for(n), 256, 0, s>>>((const int32_t*)k1.p, order.p, n, 1, key.p);
+  radix_sort_pairs(key.p, order.p, n, bits1, tk.p, tv.p, s);
+  SLT_CUDA(cudaMemcpyAsync(k1.p, key.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+struct Ctx {
+  slt_chain c;
+  const slt_options* opt;
+  cudaStream_t s;
+  std::vector<DevBuf<int32_t>> dmaps;  // device copies of maps
+  std::map<int, InverseMap> inverses;
+};
+
+const InverseMap& inverse_of(Ctx& X, int mid) {
+  auto it = X.inverses.find(mid);
+  if (it != X.inverses.end()) return it->second;
+  const MapH& M = X.c->maps[mid];
+  InverseMap& inv = X.inverses[mid];
+  build_inverse(X.dmaps[mid].p, (int64_t)M.values.size(), X.c->set_size[M.to], inv, X.s);
+  return inv;
+}
+
+// adjacency CSR (aoff [m+1], adj) from the seed map and fake edges
+void build_adjacency(Ctx& X, int first, int last, int seed_set, const int32_t* sig0, int32_t m,
+                     const std::vector<std::pair<int32_t, int32_t>>& fake, DevBuf<int32_t>& aoff, DevBuf<int32_t>& adj) {
+  cudaStream_t s = X.s;
+  slt_chain c = X.c;
+  int mid = -1;
+  bool target_kind = false;
+  for (int j = first; j < last && mid < 0; ++j)
+    for (const DescH& d : c->loops[j].descs) {
+      if (d.map < 0) continue;
+      const MapH& M = c->maps[d.map];
+      if (M.to == seed_set) { mid = d.map; target_kind = true; break; }
+      if (M.from == seed_set) { mid = d.map; target_kind = false; break; }
+    }
+  int64_t nmap = 0;
+  DevBuf<int32_t> cntoff;
+  if (mid >= 0) {
+    const MapH& M = c->maps[mid];
+    if (target_kind) {
+      nmap = c->set_size[M.from] * (int64_t)M.arity * M.arity;
+    } else {
+      const InverseMap& inv = inverse_of(X, mid);
+      int64_t nt = c->set_size[M.to];
+      DevBuf<int32_t> cnt(nt);
+      cntoff.alloc(nt + 1);
+      k_pairs_count<<<grid_for(nt), 256, 0, s>>>(inv.off.p, nt, cnt.p);
+      exclusive_scan_i32(cnt.p, cntoff.p, nt, s);
+      int32_t total = 0;
+      SLT_CUDA(cudaMemcpyAsync(&total, cntoff.p + nt, 4, cudaMemcpyDeviceToHost, s));
+      SLT_CUDA(cudaStreamSynchronize(s));
+      nmap = total;
+    }
+  }
+  int64_t n = nmap + 2 * (int64_t)fake.size();
+  DevBuf<uint32_t> pa(std::max<int64_t>(n, 1)), pb(std::max<int64_t>(n, 1));
+  if (mid >= 0 && nmap > 0) {
+    const MapH& M = c->maps[mid];
+    if (target_kind)
+      k_pairs_target<<<grid_for(c->set_size[M.from]), 256, 0, s>>>(X.dmaps[mid].p, c->set_size[M.from], M.arity, sig0,
+                                                                   (uint32_t)m, pa.p, pb.p);
+    else {
+      const InverseMap& inv = inverse_of(X, mid);
+      k_pairs_source<<<grid_for(c->set_size[M.to]), 256, 0, s>>>(inv.off.p, inv.slot.p, c->set_size[M.to], M.arity,
+                                                                 cntoff.p, sig0, (uint32_t)m, pa.p, pb.p);
+    }
+    SLT_CUDA(cudaGetLastError());
+  }
+  if (!fake.empty()) {
+    std::vector<uint32_t> ha, hb;
+    for (auto& e : fake) {
+      ha.push_back(e.first); hb.push_back(e.second);
+      ha.push_back(e.second); hb.push_back(e.first);
+    }
+    SLT_CUDA(cudaMemcpyAsync(pa.p + nmap, ha.data(), ha.size() * 4, cudaMemcpyHostToDevice, s));
+    SLT_CUDA(cudaMemcpyAsync(pb.p + nmap, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+  aoff.alloc(m + 1);
+  if (n == 0) {
+    k_fill<<<grid_for(m + 1), 256, 0, s>>>(aoff.p, m + 1, 0);
+    adj.alloc(1);
+    SLT_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  // sort by (a, b): stable by b, then stable by a
+  int bits = bits_for(m);
+  DevBuf<uint32_t> order;
+  sort_by_two(pa, bits, pb, bits, n, order, s);
+  DevBuf<uint32_t> sb(n);
+  k_gather_div<<<grid_for(n), 256, 0, s>>>((const int32_t*)pb.p, order.p, n, 1, sb.p);
+  DevBuf<int32_t> flag(n), pos(n + 1);
+  k_unique_flags<<<grid_for(n), 256, 0, s>>>(pa.p, sb.p, n, (uint32_t)m, flag.p);
+  exclusive_scan_i32(flag.p, pos.p, n, s);
+  int32_t nu = 0;
+  SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + n, 4, cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  DevBuf<uint32_t> ua(std::max(nu, 1));
+  adj.alloc(std::max(nu, 1));
+  k_compact2<<<grid_for(n), 256, 0, s>>>(pa.p, sb.p, flag.p, pos.p, n, ua.p, adj.p);
+  lower_bound_offsets(ua.p, nu, m, aoff.p, s);
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+void colour_tiles(Ctx& X, int32_t m, bool sequential, const DevBuf<int32_t>& aoff, const DevBuf<int32_t>& adj,
+                  DevBuf<int32_t>& col) {
+  cudaStream_t s = X.s;
+  if (sequential) {
+    DevBuf<uint32_t> tmp(m);
+    k_iota_u<<<grid_for(m), 256, 0, s>>>(tmp.p, m);
+    SLT_CUDA(cudaMemcpyAsync(col.p, tmp.p, m * 4, cudaMemcpyDeviceToDevice, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  DevBuf<uint64_t> prio(m);
+  DevBuf<int32_t> remaining(1);
+  k_priorities<<<grid_for(m), 256, 0, s>>>(m, X.opt->prio_seed, prio.p);
+  k_fill<<<grid_for(m), 256, 0, s>>>(col.p, m, -1);
+  for (int64_t round = 0;; ++round) {
+    if (round > m + 1) fail(SLT_ERR_CUDA, "colouring did not converge");
+    SLT_CUDA(cudaMemsetAsync(remaining.p, 0, 4, s));
+    k_jp_round<<<grid_for(m), 256, 0, s>>>(m, aoff.p, adj.p, prio.p, col.p, remaining.p);
+    SLT_CUDA(cudaGetLastError());
+    int32_t left = 0;
+    SLT_CUDA(cudaMemcpyAsync(&left, remaining.p, 4, cudaMemcpyDeviceToHost, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    if (left == 0) break;
+  }
+}
+
+void export_lists(Ctx& X, const int32_t* sig, int64_t n, int32_t m, DevBuf<int32_t>& ptr, DevBuf<int32_t>& list) {
+  cudaStream_t s = X.s;
+  ptr.alloc(m + 1);
+  list.alloc(std::max<int64_t>(n, 1));
+  DevBuf<uint32_t> k(std::max<int64_t>(n, 1)), v(std::max<int64_t>(n, 1)), tk(std::max<int64_t>(n, 1)),
+      tv(std::max<int64_t>(n, 1));
+  if (n) {
+    k_copy_i2u<<<grid_for(n), 256, 0, s>>>(sig, n, k.p);
+    k_iota_u<<<grid_for(n), 256, 0, s>>>(v.p, n);
+    radix_sort_pairs(k.p, v.p, n, bits_for(std::max(m - 1, 1)), tk.p, tv.p, s);
+    SLT_CUDA(cudaMemcpyAsync(list.p, v.p, n * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  lower_bound_offsets(k.p, n, m, ptr.p, s);
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+void export_local_map(Ctx& X, int mid, const int32_t* sig, int64_t n, int32_t m, LocalMap& L) {
+  cudaStream_t s = X.s;
+  const MapH& M = X.c->maps[mid];
+  const int a = M.arity;
+  const int64_t ns = n * a;
+  const int64_t ntgt = X.c->set_size[M.to];
+  L.fp_ptr.alloc(m + 1);
+  L.lmap.alloc(std::max<int64_t>(ns, 1));
+  if (ns == 0) {
+    k_fill<<<grid_for(m + 1), 256, 0, s>>>(L.fp_ptr.p, m + 1, 0);
+    L.fp.alloc(1);
+    SLT_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  DevBuf<uint32_t> tile(ns), tgt(ns), order, slots(ns);
+  k_iota_u<<<grid_for(ns), 256, 0, s>>>(slots.p, ns);
+  k_gather_div<<<grid_for(ns), 256, 0, s>>>(sig, slots.p, ns, a, tile.p);
+  k_copy_i2u<<<grid_for(ns), 256, 0, s>>>(X.dmaps[mid].p, ns, tgt.p);
+  sort_by_two(tile, bits_for(std::max(m - 1, 1)), tgt, bits_for(std::max<int64_t>(ntgt - 1, 1)), ns, order, s);
+  DevBuf<int32_t> flag(ns), pos(ns + 1);
+  k_lm_flags<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, X.dmaps[mid].p, ns, flag.p);
+  exclusive_scan_i32(flag.p, pos.p, ns, s);
+  int32_t nu = 0;
+  SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + ns, 4, cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  L.fp.alloc(std::max(nu, 1));
+  DevBuf<uint32_t> utile(std::max(nu, 1));
+  k_lm_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, X.dmaps[mid].p, flag.p, pos.p, ns, L.fp.p, utile.p);
+  lower_bound_offsets(utile.p, nu, m, L.fp_ptr.p, s);
+  // lmap[slot] = (inclusive count of uniques up to p) - 1 - fp_ptr[tile]
+  DevBuf<int32_t> incl(ns + 1);
+  SLT_CUDA(cudaMemcpyAsync(incl.p, pos.p + 1, ns * 4, cudaMemcpyDeviceToDevice, s));
+  // pos[p+1] is the inclusive count at p; k_lm_local reads pos[p + 1]
+  k_lm_local<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, pos.p, L.fp_ptr.p, ns, L.lmap.p);
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s) {
+  const int32_t m = sub.m;
+  // tiles grouped by colour (stable: ascending tile id within a colour)
+  {
+    DevBuf<uint32_t> k(m), v(m), tk(m), tv(m);
+    k_copy_i2u<<<grid_for(m), 256, 0, s>>>(sub.colour.p, m, k.p);
+    k_iota_u<<<grid_for(m), 256, 0, s>>>(v.p, m);
+    radix_sort_pairs(k.p, v.p, m, bits_for(std::max(sub.ncolours - 1, 1)), tk.p, tv.p, s);
+    sub.tiles_by_colour.alloc(m);
+    SLT_CUDA(cudaMemcpyAsync(sub.tiles_by_colour.p, v.p, m * 4, cudaMemcpyDeviceToDevice, s));
+    DevBuf<int32_t> cp(sub.ncolours + 1);
+    lower_bound_offsets(k.p, m, sub.ncolours, cp.p, s);
+    sub.colour_ptr = cp.download(s);
+  }
+  DevBuf<int32_t> d_iperm(mesh->nc);
+  d_iperm.upload(mesh->iperm.data(), mesh->nc, s);
+  DevBuf<int32_t> d_f2c(std::max<int64_t>(mesh->nfi * 2, 1)), d_e2c(std::max<int64_t>(mesh->nfe, 1));
+  DevBuf<int8_t> d_f2f(std::max<int64_t>(mesh->nfi * 2, 1)), d_e2f(std::max<int64_t>(mesh->nfe, 1));
+  d_f2c.upload(mesh->f2c.data(), mesh->nfi * 2, s);
+  d_e2c.upload(mesh->e2c.data(), mesh->nfe, s);
+  d_f2f.upload(mesh->f2f.data(), mesh->nfi * 2, s);
+  d_e2f.upload(mesh->e2f.data(), mesh->nfe, s);
+  const int nl = sub.last - sub.first;
+  sub.plan_ptr.resize(nl);
+  sub.plan_items.resize(nl);
+  const int tbits = bits_for(std::max(m - 1, 1)), wbits = bits_for(std::max<int64_t>(mesh->nc - 1, 1));
+  for (int jj = 0; jj < nl; ++jj) {
+    const LoopH& L = sched->loops[sub.first + jj];
+    const int32_t* sig = sub.sigma[jj].p;
+    sub.plan_ptr[jj].alloc(m + 1);
+    if (L.set == 0) {  // cell loop: work ids sorted by (tile, work id)
+      int64_t n = mesh->nc;
+      DevBuf<uint32_t> tile(n), wid(n), order;
+      DevBuf<uint32_t> e(n);
+      k_iota_u<<<grid_for(n), 256, 0, s>>>(e.p, n);
+      k_gather_div<<<grid_for(n), 256, 0, s>>>(sig, e.p, n, 1, tile.p);
+      k_gather_div<<<grid_for(n), 256, 0, s>>>(d_iperm.p, e.p, n, 1, wid.p);
+      sort_by_two(tile, tbits, wid, wbits, n, order, s);
+      sub.plan_items[jj].alloc(n);
+      k_gather_iperm<<<grid_for(n), 256, 0, s>>>(d_iperm.p, order.p, n, sub.plan_items[jj].p);
+      lower_bound_offsets(tile.p, n, m, sub.plan_ptr[jj].p, s);
+    } else {  // facet loop: (work id, face mask) per touched cell, sorted by (tile, work id)
+      const bool interior = L.set == 1;
+      const int a = interior ? 2 : 1;
+      const int64_t nf = interior ? mesh->nfi : mesh->nfe, ns = nf * a;
+      if (ns == 0) {
+        k_fill<<<grid_for(m + 1), 256, 0, s>>>(sub.plan_ptr[jj].p, m + 1, 0);
+        sub.plan_items[jj].alloc(1);
+        continue;
+      }
+      const int32_t* map = interior ? d_f2c.p : d_e2c.p;
+      const int8_t* face = interior ? d_f2f.p : d_e2f.p;
+      DevBuf<uint32_t> wid(ns), slot(ns), tile(ns), order;
+      k_plan_facet_keys<<<grid_for(ns), 256, 0, s>>>(map, face, ns, d_iperm.p, wid.p, slot.p);
+      k_gather_div<<<grid_for(ns), 256, 0, s>>>(sig, slot.p, ns, a, tile.p);
+      sort_by_two(tile, tbits, wid, wbits, ns, order, s);
+      DevBuf<uint32_t> swid(ns);
+      k_gather_div<<<grid_for(ns), 256, 0, s>>>((const int32_t*)wid.p, order.p, ns, 1, swid.p);
+      DevBuf<int32_t> flag(ns), pos(ns + 1);
+      k_plan_facet_flags<<<grid_for(ns), 256, 0, s>>>(tile.p, swid.p, ns, flag.p);
+      exclusive_scan_i32(flag.p, pos.p, ns, s);
+      int32_t nu = 0;
+      SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + ns, 4, cudaMemcpyDeviceToHost, s));
+      SLT_CUDA(cudaStreamSynchronize(s));
+      sub.plan_items[jj].alloc(std::max(nu, 1));
+      DevBuf<uint32_t> utile(std::max(nu, 1));
+      k_plan_facet_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, swid.p, order.p, face, flag.p, pos.p, ns,
+                                                     sub.plan_items[jj].p, utile.p);
+      lower_bound_offsets(utile.p, nu, m, sub.plan_ptr[jj].p, s);
+    }
+    SLT_CUDA(cudaGetLastError());
+    SLT_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out) {
+  Ctx X{c, &opt, s, {}, {}};
+  X.dmaps.resize(c->maps.size());
+  for (size_t k = 0; k < c->maps.size(); ++k) {
+    X.dmaps[k].alloc(std::max<size_t>(c->maps[k].values.size(), 1));
+    X.dmaps[k].upload(c->maps[k].values.data(), c->maps[k].values.size(), s);
+  }
+  std::vector<int> bounds = {0};
+  for (int k = 0; k < opt.nsplit; ++k) bounds.push_back(opt.split[k]);
+  bounds.push_back((int)c->loops.size());
+  const int nsets = (int)c->set_size.size();
+  const int32_t cap = 1 << 22;
+  DevBuf<int2> cbuf(cap);
+  DevBuf<int32_t> ccnt(1), nbottom(1);
+
+  for (size_t sc = 0; sc + 1 < bounds.size(); ++sc) {
+    out->subs.emplace_back();
+    SubSched& sub = out->subs.back();
+    sub.first = bounds[sc];
+    sub.last = bounds[sc + 1];
+    const int nl = sub.last - sub.first;
+    const int seed_set = c->loops[sub.first].set;
+    const int64_t nseed = c->set_size[seed_set];
+    const int32_t m = (int32_t)std::max<int64_t>((nseed + opt.tile_size - 1) / opt.tile_size, 1);
+    sub.m = m;
+    sub.rank.alloc(std::max<int64_t>(nseed, 1));
+    {
+      DevBuf<double> xy;
+      if (opt.renumber) {
+        xy.alloc(std::max<int64_t>(2 * nseed, 1));
+        xy.upload(c->points[seed_set].data(), 2 * nseed, s);
+      }
+      seed_rank(xy.p, nseed, opt.renumber, sub.rank.p, s);
+    }
+    sub.sigma.resize(nl);
+    for (int jj = 0; jj < nl; ++jj) sub.sigma[jj].alloc(std::max<int64_t>(c->set_size[c->loops[sub.first + jj].set], 1));
+    k_div<<<grid_for(nseed), 256, 0, s>>>(sub.rank.p, nseed, opt.tile_size, sub.sigma[0].p);
+    SLT_CUDA(cudaGetLastError());
+    sub.colour.alloc(m);
+    std::vector<DevBuf<int32_t>> phi(nsets);
+    std::vector<bool> has_phi(nsets);
+    std::vector<std::pair<int32_t, int32_t>> fake;
+    bool fell_back = false;
+    for (;;) {
+      DevBuf<int32_t> aoff, adj;
+      build_adjacency(X, sub.first, sub.last, seed_set, sub.sigma[0].p, m, fake, aoff, adj);
+      colour_tiles(X, m, opt.colouring == 1 || fell_back, aoff, adj, sub.colour);
+      for (int k = 0; k < nsets; ++k) has_phi[k] = false;
+      SLT_CUDA(cudaMemsetAsync(ccnt.p, 0, 4, s));
+      SLT_CUDA(cudaMemsetAsync(nbottom.p, 0, 4, s));
+      auto project = [&](int jj) {
+        const LoopH& L = c->loops[sub.first + jj];
+        for (const DescH& d : L.descs) {
+          int S = d.map < 0 ? L.set : c->maps[d.map].to;
+          int64_t n = c->set_size[S];
+          if (!has_phi[S]) {
+            if (phi[S].n < (size_t)std::max<int64_t>(n, 1)) phi[S].alloc(std::max<int64_t>(n, 1));
+            k_fill<<<grid_for(n), 256, 0, s>>>(phi[S].p, n, -1);
+            has_phi[S] = true;
+          }
+          if (n == 0) continue;
+          if (d.map < 0) {
+            k_project_direct<<<grid_for(n), 256, 0, s>>>(n, sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap);
+          } else {
+            const InverseMap& inv = inverse_of(X, d.map);
+            k_project_indirect<<<grid_for(n), 256, 0, s>>>(n, inv.off.p, inv.slot.p, c->maps[d.map].arity,
+                                                          sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap);
+          }
+          SLT_CUDA(cudaGetLastError());
+        }
+      };
+      for (int jj = 1; jj < nl; ++jj) {
+        project(jj - 1);
+        const LoopH& L = c->loops[sub.first + jj];
+        TileDescs D{};
+        D.nd = (int)L.descs.size();
+        if (D.nd > MAXD) fail(SLT_ERR_UNSUPPORTED, "more than 8 descriptors in a loop");
+        for (int d = 0; d < D.nd; ++d) {
+          const DescH& ds = L.descs[d];
+          int S = ds.map < 0 ? L.set : c->maps[ds.map].to;
+          D.map[d] = ds.map < 0 ? nullptr : X.dmaps[ds.map].p;
+          D.arity[d] = ds.map < 0 ? 1 : c->maps[ds.map].arity;
+          D.phi[d] = has_phi[S] ? phi[S].p : nullptr;
+        }
+        int64_t n = c->set_size[L.set];
+        if (n) k_tile<<<grid_for(n), 256, 0, s>>>(n, D, sub.colour.p, sub.sigma[jj].p, nbottom.p);
+        SLT_CUDA(cudaGetLastError());
+      }
+      project(nl - 1);
+      int32_t nconf = 0, nbot = 0;
+      SLT_CUDA(cudaMemcpyAsync(&nconf, ccnt.p, 4, cudaMemcpyDeviceToHost, s));
+      SLT_CUDA(cudaMemcpyAsync(&nbot, nbottom.p, 4, cudaMemcpyDeviceToHost, s));
+      SLT_CUDA(cudaStreamSynchronize(s));
+      sub.unprojected = nbot;
+      if (nconf > cap) fail(SLT_ERR_CONFLICT_CAP, "conflict buffer overflow");
+      if (nconf == 0) break;
+      std::vector<int2> h(nconf);
+      SLT_CUDA(cudaMemcpyAsync(h.data(), cbuf.p, nconf * sizeof(int2), cudaMemcpyDeviceToHost, s));
+      SLT_CUDA(cudaStreamSynchronize(s));
+      std::set<std::pair<int32_t, int32_t>> pairs;
+      for (const int2& p : h) pairs.insert({p.x, p.y});
+      sub.conflicts = (int64_t)pairs.size();
+      std::set<std::pair<int32_t, int32_t>> all(fake.begin(), fake.end());
+      all.insert(pairs.begin(), pairs.end());
+      fake.assign(all.begin(), all.end());
+      ++sub.restarts;
+      if (opt.max_rounds >= 0 && sub.restarts > opt.max_rounds) fell_back = true;
+    }
+    sub.fell_back = fell_back;
+    {
+      std::vector<int32_t> hc = sub.colour.download(s, m);
+      int32_t nc = 0;
+      for (int32_t v : hc) nc = std::max(nc, v + 1);
+      sub.ncolours = nc;
+    }
+    // assign: iteration lists; compute_local_maps
+    sub.list_ptr.resize(nl);
+    sub.list.resize(nl);
+    sub.lmaps.resize(nl);
+    for (int jj = 0; jj < nl; ++jj) {
+      const LoopH& L = c->loops[sub.first + jj];
+      int64_t n = c->set_size[L.set];
+      export_lists(X, sub.sigma[jj].p, n, m, sub.list_ptr[jj], sub.list[jj]);
+      sub.lmaps[jj].resize(L.descs.size());
+      for (size_t d = 0; d < L.descs.size(); ++d)
+        if (L.descs[d].map >= 0) export_local_map(X, L.descs[d].map, sub.sigma[jj].p, n, m, sub.lmaps[jj][d]);
+    }
+    if (c->mesh) build_plan(out, c->mesh, sub, s);
+  }
+}
+
+}  // namespace slt

@@ -1,0 +1,189 @@
+// Internal declarations shared by the translation units of libslt.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "slt.h"
+
+namespace slt {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+struct Error {
+  int code;
+  std::string msg;
+};
+// throw inside the library; every entry point catches and converts to a status
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define SLT_CUDA(x) ::slt::check_cuda((x), #x)
+
+// ---------------------------------------------------------------- device buffer
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { alloc(count); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; n = 0; (void)cudaGetLastError(); fail(SLT_ERR_OOM, "cudaMalloc failed"); }
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void upload(const T* host, size_t count, cudaStream_t s) {
+    if (count) SLT_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s, size_t count = (size_t)-1) const {
+    if (count == (size_t)-1) count = n;
+    std::vector<T> h(count);
+    if (count) SLT_CUDA(cudaMemcpyAsync(h.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    return h;
+  }
+};
+
+// ---------------------------------------------------------------- loop chain (host)
+struct MapH {
+  int32_t from, to, arity;
+  std::vector<int32_t> values;
+};
+struct DescH {
+  int32_t map;
+  char mode;
+};
+struct LoopH {
+  int32_t set;
+  std::vector<DescH> descs;
+  int32_t kernel;  // executor kernel id (elastic chains), -1 otherwise
+};
+
+struct Mesh;
+
+}  // namespace slt
+
+struct slt_chain_s {
+  std::vector<int64_t> set_size;
+  std::vector<slt::MapH> maps;
+  std::vector<slt::LoopH> loops;
+  std::vector<std::vector<double>> points;  // per set, empty when none
+  slt_mesh mesh = nullptr;                  // set when built by slt_mesh_chain
+};
+
+namespace slt {
+
+// executor kernel ids of the elastic chain loops
+enum LoopKind : int32_t {
+  K_VOLB = 0, K_INTB = 1, K_EXTB = 2, K_VOLD = 3, K_INTD = 4, K_HOOKEB = 5, K_UPDV = 6, K_UPDS = 7
+};
+// which field buffers each loop of the seventeen uses is fixed by its position (exec.cu)
+
+// ---------------------------------------------------------------- primitives (sort.cu)
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key; tmp buffers of
+// size n.  keys/vals are replaced by the sorted sequence.
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, uint32_t* tkeys,
+                      uint32_t* tvals, cudaStream_t s);
+// out[i] = sum_{k<i} in[k] for i < n, out[n] = total (out has n + 1 entries)
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+// offs[k] = first position p with sorted[p] >= k, for k = 0..nkeys (offs has nkeys + 1 entries)
+void lower_bound_offsets(const uint32_t* sorted, int64_t n, int64_t nkeys, int32_t* offs, cudaStream_t s);
+int bits_for(int64_t maxval);  // number of bits to represent values in [0, maxval]
+
+// Seed ranks (identity or Hilbert order of points) on the device.
+void seed_rank(const double* d_xy, int64_t n, int renumber, int32_t* d_rank, cudaStream_t s);
+
+// ---------------------------------------------------------------- schedule
+struct LocalMap {
+  DevBuf<int32_t> fp_ptr, fp, lmap;
+};
+struct SubSched {
+  int32_t first = 0, last = 0;
+  int32_t m = 0, ncolours = 0;
+  int64_t restarts = 0, fell_back = 0, conflicts = 0, unprojected = 0;
+  DevBuf<int32_t> rank, colour;
+  std::vector<DevBuf<int32_t>> sigma, list_ptr, list;  // per loop of the sub-chain
+  std::vector<std::vector<LocalMap>> lmaps;            // per loop, per descriptor
+  // executor plan (elastic chains only)
+  std::vector<int32_t> colour_ptr;                     // host, ncolours + 1
+  DevBuf<int32_t> tiles_by_colour;
+  std::vector<DevBuf<int32_t>> plan_ptr, plan_items;   // per loop of the sub-chain
+};
+
+}  // namespace slt
+
+struct slt_schedule_s {
+  std::vector<slt::LoopH> loops;     // copy of the chain's loops
+  std::vector<slt::MapH> maps_meta;  // from, to, arity (values not kept)
+  std::vector<int64_t> set_size;
+  slt_mesh mesh = nullptr;
+  std::vector<slt::SubSched> subs;
+};
+
+namespace slt {
+
+// ---------------------------------------------------------------- elastic mesh
+struct RefElem {
+  int p = 0, Np = 0, Nfp = 0;
+  std::vector<double> nodes;  // [Np][2]
+  std::vector<double> Dr, Ds; // [Np][Np], Dr[i*Np+j] = d phi_j / dr at node i
+  std::vector<double> Minv;   // [Np][Np]
+  std::vector<double> Lift;   // [3][Np][Nfp]
+  std::vector<int> fnode;     // [3][Nfp]
+  std::vector<double> Vinv;   // monomial coefficients of the basis
+  std::vector<int> mono;      // [nmono][2]
+  std::vector<double> eval(double r, double s) const;
+};
+RefElem make_refelem(int p);
+
+}  // namespace slt
+
+struct slt_mesh_s {
+  int64_t nc = 0, ncp = 0;  // cells, padded stride
+  int p = 0, Np = 0, Nfp = 0;
+  int64_t nfi = 0, nfe = 0;
+  slt::RefElem ref;
+  // host topology in the caller's numbering (for the chain)
+  std::vector<int32_t> f2c, e2c;      // [nfi][2], [nfe]
+  std::vector<int8_t> f2f, e2f;       // local face of each side, [nfi][2], [nfe]
+  std::vector<double> centroid;       // [nc][2]
+  std::vector<double> fmid, emid;     // facet midpoints [nfi][2], [nfe][2]
+  std::vector<int32_t> perm, iperm;   // work id -> cell, cell -> work id
+  int64_t src_cell = -1;              // caller numbering
+  // device, work layout (SoA, stride ncp)
+  slt::DevBuf<double> geo, fgeo, mat, src;
+  slt::DevBuf<int32_t> nbr, d_perm, d_iperm;
+  int32_t src_w = -1;
+  // work fields: V[2 Np], S[3 Np], U1[2 Np], U2[2 Np], E[3 Np], S1[3 Np] rows of ncp
+  slt::DevBuf<double> work;
+  slt::DevBuf<double> ricker_buf;   // for host-buffer execution
+  slt::DevBuf<double> io_v, io_s;
+};
+
+namespace slt {
+// exec.cu
+void upload_constants(const RefElem& r);
+void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
+              int64_t nsteps, cudaStream_t s, double* profile = nullptr);
+void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t s);
+void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
+// inspect.cu
+void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out);
+}  // namespace slt

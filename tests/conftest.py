@@ -19,5 +19,7 @@ def lib():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1708_03183_gb300 as slt
     return slt
