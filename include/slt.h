@@ -170,6 +170,21 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
    out [ncell][3][Np]).  Runs the untiled loops of that operator. */
 int slt_apply_operator(slt_mesh mesh, int32_t op, const double* in, double* out, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free ranking
+ * The paper has no counterpart to this entry point: it serves callers who cannot allocate
+ * device memory where they need the seed ordering (a framework that owns every allocation
+ * through its own pool, or code where cudaMalloc would synchronise the device or is not
+ * permitted).  It computes exactly the rank array of slt_inspect's Hilbert partition
+ * (renumber = 1) for n points d_xy [n][2] (device, doubles) into d_rank [n] (device, int32),
+ * asynchronously on `stream`, and allocates nothing: its scratch is one fixed device array of
+ * 17.8 MB (17,826,560 bytes), held by every GPU that loads the library until the process exits.
+ *  - n may not exceed 1,048,576 (SLT_ERR_ARG otherwise, nothing launched).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the array: calls whose GPU work overlaps (different streams or host
+ *    threads without ordering) race and give wrong ranks; order them on one stream. */
+int slt_seed_rank_noalloc(const double* d_xy, int64_t n, int32_t* d_rank, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

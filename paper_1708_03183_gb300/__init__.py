@@ -51,6 +51,7 @@ _SIGS = {
     "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
+    "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -293,6 +294,15 @@ def slt_apply_operator(mesh, op, x, out, stream=None):
     if x.numel() != info["ncell"] * rin * info["Np"] or out.numel() != info["ncell"] * rout * info["Np"]:
         raise ValueError("operator input/output sizes do not match the mesh")
     _check(lib.slt_apply_operator(mesh.ptr, op, _dev(x, "float64"), _dev(out, "float64"), _stream(stream)))
+
+
+def slt_seed_rank_noalloc(xy, rank, stream=None):
+    """Hilbert seed ranks of device points xy [n, 2] (float64) into rank [n] (int32), using only
+    the library's fixed device scratch (no allocation; at most 1,048,576 points)."""
+    n = rank.numel()
+    if xy.numel() != 2 * n:
+        raise ValueError("xy must hold two coordinates per rank entry")
+    _check(lib.slt_seed_rank_noalloc(_dev(xy, "float64"), n, _dev(rank, "int32"), _stream(stream)))
 
 
 def exported_symbols():

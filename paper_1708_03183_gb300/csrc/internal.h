@@ -107,6 +107,16 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t
 void lower_bound_offsets(const uint32_t* sorted, int64_t n, int64_t nkeys, int32_t* offs, cudaStream_t s);
 int bits_for(int64_t maxval);  // number of bits to represent values in [0, maxval]
 
+// The same steps over caller-provided scratch (no allocation, no synchronisation).
+void launch_bbox_init(unsigned long long* box, cudaStream_t s);
+void launch_bbox(const double* xy, int64_t n, unsigned long long* box, cudaStream_t s);
+void launch_hilbert_keys(const double* xy, int64_t n, const unsigned long long* box, uint32_t* keys,
+                         uint32_t* vals, cudaStream_t s);
+void launch_rank_from_order(const uint32_t* order, int64_t n, int32_t* rank, cudaStream_t s);
+int radix_blocks(int64_t n);  // blocks of one radix pass; hist/offs need 256 * blocks (+1) ints
+void radix_sort_pairs_with(uint32_t* keys, uint32_t* vals, int64_t n, int bits, uint32_t* tkeys,
+                           uint32_t* tvals, int32_t* hist, int32_t* offs, cudaStream_t s);
+
 // Seed ranks (identity or Hilbert order of points) on the device.
 void seed_rank(const double* d_xy, int64_t n, int renumber, int32_t* d_rank, cudaStream_t s);
 

@@ -160,6 +160,13 @@ __global__ void k_hilbert_keys(const double* __restrict__ xy, int64_t n, const u
   }
 }
 
+__global__ void k_box_init(unsigned long long* __restrict__ box) {
+  box[0] = ~0ull;
+  box[1] = 0ull;
+  box[2] = ~0ull;
+  box[3] = 0ull;
+}
+
 __global__ void k_rank_from_order(const uint32_t* __restrict__ order, int64_t n, int32_t* __restrict__ rank) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
     rank[order[p]] = (int32_t)p;
@@ -176,6 +183,41 @@ inline int grid_for(int64_t n, int threads = 256) {
 }
 
 }  // namespace
+
+// ---- launch wrappers over caller-provided scratch (used by the allocation-free entry point)
+void launch_bbox_init(unsigned long long* box, cudaStream_t s) {
+  k_box_init<<<1, 1, 0, s>>>(box);
+}
+void launch_bbox(const double* xy, int64_t n, unsigned long long* box, cudaStream_t s) {
+  k_bbox<<<grid_for(n), 256, 0, s>>>(xy, n, box);
+}
+void launch_hilbert_keys(const double* xy, int64_t n, const unsigned long long* box, uint32_t* keys, uint32_t* vals,
+                         cudaStream_t s) {
+  k_hilbert_keys<<<grid_for(n), 256, 0, s>>>(xy, n, box, keys, vals);
+}
+void launch_rank_from_order(const uint32_t* order, int64_t n, int32_t* rank, cudaStream_t s) {
+  k_rank_from_order<<<grid_for(n), 256, 0, s>>>(order, n, rank);
+}
+int radix_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+void radix_sort_pairs_with(uint32_t* keys, uint32_t* vals, int64_t n, int bits, uint32_t* tkeys, uint32_t* tvals,
+                           int32_t* hist, int32_t* offs, cudaStream_t s) {
+  if (n <= 1) return;
+  int nblocks = radix_blocks(n);
+  uint32_t *ik = keys, *iv = vals, *ok = tkeys, *ov = tvals;
+  int passes = (bits + 7) / 8;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_digit_hist<<<nblocks, RS_THREADS, 0, s>>>(ik, n, 8 * ps, hist, nblocks);
+    k_scan_single<<<1, 1024, 0, s>>>(hist, offs, (int64_t)RS_BINS * nblocks);
+    k_digit_scatter<<<nblocks, RS_THREADS, 0, s>>>(ik, iv, n, 8 * ps, offs, nblocks, ok, ov);
+    uint32_t* t;
+    t = ik; ik = ok; ok = t;
+    t = iv; iv = ov; ov = t;
+  }
+  if (ik != keys) {
+    SLT_CUDA(cudaMemcpyAsync(keys, ik, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    SLT_CUDA(cudaMemcpyAsync(vals, iv, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  }
+}
 
 int bits_for(int64_t maxval) {
   int b = 1;
