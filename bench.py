@@ -199,9 +199,9 @@ def workload_name(args):
     sc = getattr(args, "scale", 1)
     nx, ny = c["nx"] // sc, c["ny"] // sc
     return ("%s: %dx%d squares on %gx%g, %d triangles, DG P%d FP64, %s material, Ricker f0=%g, "
-            "sparse-tiled ts=%d, fusion {velocity, stress}" % (
+            "sparse-tiled ts=%d, fusion {velocity, stress}, %s executor" % (
                 args.config, nx, ny, c["Lx"], c["Ly"], 2 * nx * ny, c["p"], c["material"],
-                c["f0"], args.tile_size))
+                c["f0"], args.tile_size, ["dataflow", "colour-phase"][getattr(args, "executor", 0)]))
 
 
 def main():
@@ -212,6 +212,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large")
     ap.add_argument("--tile-size", type=int, default=1024)
+    ap.add_argument("--executor", type=int, default=0, help="0 dataflow (persistent), 1 colour phases")
     ap.add_argument("--no-untiled", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -253,7 +254,7 @@ def main():
     chain = slt.slt_mesh_chain(mesh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,))
+    sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,), executor=args.executor)
     inspect_s = time.perf_counter() - t0
     subs = [slt.slt_schedule_info(sched, k) for k in range(2)]
 
@@ -289,7 +290,8 @@ def main():
     kern_s = prof["chain_ms"] * 1e-3
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
-    traffic = ncu_traffic("k_tiled<2>", args.config)
+    kname = "k_dataflow<%d>" % p if args.executor == 0 else "k_tiled<%d>" % p
+    traffic = ncu_traffic(kname, args.config)
     tiled_bytes = bytes_per_step(Np, nc, True)
 
     out = {"metric": METRIC, "value": value, "unit": "dof-updates/s", "n_gpus": world, "steps": args.steps,
@@ -300,10 +302,11 @@ def main():
                           (20 * Np + 33) * nc * 8 / 1e9),
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "tiles": [s["ntiles"] for s in subs], "colours": [s["ncolours"] for s in subs],
-                      "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s},
+                      "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s,
+                      "executor": ["dataflow", "colour phases"][args.executor]},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP64_PEAK_TFLOPS,
-                        "traffic": traffic, "kernel": "k_tiled<2>",
+                        "traffic": traffic, "kernel": kname,
                         "peak_kind": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal unit counts)",
                         "launch_ms_avg": prof["chain_ms"] / max(prof["chain_launches"], 1),
                         "flops_per_step": flops},

@@ -92,10 +92,12 @@ typedef struct {
   uint64_t prio_seed;    /* colouring priority seed */
   int32_t nsplit;        /* number of split points (0 = one sub-chain) */
   int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
+  int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases */
+  int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
 } slt_options;
 
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
-   no split. */
+   no split, dataflow executor. */
 int slt_options_default(slt_options* opt);
 int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
 int slt_schedule_destroy(slt_schedule sched);
@@ -149,10 +151,16 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
  * nsteps time steps on device fields v, sigma (layout above, updated in place).
  * ricker: device array [nsteps] of the source time function at t_{n+1/2} (NULL: no source).
  * sched = NULL runs the plain untiled chain (one launch per loop, seventeen per step);
- * otherwise the schedule must come from slt_inspect on slt_mesh_chain(mesh) and the tiled
- * executor runs every sub-chain colour by colour, one CTA per tile, each tile executing its
- * slice of every loop in chain order (Algorithm 4, shared-memory mode).  Library-owned work
- * buffers are allocated at the first call for a mesh. */
+ * otherwise the schedule must come from slt_inspect on slt_mesh_chain(mesh) and each tile
+ * (one CTA) executes its slice of every loop of its sub-chain in chain order:
+ *  - executor 1 (colour phases, Algorithm 4 in shared-memory mode): one launch per colour and
+ *    sub-chain, all tiles of a colour in parallel;
+ *  - executor 0 (dataflow, default): one persistent launch for all nsteps; tiles are taken in
+ *    (step, sub-chain, colour) order and each waits only for the tiles it overlaps (lower
+ *    colours of its sub-chain, the previous sub-chain's tiles on its cells) - a linear
+ *    extension of the same order.  Waits are bounded: SLT_ERR_TIMEOUT if one gives up.  This
+ *    mode synchronises the stream before returning.
+ * Work buffers are owned by the mesh. */
 int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                 double dt, int64_t nsteps, void* stream);
 /* slt_execute that also times every kernel launch with CUDA events recorded on `stream` and

@@ -25,7 +25,8 @@ I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 
 class slt_options(ctypes.Structure):
     _fields_ = [("tile_size", I32), ("colouring", I32), ("renumber", I32), ("max_rounds", I32),
-                ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15)]
+                ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15), ("executor", I32),
+                ("wait_spins", I32)]
 
 
 _SIGS = {

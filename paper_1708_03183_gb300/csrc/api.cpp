@@ -151,6 +151,7 @@ int slt_options_default(slt_options* o) {
   o->max_rounds = 16;
   o->prio_seed = 0x5EED;
   o->nsplit = 0;
+  o->executor = 0;
   API_END
 }
 
@@ -164,6 +165,8 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
   REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
+  REQUIRE(opt->executor == 0 || opt->executor == 1, "executor must be 0 or 1");
+  REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
   const int nl = (int)c->loops.size();
   int prev = 0;
   for (int k = 0; k < opt->nsplit; ++k) {
@@ -183,6 +186,8 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   for (const MapH& M : c->maps) s->maps_meta.push_back({M.from, M.to, M.arity, {}});
   s->set_size = c->set_size;
   s->mesh = c->mesh;
+  s->executor = opt->executor;
+  if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
   inspect_chain(c, *opt, as_stream(stream), s.get());
   *out = s.release();
   API_END

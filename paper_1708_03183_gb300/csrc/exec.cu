@@ -48,6 +48,15 @@ __device__ __forceinline__ int fnode(int f, int k) {
   return f == 0 ? nidx(P, k, 0) : (f == 1 ? nidx(P, P - k, k) : nidx(P, 0, P - k));
 }
 
+// Field loads: plain (L1-cached) in the per-loop and colour-phase kernels; L2-only (ld.global.cg)
+// in the persistent dataflow kernel, where other SMs write the fields during the launch and L1
+// is not coherent across SMs.
+template <bool CG>
+__device__ __forceinline__ double ld(const double* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 // buffers of the work layout, each [rows][ncp]
 enum Buf { B_V = 0, B_S = 1, B_U1 = 2, B_U2 = 3, B_E = 4, B_S1 = 5 };
 
@@ -67,7 +76,7 @@ struct Params {
   const int32_t* plan_items[17];
 };
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void vol_div(const Params& a, int64_t w, const double* S, double* U, double rx, double ry,
                                         double sx, double sy) {
   // U = div(S) scaled (rx.. already divided by rho): x row uses (sxx, sxy), y row (sxy, syy)
@@ -79,8 +88,8 @@ __device__ __forceinline__ void vol_div(const Params& a, int64_t w, const double
     double A[Np], B[Np];
 #pragma unroll
     for (int j = 0; j < Np; ++j) {
-      double s1 = S[(int64_t)((comp == 0 ? 0 : 2) * Np + j) * n + w];
-      double s2 = S[(int64_t)((comp == 0 ? 2 : 1) * Np + j) * n + w];
+      double s1 = ld<CG>(&S[(int64_t)((comp == 0 ? 0 : 2) * Np + j) * n + w]);
+      double s2 = ld<CG>(&S[(int64_t)((comp == 0 ? 2 : 1) * Np + j) * n + w]);
       A[j] = fma(ry, s2, rx * s1);
       B[j] = fma(sy, s2, sx * s1);
     }
@@ -98,14 +107,14 @@ __device__ __forceinline__ void vol_div(const Params& a, int64_t w, const double
   }
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void volB(const Params& a, int64_t w, const double* S, double* U) {
   const int64_t n = a.ncp;
   double ir = a.mat[w];
-  vol_div<P>(a, w, S, U, a.geo[w] * ir, a.geo[n + w] * ir, a.geo[2 * n + w] * ir, a.geo[3 * n + w] * ir);
+  vol_div<P, CG>(a, w, S, U, a.geo[w] * ir, a.geo[n + w] * ir, a.geo[2 * n + w] * ir, a.geo[3 * n + w] * ir);
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void volD(const Params& a, int64_t w, const double* V, double* E) {
   constexpr int Np = np_of(P);
   const RefC& R = c_ref[P];
@@ -114,8 +123,8 @@ __device__ __forceinline__ void volD(const Params& a, int64_t w, const double* V
   double vx[Np], vy[Np];
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
-    vx[j] = V[(int64_t)j * n + w];
-    vy[j] = V[(int64_t)(Np + j) * n + w];
+    vx[j] = ld<CG>(&V[(int64_t)j * n + w]);
+    vy[j] = ld<CG>(&V[(int64_t)(Np + j) * n + w]);
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
@@ -135,7 +144,7 @@ __device__ __forceinline__ void volD(const Params& a, int64_t w, const double* V
 }
 
 // S1 = C E at the nodes, then U = div(S1)/rho
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void hookeB(const Params& a, int64_t w, const double* E, double* S1, double* U) {
   constexpr int Np = np_of(P);
   const int64_t n = a.ncp;
@@ -143,15 +152,16 @@ __device__ __forceinline__ void hookeB(const Params& a, int64_t w, const double*
   double l2m = fma(2.0, mu, lam);
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
-    double exx = E[(int64_t)j * n + w], eyy = E[(int64_t)(Np + j) * n + w], g = E[(int64_t)(2 * Np + j) * n + w];
+    double exx = ld<CG>(&E[(int64_t)j * n + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * n + w]),
+           g = ld<CG>(&E[(int64_t)(2 * Np + j) * n + w]);
     S1[(int64_t)j * n + w] = fma(lam, eyy, l2m * exx);
     S1[(int64_t)(Np + j) * n + w] = fma(lam, exx, l2m * eyy);
     S1[(int64_t)(2 * Np + j) * n + w] = mu * g;
   }
-  volB<P>(a, w, S1, U);
+  volB<P, CG>(a, w, S1, U);
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void intB(const Params& a, int64_t w, int mask, const double* S, double* U) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
@@ -173,9 +183,9 @@ __device__ __forceinline__ void intB(const Params& a, int64_t w, int mask, const
     for (int k = 0; k < Nfp; ++k) {
       const int i0 = fnode<P>(f, k);
       const int i1 = fnode<P>(fn, flip ? P - k : k);
-      double dxx = S[(int64_t)i0 * n + w] - S[(int64_t)i1 * n + wn];
-      double dyy = S[(int64_t)(Np + i0) * n + w] - S[(int64_t)(Np + i1) * n + wn];
-      double dxy = S[(int64_t)(2 * Np + i0) * n + w] - S[(int64_t)(2 * Np + i1) * n + wn];
+      double dxx = ld<CG>(&S[(int64_t)i0 * n + w]) - ld<CG>(&S[(int64_t)i1 * n + wn]);
+      double dyy = ld<CG>(&S[(int64_t)(Np + i0) * n + w]) - ld<CG>(&S[(int64_t)(Np + i1) * n + wn]);
+      double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * n + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * n + wn]);
       gx[k] = fma(dxy, ny, dxx * nx);
       gy[k] = fma(dyy, ny, dxy * nx);
     }
@@ -189,12 +199,12 @@ __device__ __forceinline__ void intB(const Params& a, int64_t w, int mask, const
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * n + w] += ax[i];
-    U[(int64_t)(Np + i) * n + w] += ay[i];
+    U[(int64_t)i * n + w] = ld<CG>(&U[(int64_t)i * n + w]) + ax[i];
+    U[(int64_t)(Np + i) * n + w] = ld<CG>(&U[(int64_t)(Np + i) * n + w]) + ay[i];
   }
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void extB(const Params& a, int64_t w, int mask, const double* S, double* U) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
@@ -212,7 +222,8 @@ __device__ __forceinline__ void extB(const Params& a, int64_t w, int mask, const
 #pragma unroll
     for (int k = 0; k < Nfp; ++k) {
       const int i0 = fnode<P>(f, k);
-      double sxx = S[(int64_t)i0 * n + w], syy = S[(int64_t)(Np + i0) * n + w], sxy = S[(int64_t)(2 * Np + i0) * n + w];
+      double sxx = ld<CG>(&S[(int64_t)i0 * n + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * n + w]),
+             sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * n + w]);
       gx[k] = fma(sxy, ny, sxx * nx);
       gy[k] = fma(syy, ny, sxy * nx);
     }
@@ -226,12 +237,12 @@ __device__ __forceinline__ void extB(const Params& a, int64_t w, int mask, const
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * n + w] += ax[i];
-    U[(int64_t)(Np + i) * n + w] += ay[i];
+    U[(int64_t)i * n + w] = ld<CG>(&U[(int64_t)i * n + w]) + ax[i];
+    U[(int64_t)(Np + i) * n + w] = ld<CG>(&U[(int64_t)(Np + i) * n + w]) + ay[i];
   }
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void intD(const Params& a, int64_t w, int mask, const double* V, double* E) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
@@ -252,8 +263,8 @@ __device__ __forceinline__ void intD(const Params& a, int64_t w, int mask, const
     for (int k = 0; k < Nfp; ++k) {
       const int i0 = fnode<P>(f, k);
       const int i1 = fnode<P>(fn, flip ? P - k : k);
-      dx[k] = V[(int64_t)i0 * n + w] - V[(int64_t)i1 * n + wn];
-      dy[k] = V[(int64_t)(Np + i0) * n + w] - V[(int64_t)(Np + i1) * n + wn];
+      dx[k] = ld<CG>(&V[(int64_t)i0 * n + w]) - ld<CG>(&V[(int64_t)i1 * n + wn]);
+      dy[k] = ld<CG>(&V[(int64_t)(Np + i0) * n + w]) - ld<CG>(&V[(int64_t)(Np + i1) * n + wn]);
     }
 #pragma unroll
     for (int i = 0; i < Np; ++i) {
@@ -270,13 +281,13 @@ __device__ __forceinline__ void intD(const Params& a, int64_t w, int mask, const
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    E[(int64_t)i * n + w] += exx[i];
-    E[(int64_t)(Np + i) * n + w] += eyy[i];
-    E[(int64_t)(2 * Np + i) * n + w] += eg[i];
+    E[(int64_t)i * n + w] = ld<CG>(&E[(int64_t)i * n + w]) + exx[i];
+    E[(int64_t)(Np + i) * n + w] = ld<CG>(&E[(int64_t)(Np + i) * n + w]) + eyy[i];
+    E[(int64_t)(2 * Np + i) * n + w] = ld<CG>(&E[(int64_t)(2 * Np + i) * n + w]) + eg[i];
   }
 }
 
-template <int P>
+template <int P, bool CG>
 __device__ __forceinline__ void updV(const Params& a, int64_t w) {
   constexpr int Np = np_of(P);
   const int64_t n = a.ncp;
@@ -286,12 +297,12 @@ __device__ __forceinline__ void updV(const Params& a, int64_t w) {
 #pragma unroll
   for (int q = 0; q < 2 * Np; ++q) {
     int64_t o = (int64_t)q * n + w;
-    V[o] = fma(a.dt, fma(a.c24, U2[o], U1[o]), V[o]);
+    V[o] = fma(a.dt, fma(a.c24, ld<CG>(&U2[o]), ld<CG>(&U1[o])), ld<CG>(&V[o]));
   }
 }
 
-template <int P>
-__device__ __forceinline__ void updS(const Params& a, int64_t w) {
+template <int P, bool CG>
+__device__ __forceinline__ void updS(const Params& a, int64_t w, int64_t step) {
   constexpr int Np = np_of(P);
   const int64_t n = a.ncp;
   double* S = a.buf[B_S];
@@ -300,15 +311,16 @@ __device__ __forceinline__ void updS(const Params& a, int64_t w) {
   double lam = a.mat[n + w], mu = a.mat[2 * n + w];
   double l2m = fma(2.0, mu, lam);
   const bool src = (w == a.src_w) && a.ricker != nullptr;
-  const double gs = src ? a.dt * a.ricker[a.step] : 0.0;
+  const double gs = src ? a.dt * a.ricker[step] : 0.0;
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
-    double exx = E[(int64_t)j * n + w], eyy = E[(int64_t)(Np + j) * n + w], g = E[(int64_t)(2 * Np + j) * n + w];
+    double exx = ld<CG>(&E[(int64_t)j * n + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * n + w]),
+           g = ld<CG>(&E[(int64_t)(2 * Np + j) * n + w]);
     double cxx = fma(lam, eyy, l2m * exx), cyy = fma(lam, exx, l2m * eyy), cxy = mu * g;
     int64_t oxx = (int64_t)j * n + w, oyy = (int64_t)(Np + j) * n + w, oxy = (int64_t)(2 * Np + j) * n + w;
-    double nxx = fma(a.dt, fma(a.c24, cxx, S1[oxx]), S[oxx]);
-    double nyy = fma(a.dt, fma(a.c24, cyy, S1[oyy]), S[oyy]);
-    S[oxy] = fma(a.dt, fma(a.c24, cxy, S1[oxy]), S[oxy]);
+    double nxx = fma(a.dt, fma(a.c24, cxx, ld<CG>(&S1[oxx])), ld<CG>(&S[oxx]));
+    double nyy = fma(a.dt, fma(a.c24, cyy, ld<CG>(&S1[oyy])), ld<CG>(&S[oyy]));
+    S[oxy] = fma(a.dt, fma(a.c24, cxy, ld<CG>(&S1[oxy])), ld<CG>(&S[oxy]));
     if (src) {
       nxx += gs * a.src[j];
       nyy += gs * a.src[j];
@@ -319,30 +331,30 @@ __device__ __forceinline__ void updS(const Params& a, int64_t w) {
 }
 
 // one iteration of loop J; item = work id (cell loops) or (work id << 3) | face mask (facet loops)
-template <int P>
-__device__ __forceinline__ void run_loop(const Params& a, int J, int32_t item) {
+template <int P, bool CG>
+__device__ __forceinline__ void run_loop(const Params& a, int J, int32_t item, int64_t step) {
   double* const* b = a.buf;
   const int64_t w = (J == 1 || J == 2 || J == 4 || J == 6 || J == 7 || J == 10 || J == 12 || J == 13 || J == 15)
                         ? (int64_t)(item >> 3) : (int64_t)item;
   const int mask = item & 7;
   switch (J) {
-    case 0: volB<P>(a, w, b[B_S], b[B_U1]); break;
-    case 1: intB<P>(a, w, mask, b[B_S], b[B_U1]); break;
-    case 2: extB<P>(a, w, mask, b[B_S], b[B_U1]); break;
-    case 3: volD<P>(a, w, b[B_U1], b[B_E]); break;
-    case 4: intD<P>(a, w, mask, b[B_U1], b[B_E]); break;
-    case 5: hookeB<P>(a, w, b[B_E], b[B_S1], b[B_U2]); break;
-    case 6: intB<P>(a, w, mask, b[B_S1], b[B_U2]); break;
-    case 7: extB<P>(a, w, mask, b[B_S1], b[B_U2]); break;
-    case 8: updV<P>(a, w); break;
-    case 9: volD<P>(a, w, b[B_V], b[B_E]); break;
-    case 10: intD<P>(a, w, mask, b[B_V], b[B_E]); break;
-    case 11: hookeB<P>(a, w, b[B_E], b[B_S1], b[B_U1]); break;
-    case 12: intB<P>(a, w, mask, b[B_S1], b[B_U1]); break;
-    case 13: extB<P>(a, w, mask, b[B_S1], b[B_U1]); break;
-    case 14: volD<P>(a, w, b[B_U1], b[B_E]); break;
-    case 15: intD<P>(a, w, mask, b[B_U1], b[B_E]); break;
-    case 16: updS<P>(a, w); break;
+    case 0: volB<P, CG>(a, w, b[B_S], b[B_U1]); break;
+    case 1: intB<P, CG>(a, w, mask, b[B_S], b[B_U1]); break;
+    case 2: extB<P, CG>(a, w, mask, b[B_S], b[B_U1]); break;
+    case 3: volD<P, CG>(a, w, b[B_U1], b[B_E]); break;
+    case 4: intD<P, CG>(a, w, mask, b[B_U1], b[B_E]); break;
+    case 5: hookeB<P, CG>(a, w, b[B_E], b[B_S1], b[B_U2]); break;
+    case 6: intB<P, CG>(a, w, mask, b[B_S1], b[B_U2]); break;
+    case 7: extB<P, CG>(a, w, mask, b[B_S1], b[B_U2]); break;
+    case 8: updV<P, CG>(a, w); break;
+    case 9: volD<P, CG>(a, w, b[B_V], b[B_E]); break;
+    case 10: intD<P, CG>(a, w, mask, b[B_V], b[B_E]); break;
+    case 11: hookeB<P, CG>(a, w, b[B_E], b[B_S1], b[B_U1]); break;
+    case 12: intB<P, CG>(a, w, mask, b[B_S1], b[B_U1]); break;
+    case 13: extB<P, CG>(a, w, mask, b[B_S1], b[B_U1]); break;
+    case 14: volD<P, CG>(a, w, b[B_U1], b[B_E]); break;
+    case 15: intD<P, CG>(a, w, mask, b[B_U1], b[B_E]); break;
+    case 16: updS<P, CG>(a, w, step); break;
     default: break;
   }
 }
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(128) k_loop(Params a) {
     if (!mask) return;
     item = (int32_t)((w << 3) | mask);
   }
-  run_loop<P>(a, J, item);
+  run_loop<P, false>(a, J, item, a.step);
 }
 
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every loop of the
@@ -378,8 +390,87 @@ __global__ void __launch_bounds__(256) k_tiled(Params a, int first, int last, co
   for (int J = first; J < last; ++J) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
     const int32_t* items = a.plan_items[J];
-    for (int32_t i = b + threadIdx.x; i < e; i += blockDim.x) run_loop<P>(a, J, items[i]);
+    for (int32_t i = b + threadIdx.x; i < e; i += blockDim.x) run_loop<P, false>(a, J, items[i], a.step);
     __syncthreads();
+  }
+}
+
+// Persistent dataflow executor: nodes (step, sub-chain, tile) in topological order, taken from an
+// atomic queue; a tile waits only for the tiles it overlaps (lower colours of its sub-chain, the
+// previous sub-chain that touched its cells), then runs its slice of every loop of the sub-chain.
+struct DF {
+  long long total, nps;           // nodes, nodes per step
+  int32_t cum[17];                // global tile id base of each sub-chain (cum[k] + local id)
+  int32_t first[16], last[16];    // loop range of each sub-chain
+  const int32_t* order;           // [sum m] local tile ids, colour-sorted, per sub-chain concatenated
+  const int32_t* dep_ptr;         // [sum m + 1]
+  const int32_t* dep;             // (global tile << 1) | 1 when it is the previous step's tile
+  int32_t* done;                  // [sum m] steps completed by each tile
+  unsigned long long* head;       // next node
+  int32_t* err;                   // set when a wait gave up
+  long long max_spins;
+};
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_dataflow(Params a, DF df) {
+  __shared__ long long s_node;
+  __shared__ int s_stop;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      const long long node = (long long)atomicAdd(df.head, 1ull);
+      if (node >= df.total || ld_acquire(df.err)) {
+        stop = 1;
+      } else {
+        const long long st = node / df.nps;
+        const int r = (int)(node % df.nps);
+        int k = 0;
+        while (r >= df.cum[k + 1]) ++k;
+        const int g = df.cum[k] + df.order[r];
+        for (int q = df.dep_ptr[g]; q < df.dep_ptr[g + 1] && !stop; ++q) {
+          const int e = df.dep[q];
+          const int need = (int)(st + 1 - (e & 1));
+          long long spins = 0;
+          while (ld_acquire(&df.done[e >> 1]) < need) {
+            if (++spins > df.max_spins || ld_acquire(df.err)) {
+              atomicExch(df.err, 1);
+              stop = 1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+      s_node = node;
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const long long node = s_node;
+    const long long st = node / df.nps;
+    const int r = (int)(node % df.nps);
+    int k = 0;
+    while (r >= df.cum[k + 1]) ++k;
+    const int t = df.order[r];
+    for (int J = df.first[k]; J < df.last[k]; ++J) {
+      const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
+      const int32_t* items = a.plan_items[J];
+      for (int32_t i = b + threadIdx.x; i < e; i += blockDim.x) run_loop<P, true>(a, J, items[i], st);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(&df.done[df.cum[k] + t], (int)(st + 1));
+    }
   }
 }
 
@@ -512,7 +603,54 @@ void io_grid(int64_t n, int& g) {
 }
 
 template <int P>
+void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
+  DataflowPlan& D = sched->df;
+  DF df{};
+  df.nps = D.cum.back();
+  df.total = (long long)nsteps * df.nps;
+  for (size_t k = 0; k < D.cum.size(); ++k) df.cum[k] = D.cum[k];
+  for (size_t k = 0; k < sched->subs.size(); ++k) {
+    const SubSched& sub = sched->subs[k];
+    df.first[k] = sub.first;
+    df.last[k] = sub.last;
+    for (int j = sub.first; j < sub.last; ++j) {
+      a.plan_ptr[j] = sub.plan_ptr[j - sub.first].p;
+      a.plan_items[j] = sub.plan_items[j - sub.first].p;
+    }
+  }
+  df.order = D.order.p;
+  df.dep_ptr = D.dep_ptr.p;
+  df.dep = D.dep.p;
+  df.done = D.done.p;
+  df.head = D.head.p;
+  df.err = D.err.p;
+  df.max_spins = sched->wait_spins;
+  if (df.total == 0) return;
+  SLT_CUDA(cudaMemsetAsync(D.done.p, 0, D.done.n * sizeof(int32_t), s));
+  SLT_CUDA(cudaMemsetAsync(D.head.p, 0, sizeof(unsigned long long), s));
+  SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
+  int dev = 0, nsm = 0, per = 0;
+  SLT_CUDA(cudaGetDevice(&dev));
+  SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P>, 256, 0));
+  long long grid = (long long)nsm * std::max(per, 1);
+  if (grid > df.total) grid = df.total;
+  g_rec.begin(0, s);
+  k_dataflow<P><<<(unsigned)grid, 256, 0, s>>>(a, df);
+  g_rec.end(s);
+  SLT_CUDA(cudaGetLastError());
+  int32_t herr = 0;
+  SLT_CUDA(cudaMemcpyAsync(&herr, D.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  if (herr) fail(SLT_ERR_TIMEOUT, "a tile's dependency wait gave up (dataflow executor)");
+}
+
+template <int P>
 void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
+  if (sched && sched->executor == 0) {
+    run_dataflow<P>(sched, a, nsteps, s);
+    return;
+  }
   for (int64_t step = 0; step < nsteps; ++step) {
     a.step = step;
     if (!sched) {

@@ -680,6 +680,89 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     }
     if (c->mesh) build_plan(out, c->mesh, sub, s);
   }
+  if (c->mesh) build_dataflow(out, c->mesh, s);
+}
+
+// Dependencies between tiles for the dataflow executor, from the cells each tile touches in
+// each sub-chain (its plan items): inside a sub-chain, a tile waits for the lower-colour tiles
+// that touch one of its cells; across sub-chains, for the tiles of the previous sub-chain (in
+// chain order, wrapping to the previous step) that touched the same cell.  Every access to a
+// cell is thereby ordered as in the untiled chain.
+void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
+  DataflowPlan& D = sched->df;
+  const int K = (int)sched->subs.size();
+  const int64_t nc = mesh->nc;
+  constexpr int CAP = 16;
+  D.cum.assign(K + 1, 0);
+  for (int k = 0; k < K; ++k) D.cum[k + 1] = D.cum[k] + sched->subs[k].m;
+  const int32_t G = D.cum[K];
+  std::vector<int32_t> order(G), colour(G);
+  std::vector<std::vector<int32_t>> touch(K, std::vector<int32_t>(nc * CAP));
+  std::vector<std::vector<uint8_t>> ntouch(K, std::vector<uint8_t>(nc, 0));
+  for (int k = 0; k < K; ++k) {
+    SubSched& sub = sched->subs[k];
+    std::vector<int32_t> o = sub.tiles_by_colour.download(s, sub.m);
+    std::vector<int32_t> col = sub.colour.download(s, sub.m);
+    for (int32_t i = 0; i < sub.m; ++i) { order[D.cum[k] + i] = o[i]; colour[D.cum[k] + i] = col[i]; }
+    for (int jj = 0; jj < sub.last - sub.first; ++jj) {
+      const bool cell_loop = sched->loops[sub.first + jj].set == 0;
+      std::vector<int32_t> ptr = sub.plan_ptr[jj].download(s, sub.m + 1);
+      std::vector<int32_t> items = sub.plan_items[jj].download(s, std::max(ptr[sub.m], 1));
+      for (int32_t t = 0; t < sub.m; ++t)
+        for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
+          const int64_t w = cell_loop ? items[i] : (items[i] >> 3);
+          int32_t* T = &touch[k][w * CAP];
+          uint8_t& n = ntouch[k][w];
+          bool have = false;
+          for (int q = 0; q < n; ++q) have |= T[q] == t;
+          if (have) continue;
+          if (n == CAP) fail(SLT_ERR_UNSUPPORTED, "a cell is touched by more than 16 tiles of one sub-chain");
+          T[n++] = t;
+        }
+    }
+  }
+  std::vector<std::vector<int32_t>> deps(G);
+  auto push = [&](int32_t g, int32_t e) {
+    if (deps[g].empty() || deps[g].back() != e) deps[g].push_back(e);
+  };
+  std::vector<int> seq;
+  for (int64_t w = 0; w < nc; ++w) {
+    seq.clear();
+    for (int k = 0; k < K; ++k) if (ntouch[k][w]) seq.push_back(k);
+    for (size_t i = 0; i < seq.size(); ++i) {
+      const int k = seq[i];
+      const int prev = i ? seq[i - 1] : seq.back();
+      const int wrap = i ? 0 : 1;
+      const int32_t* T = &touch[k][w * CAP];
+      const int32_t* Tp = &touch[prev][w * CAP];
+      for (int x = 0; x < ntouch[k][w]; ++x) {
+        const int32_t gb = D.cum[k] + T[x];
+        for (int y = 0; y < ntouch[k][w]; ++y) {
+          const int32_t ga = D.cum[k] + T[y];
+          if (colour[ga] < colour[gb]) push(gb, ga << 1);
+        }
+        for (int y = 0; y < ntouch[prev][w]; ++y) push(gb, ((D.cum[prev] + Tp[y]) << 1) | wrap);
+      }
+    }
+  }
+  std::vector<int32_t> ptr(G + 1, 0), flat;
+  for (int32_t g = 0; g < G; ++g) {
+    std::sort(deps[g].begin(), deps[g].end());
+    deps[g].erase(std::unique(deps[g].begin(), deps[g].end()), deps[g].end());
+    ptr[g + 1] = ptr[g] + (int32_t)deps[g].size();
+    flat.insert(flat.end(), deps[g].begin(), deps[g].end());
+  }
+  D.ndeps = (int64_t)flat.size();
+  D.order.alloc(G);
+  D.order.upload(order.data(), G, s);
+  D.dep_ptr.alloc(G + 1);
+  D.dep_ptr.upload(ptr.data(), G + 1, s);
+  D.dep.alloc(std::max<size_t>(flat.size(), 1));
+  D.dep.upload(flat.data(), flat.size(), s);
+  D.done.alloc(G);
+  D.err.alloc(1);
+  D.head.alloc(1);
+  SLT_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace slt

@@ -139,7 +139,22 @@ struct SubSched {
 
 }  // namespace slt
 
+namespace slt {
+// dependencies of the persistent dataflow executor (elastic chains)
+struct DataflowPlan {
+  std::vector<int32_t> cum;          // global tile id base per sub-chain, size nsub + 1
+  DevBuf<int32_t> order;             // colour-sorted local tile ids, per sub-chain concatenated
+  DevBuf<int32_t> dep_ptr, dep;      // CSR over global tiles: (global tile << 1) | previous step
+  DevBuf<int32_t> done, err;
+  DevBuf<unsigned long long> head;
+  int64_t ndeps = 0;
+};
+}  // namespace slt
+
 struct slt_schedule_s {
+  int32_t executor = 0;              // 0 dataflow, 1 colour phases
+  int64_t wait_spins = 1ll << 24;    // bounded dependency wait of the dataflow executor
+  slt::DataflowPlan df;
   std::vector<slt::LoopH> loops;     // copy of the chain's loops
   std::vector<slt::MapH> maps_meta;  // from, to, arity (values not kept)
   std::vector<int64_t> set_size;
@@ -194,6 +209,7 @@ void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const do
               int64_t nsteps, cudaStream_t s, double* profile = nullptr);
 void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t s);
 void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
+void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
 // inspect.cu
 void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out);
 }  // namespace slt

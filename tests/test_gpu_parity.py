@@ -39,26 +39,58 @@ def test_untiled_chain_matches_oracle(lib, name):
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL, (rel_l2(v, vo), rel_l2(s, so))
 
 
+@pytest.mark.parametrize("executor", [0, 1])
 @pytest.mark.parametrize("name,ts", [("tiny", 64), ("tiny", 7), ("tiny", 1), ("tiny", 10 ** 6),
                                      ("small_p2", 64), ("small_p2", 200), ("small_p3", 48), ("small_p4", 40)])
-def test_tiled_chain_matches_oracle(lib, name, ts):
+def test_tiled_chain_matches_oracle(lib, name, ts, executor):
     cfg = workload(name)
     mesh = gpu_mesh(lib, cfg)
     ch = lib.slt_mesh_chain(mesh)
-    sched = lib.slt_inspect(ch, tile_size=ts, split=(9,))
+    sched = lib.slt_inspect(ch, tile_size=ts, split=(9,), executor=executor)
     v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
     vo, so = oracle_run(name)
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL, (rel_l2(v, vo), rel_l2(s, so))
 
 
-@pytest.mark.parametrize("split", [(), (9,), (3, 9, 12), tuple(range(1, 16))])
-def test_fusion_schemes_match_oracle(lib, split):
+@pytest.mark.parametrize("executor", [0, 1])
+@pytest.mark.parametrize("split", [(), (9,), (3, 9, 12), (2, 7, 13), tuple(range(1, 16))])
+def test_fusion_schemes_match_oracle(lib, split, executor):
     cfg = workload("tiny")
     mesh = gpu_mesh(lib, cfg)
-    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=32, split=split)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=32, split=split, executor=executor)
     v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
     vo, so = oracle_run("tiny")
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL
+
+
+@pytest.mark.parametrize("name,ts", [("small_p2", 64), ("small_p3", 16)])
+def test_dataflow_equals_colour_phases_bitwise(lib, name, ts):
+    # each cell's arithmetic is the same whatever order the tiles run in: identical bits
+    cfg = workload(name)
+    mesh = gpu_mesh(lib, cfg)
+    out = []
+    for ex in (0, 1):
+        sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=(9,), executor=ex)
+        out.append(gpu_run(lib, cfg, sched=sched, mesh=mesh))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_dataflow_wait_limit_reports_timeout_and_context_survives(lib):
+    # with a one-poll wait limit the tiles that must wait for a neighbour give up: the kernel
+    # sets its error flag and returns, the call reports SLT_ERR_TIMEOUT, and the next call works
+    import torch
+    cfg = workload("tiny")
+    mesh = gpu_mesh(lib, cfg)
+    impatient = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=16, split=(9,), wait_spins=1)
+    v = torch.tensor(cfg["v0"], device="cuda")
+    s = torch.tensor(cfg["s0"], device="cuda")
+    with pytest.raises(lib.SltError) as e:
+        lib.slt_execute(mesh, impatient, v, s, None, cfg["dt"], 20)
+    assert e.value.code == -4
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=16, split=(9,))
+    vg, sg = gpu_run(lib, cfg, sched=sched, mesh=mesh)
+    vo, so = oracle_run("tiny")
+    assert rel_l2(vg, vo) < TOL and rel_l2(sg, so) < TOL
 
 
 def test_host_buffers_and_no_source(lib):
