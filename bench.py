@@ -42,31 +42,6 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def flops_per_step(Np, Nfp, nc, nfi, nfe):
-    """FP64 flops the executor's kernels perform in one time step (an FMA counts 2).
-
-    Per cell: volB 8Np^2+10Np+4, hookeB 8Np^2+17Np+6 (twice), volD 8Np^2+9Np (three times),
-    updV 8Np, updS 19Np+2; per cell side of an interior facet: intB 4NpNfp+9Nfp+4 and intD
-    4NpNfp+6Np+2Nfp+3 (three loops each); per exterior facet: extB 4NpNfp+6Nfp+3 (three loops);
-    final increments 2Np (intB, extB) and 3Np (intD) per cell and facet loop."""
-    cell = (8 * Np * Np + 10 * Np + 4) + 2 * (8 * Np * Np + 17 * Np + 6) + 3 * (8 * Np * Np + 9 * Np) \
-        + 8 * Np + 19 * Np + 2 + 3 * 2 * Np + 3 * 3 * Np
-    side_b = 4 * Np * Nfp + 9 * Nfp + 4
-    side_d = 4 * Np * Nfp + 6 * Np + 2 * Nfp + 3
-    ext = 4 * Np * Nfp + 6 * Nfp + 3 + 2 * Np
-    return nc * cell + 2 * nfi * 3 * (side_b + side_d) + nfe * 3 * ext
-
-
-def bytes_per_step(Np, nc, tiled):
-    """Algorithmic DRAM bytes of one time step.  Tiled (ideal): the prognostic fields v, sigma
-    read and written once plus per-cell geometry, material and neighbours read once
-    (80 Np + 140 B per cell).  Untiled: every loop streams its operand and result fields and
-    the metadata it needs (808 Np + 808 B per cell, counted loop by loop in the design doc)."""
-    if tiled:
-        return nc * (80 * Np + 140)
-    return nc * (808 * Np + 808)
-
-
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("exec.cu", "internal.h"):
@@ -211,8 +186,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large")
-    ap.add_argument("--tile-size", type=int, default=1024)
+    ap.add_argument("--tile-size", type=int, default=512)
     ap.add_argument("--executor", type=int, default=0, help="0 dataflow (persistent), 1 colour phases")
+    ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128 or 256)")
     ap.add_argument("--no-untiled", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -254,7 +230,8 @@ def main():
     chain = slt.slt_mesh_chain(mesh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,), executor=args.executor)
+    sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,), executor=args.executor,
+                            block_threads=args.block)
     inspect_s = time.perf_counter() - t0
     subs = [slt.slt_schedule_info(sched, k) for k in range(2)]
 
@@ -286,13 +263,14 @@ def main():
 
     ms, prof, clocks = timed(sched, args.steps, args.warmup)
     value = units_per_step * args.steps * world / (ms * 1e-3)
-    flops = flops_per_step(Np, Nfp, nc, info["nfi"], info["nfe"])
+    cost = slt.slt_mesh_cost(mesh)   # the library's own count of the work its kernels do
+    flops = cost["flops_per_step"]
     kern_s = prof["chain_ms"] * 1e-3
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
-    kname = "k_dataflow<%d>" % p if args.executor == 0 else "k_tiled<%d>" % p
+    kname = ("k_dataflow<%d,%d>" if args.executor == 0 else "k_tiled<%d,%d>") % (p, args.block)
     traffic = ncu_traffic(kname, args.config)
-    tiled_bytes = bytes_per_step(Np, nc, True)
+    tiled_bytes = cost["tiled_bytes_per_step"]
 
     out = {"metric": METRIC, "value": value, "unit": "dof-updates/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -303,7 +281,7 @@ def main():
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "tiles": [s["ntiles"] for s in subs], "colours": [s["ncolours"] for s in subs],
                       "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s,
-                      "executor": ["dataflow", "colour phases"][args.executor]},
+                      "executor": ["dataflow", "colour phases"][args.executor], "block_threads": args.block},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP64_PEAK_TFLOPS,
                         "traffic": traffic, "kernel": kname,
@@ -319,7 +297,7 @@ def main():
     if not args.no_untiled:
         K = max(args.steps // 4, 10)
         ums, uprof, uclk = timed(None, K, args.warmup)
-        ub = bytes_per_step(Np, nc, False)
+        ub = cost["untiled_bytes_per_step"]
         uk = uprof["chain_ms"] * 1e-3
         out["untiled"] = {"value": units_per_step * K * world / (ums * 1e-3), "ms_per_step": ums / K, "steps": K,
                           "roofline_frac_fp64": flops * K / uk / 1e12 / FP64_PEAK_TFLOPS,

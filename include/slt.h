@@ -94,6 +94,7 @@ typedef struct {
   int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
   int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
+  int32_t block_threads; /* threads per tile CTA: 128 or 256 (0 = 256) */
 } slt_options;
 
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
@@ -139,6 +140,14 @@ int slt_mesh_destroy(slt_mesh mesh);
 /* info[0..7] = ncell, degree, Np, interior facets, exterior facets, source cell (-1: none),
    number of chain loops (17), velocity/stress split loop (9). */
 int slt_mesh_info(slt_mesh mesh, int64_t info[8]);
+/* Work of one time step on this mesh, as the executor performs it: cost[0] = FP64 flops
+   (an FMA counts 2; structural zeros of the reference differentiation matrices are skipped;
+   interior facets counted from both sides, as the per-cell pulls compute them), cost[1] =
+   algorithmic DRAM bytes of the tiled chain when every tile's data stays on chip (v and sigma
+   read and written once, geometry and material read once: (80 Np + 140) B per cell), cost[2]
+   = algorithmic DRAM bytes of the untiled chain, every loop streaming its operands and results
+   ((808 Np + 808) B per cell), cost[3] = nonzeros of Dr plus Ds. */
+int slt_mesh_cost(slt_mesh mesh, double cost[4]);
 /* The seventeen-loop chain of one time step over the sets cells (0), interior facets (1),
    exterior facets (2), with maps facet->cell (arity 2, map 0) and exterior facet->cell
    (arity 1, map 1); points: cell centroids ((x0 + x1) + x2) / 3 on set 0, facet midpoints

@@ -26,7 +26,7 @@ I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 class slt_options(ctypes.Structure):
     _fields_ = [("tile_size", I32), ("colouring", I32), ("renumber", I32), ("max_rounds", I32),
                 ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15), ("executor", I32),
-                ("wait_spins", I32)]
+                ("wait_spins", I32), ("block_threads", I32)]
 
 
 _SIGS = {
@@ -48,6 +48,7 @@ _SIGS = {
     "slt_mesh_destroy": (ctypes.c_int, [P]),
     "slt_mesh_info": (ctypes.c_int, [P, P]),
     "slt_mesh_chain": (ctypes.c_int, [P, P]),
+    "slt_mesh_cost": (ctypes.c_int, [P, P]),
     "slt_execute": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
@@ -227,6 +228,13 @@ def slt_mesh_info(mesh):
     _check(lib.slt_mesh_info(mesh.ptr, ctypes.c_void_p(info.ctypes.data)))
     keys = ["ncell", "degree", "Np", "nfi", "nfe", "src_cell", "nloops", "split"]
     return dict(zip(keys, (int(x) for x in info)))
+
+
+def slt_mesh_cost(mesh):
+    c = np.zeros(4, dtype=np.float64)
+    _check(lib.slt_mesh_cost(mesh.ptr, ctypes.c_void_p(c.ctypes.data)))
+    return dict(flops_per_step=float(c[0]), tiled_bytes_per_step=float(c[1]), untiled_bytes_per_step=float(c[2]),
+                nnz_dr_ds=int(c[3]))
 
 
 def slt_mesh_chain(mesh):

@@ -40,8 +40,20 @@ def build(verbose=False, force=False):
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
+    # build-time generator: nonzero pattern of the reference differentiation matrices
+    gen = os.path.join(OUT, "refgen")
+    r = subprocess.run([nvcc, "-x", "c++", "-std=c++17", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                        os.path.join(CSRC, "refgen.cpp"), os.path.join(CSRC, "refelem.cpp"), "-o", gen],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("refgen build failed:\n%s%s" % (r.stdout, r.stderr))
+    r = subprocess.run([gen], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("refgen failed:\n%s" % r.stderr)
+    with open(os.path.join(OUT, "refmask.h"), "w") as f:
+        f.write(r.stdout)
     common = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-              "-I", CSRC] + ARCH
+              "-I", CSRC, "-I", OUT] + ARCH
 
     def compile_one(src):
         obj = os.path.join(OUT, src + ".o")

@@ -167,6 +167,8 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
   REQUIRE(opt->executor == 0 || opt->executor == 1, "executor must be 0 or 1");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
+  REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256,
+          "block_threads must be 0, 128 or 256");
   const int nl = (int)c->loops.size();
   int prev = 0;
   for (int k = 0; k < opt->nsplit; ++k) {
@@ -188,6 +190,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   s->mesh = c->mesh;
   s->executor = opt->executor;
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
+  if (opt->block_threads) s->block = opt->block_threads;
   inspect_chain(c, *opt, as_stream(stream), s.get());
   *out = s.release();
   API_END
@@ -326,6 +329,12 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
   for (size_t k = 0; k < m->e2c.size(); ++k) midpoint(m->e2c[k], m->e2f[k], m->emid);
   m->nfi = (int64_t)m->f2c.size() / 2;
   m->nfe = (int64_t)m->e2c.size();
+  for (int64_t c = 0; c < nc; ++c) {
+    bool in = false, ex = false;
+    for (int f = 0; f < 3; ++f) (nbr_c[c][f] >= 0 ? in : ex) = true;
+    m->cells_int += in;
+    m->cells_ext += ex;
+  }
   // geometry (caller numbering)
   std::vector<double> rx(nc), ry(nc), sx(nc), sy(nc), adet(nc), fg(9 * nc);
   m->centroid.resize(2 * nc);
@@ -425,6 +434,29 @@ int slt_mesh_info(slt_mesh m, int64_t info[8]) {
   info[5] = m->src_cell;
   info[6] = 17;
   info[7] = 9;
+  API_END
+}
+
+int slt_mesh_cost(slt_mesh m, double cost[4]) {
+  API_BEGIN
+  REQUIRE(m && cost, "null argument");
+  const double Np = m->Np, Nfp = m->Nfp;
+  double mx = 0.0;
+  for (double x : m->ref.Dr) mx = std::fmax(mx, std::fabs(x));
+  for (double x : m->ref.Ds) mx = std::fmax(mx, std::fabs(x));
+  double nnz = 0.0;
+  for (double x : m->ref.Dr) nnz += std::fabs(x) > 1e-12 * mx;
+  for (double x : m->ref.Ds) nnz += std::fabs(x) > 1e-12 * mx;
+  // FP64 flops of the kernels in exec.cu (an FMA counts 2), structural zeros skipped
+  const double volB = 12 * Np + 4 * nnz + 4, volD = 13 * Np + 4 * nnz, hookeB = 2 + 7 * Np + volB;
+  const double cell = volB + 2 * hookeB + 3 * volD + 8 * Np + 19 * Np + 2;
+  const double side = (4 + 9 * Nfp + 4 * Np * Nfp) + (3 + 2 * Nfp + Np * (4 * Nfp + 6));
+  const double ext = 3 + 6 * Nfp + 4 * Np * Nfp;
+  cost[0] = m->nc * cell + 2.0 * m->nfi * 3 * side + m->cells_int * 15 * Np + m->nfe * 3 * ext +
+            m->cells_ext * 6 * Np;
+  cost[1] = m->nc * (80 * Np + 140);
+  cost[2] = m->nc * (808 * Np + 808);
+  cost[3] = nnz;
   API_END
 }
 

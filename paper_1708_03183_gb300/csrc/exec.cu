@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "refmask.h"  // generated: dr_nz(p, i), ds_nz(p, i) nonzero bits of row i
 
 namespace slt {
 
@@ -95,12 +96,11 @@ __device__ __forceinline__ void vol_div(const Params& a, int64_t w, const double
     }
 #pragma unroll
     for (int i = 0; i < Np; ++i) {
-      double acc = R.Dr[i * MAXNP] * A[0];
-      acc = fma(R.Ds[i * MAXNP], B[0], acc);
+      double acc = 0.0;
 #pragma unroll
-      for (int j = 1; j < Np; ++j) {
-        acc = fma(R.Dr[i * MAXNP + j], A[j], acc);
-        acc = fma(R.Ds[i * MAXNP + j], B[j], acc);
+      for (int j = 0; j < Np; ++j) {
+        if ((dr_nz(P, i) >> j) & 1u) acc = fma(R.Dr[i * MAXNP + j], A[j], acc);
+        if ((ds_nz(P, i) >> j) & 1u) acc = fma(R.Ds[i * MAXNP + j], B[j], acc);
       }
       U[(int64_t)(comp * Np + i) * n + w] = acc;
     }
@@ -128,14 +128,17 @@ __device__ __forceinline__ void volD(const Params& a, int64_t w, const double* V
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    double drx = R.Dr[i * MAXNP] * vx[0], dsx = R.Ds[i * MAXNP] * vx[0];
-    double dry = R.Dr[i * MAXNP] * vy[0], dsy = R.Ds[i * MAXNP] * vy[0];
+    double drx = 0.0, dsx = 0.0, dry = 0.0, dsy = 0.0;
 #pragma unroll
-    for (int j = 1; j < Np; ++j) {
-      drx = fma(R.Dr[i * MAXNP + j], vx[j], drx);
-      dsx = fma(R.Ds[i * MAXNP + j], vx[j], dsx);
-      dry = fma(R.Dr[i * MAXNP + j], vy[j], dry);
-      dsy = fma(R.Ds[i * MAXNP + j], vy[j], dsy);
+    for (int j = 0; j < Np; ++j) {
+      if ((dr_nz(P, i) >> j) & 1u) {
+        drx = fma(R.Dr[i * MAXNP + j], vx[j], drx);
+        dry = fma(R.Dr[i * MAXNP + j], vy[j], dry);
+      }
+      if ((ds_nz(P, i) >> j) & 1u) {
+        dsx = fma(R.Ds[i * MAXNP + j], vx[j], dsx);
+        dsy = fma(R.Ds[i * MAXNP + j], vy[j], dsy);
+      }
     }
     E[(int64_t)i * n + w] = fma(sx, dsx, rx * drx);
     E[(int64_t)(Np + i) * n + w] = fma(sy, dsy, ry * dry);
@@ -382,15 +385,23 @@ __global__ void __launch_bounds__(128) k_loop(Params a) {
   run_loop<P, false>(a, J, item, a.step);
 }
 
+// No register cap: forcing 24 warps per SM (80 registers at p = 2) made the tiled kernels slower
+// (their loads are latency bound and more resident tiles overflow L2); one CTA is the minimum.
+template <int P, int BS>
+constexpr int tile_min_blocks() {
+  return 1;
+}
+
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every loop of the
 // sub-chain [first, last) in order, loops separated by a CTA barrier.
-template <int P>
-__global__ void __launch_bounds__(256) k_tiled(Params a, int first, int last, const int32_t* __restrict__ tiles) {
+template <int P, int BS>
+__global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_tiled(Params a, int first, int last,
+                                                                       const int32_t* __restrict__ tiles) {
   const int t = tiles[blockIdx.x];
   for (int J = first; J < last; ++J) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
     const int32_t* items = a.plan_items[J];
-    for (int32_t i = b + threadIdx.x; i < e; i += blockDim.x) run_loop<P, false>(a, J, items[i], a.step);
+    for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, false>(a, J, items[i], a.step);
     __syncthreads();
   }
 }
@@ -420,8 +431,8 @@ __device__ __forceinline__ void st_release(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_dataflow(Params a, DF df) {
+template <int P, int BS>
+__global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Params a, DF df) {
   __shared__ long long s_node;
   __shared__ int s_stop;
   for (;;) {
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(256) k_dataflow(Params a, DF df) {
     for (int J = df.first[k]; J < df.last[k]; ++J) {
       const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
       const int32_t* items = a.plan_items[J];
-      for (int32_t i = b + threadIdx.x; i < e; i += blockDim.x) run_loop<P, true>(a, J, items[i], st);
+      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, true>(a, J, items[i], st);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -504,7 +515,8 @@ void launch_untiled_range(const Params& a, int first, int last, cudaStream_t s) 
 }
 
 template <int P>
-void launch_tiled_colour(const Params& a, int first, int last, const int32_t* tiles, int ntiles, cudaStream_t s);
+void launch_tiled_colour(const Params& a, int first, int last, const int32_t* tiles, int ntiles, int bs,
+                         cudaStream_t s);
 
 // caller layout [cell][comp][Np] <-> work layout [comp*Np + node][ncp] in work order
 __global__ void k_to_work(const double* __restrict__ in, int rows, const int32_t* __restrict__ perm, int64_t nc,
@@ -589,10 +601,12 @@ void launch_loop(const Params& a, cudaStream_t s) {
 }
 
 template <int P>
-void launch_tiled_colour(const Params& a, int first, int last, const int32_t* tiles, int ntiles, cudaStream_t s) {
+void launch_tiled_colour(const Params& a, int first, int last, const int32_t* tiles, int ntiles, int bs,
+                         cudaStream_t s) {
   if (ntiles <= 0) return;
   g_rec.begin(0, s);
-  k_tiled<P><<<ntiles, 256, 0, s>>>(a, first, last, tiles);
+  if (bs == 128) k_tiled<P, 128><<<ntiles, 128, 0, s>>>(a, first, last, tiles);
+  else k_tiled<P, 256><<<ntiles, 256, 0, s>>>(a, first, last, tiles);
   g_rec.end(s);
   SLT_CUDA(cudaGetLastError());
 }
@@ -632,11 +646,14 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P>, 256, 0));
+  const int bs = sched->block;
+  if (bs == 128) SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 128>, 128, 0));
+  else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 256>, 256, 0));
   long long grid = (long long)nsm * std::max(per, 1);
   if (grid > df.total) grid = df.total;
   g_rec.begin(0, s);
-  k_dataflow<P><<<(unsigned)grid, 256, 0, s>>>(a, df);
+  if (bs == 128) k_dataflow<P, 128><<<(unsigned)grid, 128, 0, s>>>(a, df);
+  else k_dataflow<P, 256><<<(unsigned)grid, 256, 0, s>>>(a, df);
   g_rec.end(s);
   SLT_CUDA(cudaGetLastError());
   int32_t herr = 0;
@@ -664,7 +681,7 @@ void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStr
       }
       for (int c = 0; c < sub.ncolours; ++c)
         launch_tiled_colour<P>(a, sub.first, sub.last, sub.tiles_by_colour.p + sub.colour_ptr[c],
-                               sub.colour_ptr[c + 1] - sub.colour_ptr[c], s);
+                               sub.colour_ptr[c + 1] - sub.colour_ptr[c], sched->block, s);
     }
   }
 }

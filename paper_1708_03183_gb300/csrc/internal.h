@@ -153,6 +153,7 @@ struct DataflowPlan {
 
 struct slt_schedule_s {
   int32_t executor = 0;              // 0 dataflow, 1 colour phases
+  int32_t block = 256;               // threads per tile CTA (128 or 256)
   int64_t wait_spins = 1ll << 24;    // bounded dependency wait of the dataflow executor
   slt::DataflowPlan df;
   std::vector<slt::LoopH> loops;     // copy of the chain's loops
@@ -192,6 +193,7 @@ struct slt_mesh_s {
   std::vector<double> fmid, emid;     // facet midpoints [nfi][2], [nfe][2]
   std::vector<int32_t> perm, iperm;   // work id -> cell, cell -> work id
   int64_t src_cell = -1;              // caller numbering
+  int64_t cells_int = 0, cells_ext = 0;  // cells with an interior / exterior face
   // device, work layout (SoA, stride ncp)
   slt::DevBuf<double> geo, fgeo, mat, src;
   slt::DevBuf<int32_t> nbr, d_perm, d_iperm;
