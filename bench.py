@@ -168,6 +168,45 @@ def run_reference(args, rank):
     print(json.dumps(line))
 
 
+def adjoint_timing(slt, synth, args, barrier):
+    """Forward (slt_record) and gradient (slt_adjoint) time on the adjoint workload's mesh: 448x224
+    squares (200k cells, P2, layered +-5 % per cell), one shot of the top row of the 8x8 source
+    grid, 50 receivers along the top edge, checkpoints every 50 steps, `--adjoint-steps` steps.
+    Both record the receivers after every step, so their forward steps run as the untiled
+    chain (one launch per loop): the persistent tiled executor needs many steps per launch."""
+    import numpy as np
+    import torch
+    n = args.adjoint_steps
+    cfg = synth.build_config("adjoint", nsteps=n)
+    m = cfg["mesh"]
+    nc = m["cell2vert"].shape[0]
+    shot = np.array([(0 + 0.5) * 300.0 / 8, (7 + 0.5) * 150.0 / 8])
+    rec = np.stack([(np.arange(50) + 0.5) * 6.0, np.full(50, 149.0)], 1)
+    base = synth.layered(m)
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], *base, shot)
+    sched = None
+    r = slt.slt_receivers_create(mesh, rec)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    data = torch.zeros((n, 50, 2), dtype=torch.float64, device="cuda")
+    slt.slt_record(mesh, sched, r, rk, cfg["dt"], n, data)          # synthetic data, unperturbed model
+    slt.slt_mesh_set_material(mesh, cfg["rho"], cfg["lam"], cfg["mu"])  # perturbed model
+    tr = torch.zeros_like(data)
+    g = torch.zeros((3, nc), dtype=torch.float64, device="cuda")
+    barrier()
+    t0 = time.perf_counter()
+    slt.slt_record(mesh, sched, r, rk, cfg["dt"], n, tr)
+    barrier()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J = slt.slt_adjoint(mesh, sched, r, rk, cfg["dt"], n, data, 50, g)
+    barrier()
+    t_adj = time.perf_counter() - t0
+    return {"workload": "448x224 squares (%d cells), P2, 1 shot, 50 receivers, %d steps, checkpoints every 50" % (nc, n),
+            "forward_ms_per_step": 1e3 * t_fwd / n, "gradient_ms_per_step": 1e3 * t_adj / n,
+            "adjoint_over_forward": t_adj / t_fwd, "misfit": J,
+            "note": "gradient = forward with checkpoints + segment recompute + reverse sweep"}
+
+
 def workload_name(args):
     import synth
     c = synth.CONFIGS[args.config]
@@ -193,6 +232,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--scale", type=int, default=1, help="divide nx, ny of the workload (small profiling cases)")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -324,6 +365,9 @@ def main():
     out["e2e"] = {"value": units_per_step * args.e2e_steps * world / e2e_s, "unit": "dof-updates/s",
                   "h2d_bytes_per_step": 5 * Np * nc * 8 + 8, "d2h_bytes_per_step": 5 * Np * nc * 8,
                   "steps": args.e2e_steps}
+
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint_timing(slt, synth, args, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, d = oracle_sample_rate(args.config, 10)

@@ -40,6 +40,7 @@ typedef enum {
 typedef struct slt_chain_s* slt_chain;       /* loop chain description (host) */
 typedef struct slt_schedule_s* slt_schedule; /* inspector output (device resident) */
 typedef struct slt_mesh_s* slt_mesh;         /* DG elastic mesh (device resident) */
+typedef struct slt_receivers_s* slt_receivers; /* point receivers on a mesh */
 
 const char* slt_last_error(void);
 /* Library version and the compute capability it was built for (e.g. 103). */
@@ -186,6 +187,34 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
    in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
    out [ncell][3][Np]).  Runs the untiled loops of that operator. */
 int slt_apply_operator(slt_mesh mesh, int32_t op, const double* in, double* out, void* stream);
+
+/* ------------------------------------------------------------------ misfit and gradient
+ * The spec extension of the paper's forward chain: the gradient of a seismogram misfit
+ * with respect to per-cell rho, lambda, mu by the discrete adjoint of the time step.
+ *
+ * Replace the material (host arrays, caller numbering; mu > 0, lambda + mu > 0, rho > 0) or
+ * the point source (NULL: none) of a mesh without rebuilding it; both synchronise `stream`. */
+int slt_mesh_set_material(slt_mesh mesh, const double* rho, const double* lam, const double* mu, void* stream);
+int slt_mesh_set_source(slt_mesh mesh, const double* src_xy, void* stream);
+/* nrec point receivers at host positions xy [nrec][2] (each in some cell: the smallest cell id
+   containing it); the velocity there is the DG field evaluated at the point. */
+int slt_receivers_create(slt_mesh mesh, int32_t nrec, const double* host_xy, slt_receivers* out);
+int slt_receivers_destroy(slt_receivers rec);
+/* Run nsteps from rest (v = sigma = 0) and record traces [nsteps][nrec][2] (device) =
+   velocity at every receiver at t_{n+1/2}.  sched as in slt_execute (NULL = untiled); the
+   steps are executed one call at a time, so with the dataflow executor each step is one
+   persistent launch (no overlap between steps) and the untiled chain is usually faster. */
+int slt_record(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
+               int64_t nsteps, double* traces, void* stream);
+/* Misfit J = 1/2 dt sum_n sum_r |trace - data|^2 (data: device [nsteps][nrec][2]) of a run
+   from rest, written to *misfit (host), and its gradient grad (device [3][ncell], caller
+   numbering: d/drho, d/dlambda, d/dmu) by the discrete adjoint: the forward run keeps (v, sigma)
+   every checkpoint_every steps (device memory: nsteps / k + k states), each segment is
+   recomputed forward (with sched's executor) and swept backwards in time.  Synchronises.
+   Uses the mesh's current material and source. */
+int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
+                int64_t nsteps, const double* data, int32_t checkpoint_every, double* grad, double* misfit,
+                void* stream);
 
 /* ------------------------------------------------------------------ allocation-free ranking
  * The paper has no counterpart to this entry point: it serves callers who cannot allocate

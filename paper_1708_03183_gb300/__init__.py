@@ -54,6 +54,12 @@ _SIGS = {
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
+    "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
+    "slt_mesh_set_source": (ctypes.c_int, [P, P, P]),
+    "slt_receivers_create": (ctypes.c_int, [P, I32, P, P]),
+    "slt_receivers_destroy": (ctypes.c_int, [P]),
+    "slt_record": (ctypes.c_int, [P, P, P, P, F64, I64, P, P]),
+    "slt_adjoint": (ctypes.c_int, [P, P, P, P, F64, I64, P, I32, P, P, P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -126,6 +132,10 @@ class Schedule(_Handle):
 
 class Mesh(_Handle):
     _destroy = "slt_mesh_destroy"
+
+
+class Receivers(_Handle):
+    _destroy = "slt_receivers_destroy"
 
 
 # ------------------------------------------------------------------ loop chain
@@ -312,6 +322,56 @@ def slt_seed_rank_noalloc(xy, rank, stream=None):
     if xy.numel() != 2 * n:
         raise ValueError("xy must hold two coordinates per rank entry")
     _check(lib.slt_seed_rank_noalloc(_dev(xy, "float64"), n, _dev(rank, "int32"), _stream(stream)))
+
+
+def slt_mesh_set_material(mesh, rho, lam, mu, stream=None):
+    r, rp = _host(rho, np.float64)
+    l, lp = _host(lam, np.float64)
+    m, mp = _host(mu, np.float64)
+    n = slt_mesh_info(mesh)["ncell"]
+    if r.size != n or l.size != n or m.size != n:
+        raise ValueError("material arrays need one value per cell")
+    _check(lib.slt_mesh_set_material(mesh.ptr, rp, lp, mp, _stream(stream)))
+
+
+def slt_mesh_set_source(mesh, src_xy, stream=None):
+    sp = None
+    if src_xy is not None:
+        s_, sp = _host(src_xy, np.float64)
+    _check(lib.slt_mesh_set_source(mesh.ptr, sp, _stream(stream)))
+
+
+def slt_receivers_create(mesh, xy):
+    a, ap = _host(np.asarray(xy).reshape(-1, 2), np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.slt_receivers_create(mesh.ptr, a.shape[0], ap, ctypes.byref(h)))
+    rec = Receivers(h)
+    rec.n = a.shape[0]
+    rec.mesh = mesh
+    return rec
+
+
+def slt_record(mesh, sched, rec, ricker, dt, nsteps, traces, stream=None):
+    """traces: CUDA float64 [nsteps, nrec, 2], written."""
+    if traces.numel() != nsteps * rec.n * 2 or (ricker is not None and ricker.numel() < nsteps):
+        raise ValueError("traces need nsteps * nrec * 2 values and the source series nsteps")
+    _check(lib.slt_record(mesh.ptr, sched.ptr if sched is not None else None, rec.ptr, _dev(ricker, "float64"),
+                          float(dt), int(nsteps), _dev(traces, "float64"), _stream(stream)))
+
+
+def slt_adjoint(mesh, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, stream=None):
+    """Misfit against data [nsteps, nrec, 2] (CUDA float64) and its gradient written to grad
+    [3, ncell] (CUDA float64: d/drho, d/dlambda, d/dmu).  Returns the misfit."""
+    n = slt_mesh_info(mesh)["ncell"]
+    if data.numel() != nsteps * rec.n * 2 or grad.numel() != 3 * n:
+        raise ValueError("data needs nsteps * nrec * 2 values and grad 3 * ncell")
+    if ricker is not None and ricker.numel() < nsteps:
+        raise ValueError("the source series is shorter than nsteps")
+    J = ctypes.c_double()
+    _check(lib.slt_adjoint(mesh.ptr, sched.ptr if sched is not None else None, rec.ptr, _dev(ricker, "float64"),
+                           float(dt), int(nsteps), _dev(data, "float64"), int(checkpoint_every),
+                           _dev(grad, "float64"), ctypes.byref(J), _stream(stream)))
+    return J.value
 
 
 def exported_symbols():

@@ -52,6 +52,45 @@ using namespace slt;
 
 static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
+// Smallest cell id whose barycentric coordinates of xy are all >= -1e-12; (r, s) reference
+// coordinates.  Returns -1 when no cell contains the point.
+static int64_t locate(slt_mesh m, const double* xy, double* r, double* t) {
+  for (int64_t c = 0; c < m->nc; ++c) {
+    const double* a = &m->affine[7 * c];
+    double dx = xy[0] - a[0], dy = xy[1] - a[1];
+    double rr = a[2] * dx + a[3] * dy, tt = a[4] * dx + a[5] * dy;
+    if (rr >= -1e-12 && tt >= -1e-12 && 1.0 - rr - tt >= -1e-12) {
+      *r = rr;
+      *t = tt;
+      return c;
+    }
+  }
+  return -1;
+}
+
+// Point source M_K^-1 phi(x_s) in the cell containing x_s (NULL: no source).
+static void set_source(slt_mesh m, const double* src_xy, cudaStream_t s) {
+  std::vector<double> hsrc(m->Np, 0.0);
+  m->src_cell = -1;
+  m->src_w = -1;
+  if (src_xy) {
+    REQUIRE(std::isfinite(src_xy[0]) && std::isfinite(src_xy[1]), "source position must be finite");
+    double r = 0, t = 0;
+    int64_t c = locate(m, src_xy, &r, &t);
+    REQUIRE(c >= 0, "the source lies outside the mesh");
+    std::vector<double> phi = m->ref.eval(r, t);
+    for (int i = 0; i < m->Np; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < m->Np; ++j) acc += m->ref.Minv[i * m->Np + j] * phi[j];
+      hsrc[i] = acc / m->affine[7 * c + 6];
+    }
+    m->src_cell = c;
+    m->src_w = m->iperm[c];
+  }
+  m->src.upload(hsrc.data(), m->Np, s);
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
 extern "C" {
 
 const char* slt_last_error(void) { return g_err.c_str(); }
@@ -338,6 +377,7 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
   // geometry (caller numbering)
   std::vector<double> rx(nc), ry(nc), sx(nc), sy(nc), adet(nc), fg(9 * nc);
   m->centroid.resize(2 * nc);
+  m->affine.resize(7 * nc);
   for (int64_t c = 0; c < nc; ++c) {
     const double* X = cellxy + 6 * c;
     double j11 = X[2] - X[0], j21 = X[3] - X[1], j12 = X[4] - X[0], j22 = X[5] - X[1];
@@ -345,6 +385,8 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
     REQUIRE(det != 0.0 && std::isfinite(det), "degenerate cell");
     rx[c] = j22 / det; ry[c] = -j12 / det; sx[c] = -j21 / det; sy[c] = j11 / det;
     adet[c] = std::fabs(det);
+    const double aff[7] = {X[0], X[1], rx[c], ry[c], sx[c], sy[c], adet[c]};
+    std::copy(aff, aff + 7, m->affine.begin() + 7 * c);
     for (int f = 0; f < 3; ++f) {
       const double *P = X + 2 * f, *Q = X + 2 * ((f + 1) % 3), *O = X + 2 * ((f + 2) % 3);
       double tx = Q[0] - P[0], ty = Q[1] - P[1];
@@ -385,31 +427,17 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
   m->mat.alloc(3 * ncp); m->mat.upload(hmat.data(), 3 * ncp, s);
   m->nbr.alloc(3 * ncp); m->nbr.upload(hnbr.data(), 3 * ncp, s);
   m->d_perm.alloc(nc); m->d_perm.upload(m->perm.data(), nc, s);
-  m->d_iperm.alloc(nc); m->d_iperm.upload(m->iperm.data(), nc, s);
-  // point source: smallest cell id whose barycentric coordinates are all >= -1e-12
-  std::vector<double> hsrc(m->Np, 0.0);
-  if (src_xy) {
-    REQUIRE(std::isfinite(src_xy[0]) && std::isfinite(src_xy[1]), "source position must be finite");
-    for (int64_t c = 0; c < nc && m->src_cell < 0; ++c) {
-      const double* X = cellxy + 6 * c;
-      double dx = src_xy[0] - X[0], dy = src_xy[1] - X[1];
-      double r = rx[c] * dx + ry[c] * dy, t = sx[c] * dx + sy[c] * dy;
-      if (r >= -1e-12 && t >= -1e-12 && 1.0 - r - t >= -1e-12) {
-        m->src_cell = c;
-        std::vector<double> phi = m->ref.eval(r, t);
-        for (int i = 0; i < m->Np; ++i) {
-          double acc = 0.0;
-          for (int j = 0; j < m->Np; ++j) acc += m->ref.Minv[i * m->Np + j] * phi[j];
-          hsrc[i] = acc / adet[c];
-        }
-      }
-    }
-    REQUIRE(m->src_cell >= 0, "the source lies outside the mesh");
-    m->src_w = m->iperm[m->src_cell];
+  {
+    std::vector<double> hdet(ncp, 0.0);
+    for (int64_t w = 0; w < nc; ++w) hdet[w] = adet[m->perm[w]];
+    m->adet.alloc(ncp);
+    m->adet.upload(hdet.data(), ncp, s);
   }
+  m->d_iperm.alloc(nc); m->d_iperm.upload(m->iperm.data(), nc, s);
   m->src.alloc(m->Np);
-  m->src.upload(hsrc.data(), m->Np, s);
+  set_source(m.get(), src_xy, s);
   upload_constants(m->ref);
+  upload_adjoint_constants(m->ref);
   m->work.alloc(15 * (int64_t)m->Np * ncp);
   SLT_CUDA(cudaMemsetAsync(m->work.p, 0, 15 * (int64_t)m->Np * ncp * sizeof(double), s));
   SLT_CUDA(cudaStreamSynchronize(s));
@@ -539,6 +567,98 @@ int slt_execute_host(slt_mesh m, slt_schedule sched, double* hv, double* hs, con
   SLT_CUDA(cudaMemcpyAsync(hv, m->io_v.p, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaMemcpyAsync(hs, m->io_s.p, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+int slt_mesh_set_source(slt_mesh m, const double* src_xy, void* stream) {
+  API_BEGIN
+  REQUIRE(m, "null mesh");
+  set_source(m, src_xy, as_stream(stream));
+  API_END
+}
+
+int slt_mesh_set_material(slt_mesh m, const double* rho, const double* lam, const double* mu, void* stream) {
+  API_BEGIN
+  REQUIRE(m && rho && lam && mu, "null argument");
+  for (int64_t c = 0; c < m->nc; ++c) {
+    REQUIRE(std::isfinite(rho[c]) && rho[c] > 0, "rho must be finite and positive");
+    REQUIRE(std::isfinite(lam[c]) && std::isfinite(mu[c]) && mu[c] > 0 && lam[c] + mu[c] > 0,
+            "lambda, mu must be finite with mu > 0 and lambda + mu > 0");
+  }
+  const int64_t ncp = m->ncp;
+  std::vector<double> hmat(3 * ncp, 0.0);
+  for (int64_t w = 0; w < m->nc; ++w) {
+    int64_t c = m->perm[w];
+    hmat[w] = 1.0 / rho[c];
+    hmat[ncp + w] = lam[c];
+    hmat[2 * ncp + w] = mu[c];
+  }
+  m->mat.upload(hmat.data(), 3 * ncp, as_stream(stream));
+  SLT_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  API_END
+}
+
+int slt_receivers_create(slt_mesh m, int32_t nrec, const double* xy, slt_receivers* out) {
+  API_BEGIN
+  REQUIRE(m && out && (xy || nrec == 0), "null argument");
+  REQUIRE(nrec >= 0 && nrec <= 65536, "nrec must be in 0..65536");
+  std::unique_ptr<slt_receivers_s> r(new slt_receivers_s());
+  r->mesh = m;
+  r->n = nrec;
+  const int Np = m->Np;
+  std::vector<int32_t> hw(std::max(nrec, 1));
+  std::vector<double> hphi(std::max(nrec, 1) * Np), hq(std::max(nrec, 1) * Np);
+  for (int32_t k = 0; k < nrec; ++k) {
+    double rr = 0, tt = 0;
+    REQUIRE(std::isfinite(xy[2 * k]) && std::isfinite(xy[2 * k + 1]), "receiver positions must be finite");
+    int64_t c = locate(m, xy + 2 * k, &rr, &tt);
+    REQUIRE(c >= 0, "a receiver lies outside the mesh");
+    hw[k] = m->iperm[c];
+    std::vector<double> phi = m->ref.eval(rr, tt);
+    for (int i = 0; i < Np; ++i) {
+      hphi[k * Np + i] = phi[i];
+      double acc = 0.0;
+      for (int j = 0; j < Np; ++j) acc += m->ref.Minv[i * Np + j] * phi[j];
+      hq[k * Np + i] = acc / m->affine[7 * c + 6];
+    }
+  }
+  r->w.alloc(hw.size());
+  r->w.upload(hw.data(), hw.size(), nullptr);
+  r->phi.alloc(hphi.size());
+  r->phi.upload(hphi.data(), hphi.size(), nullptr);
+  r->q.alloc(hq.size());
+  r->q.upload(hq.data(), hq.size(), nullptr);
+  SLT_CUDA(cudaStreamSynchronize(nullptr));
+  *out = r.release();
+  API_END
+}
+
+int slt_receivers_destroy(slt_receivers r) {
+  API_BEGIN
+  delete r;
+  API_END
+}
+
+int slt_record(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,
+               double* traces, void* stream) {
+  API_BEGIN
+  REQUIRE(m && rec && traces, "null argument");
+  REQUIRE(rec->mesh == m, "the receivers belong to another mesh");
+  REQUIRE(nsteps >= 0 && std::isfinite(dt), "nsteps >= 0 and finite dt required");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  record_run(m, sched, rec, ricker, dt, nsteps, traces, as_stream(stream));
+  API_END
+}
+
+int slt_adjoint(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,
+                const double* data, int32_t checkpoint_every, double* grad, double* misfit, void* stream) {
+  API_BEGIN
+  REQUIRE(m && rec && data && grad && misfit, "null argument");
+  REQUIRE(rec->mesh == m, "the receivers belong to another mesh");
+  REQUIRE(nsteps >= 1 && std::isfinite(dt), "nsteps >= 1 and finite dt required");
+  REQUIRE(checkpoint_every >= 1, "checkpoint_every must be >= 1");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  adjoint_run(m, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, as_stream(stream));
   API_END
 }
 

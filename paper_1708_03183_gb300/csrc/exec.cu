@@ -701,6 +701,44 @@ void upload_constants(const RefElem& r) {
   SLT_CUDA(cudaMemcpyToSymbol(c_ref, &h, sizeof(RefC), r.p * sizeof(RefC)));
 }
 
+void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, double dt, int64_t step0,
+                     int64_t nsteps, cudaStream_t s) {
+  Params a = make_params(m);
+  a.dt = dt;
+  a.c24 = dt * dt / 24.0;
+  a.ricker = ricker ? ricker + step0 : nullptr;
+  switch (m->p) {
+    case 1: run_steps<1>(m, sched, a, nsteps, s); break;
+    case 2: run_steps<2>(m, sched, a, nsteps, s); break;
+    case 3: run_steps<3>(m, sched, a, nsteps, s); break;
+    case 4: run_steps<4>(m, sched, a, nsteps, s); break;
+  }
+}
+
+// Operators on work-layout buffers (untiled loops with redirected operands), for the adjoint.
+void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s) {
+  Params a = make_params(m);
+  a.buf[B_S] = const_cast<double*>(in3);
+  a.buf[B_U1] = out2;
+  switch (m->p) {
+    case 1: launch_untiled_range<1>(a, 0, 3, s); break;
+    case 2: launch_untiled_range<2>(a, 0, 3, s); break;
+    case 3: launch_untiled_range<3>(a, 0, 3, s); break;
+    case 4: launch_untiled_range<4>(a, 0, 3, s); break;
+  }
+}
+void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s) {
+  Params a = make_params(m);
+  a.buf[B_U1] = const_cast<double*>(in2);
+  a.buf[B_E] = out3;
+  switch (m->p) {
+    case 1: launch_untiled_range<1>(a, 3, 5, s); break;
+    case 2: launch_untiled_range<2>(a, 3, 5, s); break;
+    case 3: launch_untiled_range<3>(a, 3, 5, s); break;
+    case 4: launch_untiled_range<4>(a, 3, 5, s); break;
+  }
+}
+
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile) {
   g_rec = Recorder();

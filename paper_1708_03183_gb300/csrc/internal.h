@@ -192,6 +192,7 @@ struct slt_mesh_s {
   std::vector<double> centroid;       // [nc][2]
   std::vector<double> fmid, emid;     // facet midpoints [nfi][2], [nfe][2]
   std::vector<int32_t> perm, iperm;   // work id -> cell, cell -> work id
+  std::vector<double> affine;         // [nc][7]: x0, y0, rx, ry, sx, sy, |det J| (caller numbering)
   int64_t src_cell = -1;              // caller numbering
   int64_t cells_int = 0, cells_ext = 0;  // cells with an interior / exterior face
   // device, work layout (SoA, stride ncp)
@@ -202,6 +203,14 @@ struct slt_mesh_s {
   slt::DevBuf<double> work;
   slt::DevBuf<double> ricker_buf;   // for host-buffer execution
   slt::DevBuf<double> io_v, io_s;
+  slt::DevBuf<double> adet;         // |det J| per cell, work order
+};
+
+struct slt_receivers_s {
+  slt_mesh mesh = nullptr;
+  int32_t n = 0;
+  slt::DevBuf<int32_t> w;           // work id of the receiver's cell
+  slt::DevBuf<double> phi, q;       // basis values at the receiver; M_hat^-1 phi / |det J|
 };
 
 namespace slt {
@@ -210,6 +219,18 @@ void upload_constants(const RefElem& r);
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile = nullptr);
 void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t s);
+// time steps on the mesh's work buffers V, S (work layout), source series entry step0 + n
+void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, double dt, int64_t step0,
+                     int64_t nsteps, cudaStream_t s);
+// A: stress-like [3Np][ncp] -> velocity rate [2Np][ncp]; E: velocity-like -> strain [3Np][ncp]
+void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s);
+void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s);
+// adjoint.cu
+void upload_adjoint_constants(const RefElem& r);
+void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,
+                double* traces, cudaStream_t s);
+void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t N,
+                 const double* data, int32_t k, double* grad_out, double* J_host, cudaStream_t s);
 void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
 // inspect.cu
