@@ -225,7 +225,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large")
-    ap.add_argument("--tile-size", type=int, default=512)
+    ap.add_argument("--tile-size", type=int, default=256)
     ap.add_argument("--executor", type=int, default=0, help="0 dataflow (persistent), 1 colour phases")
     ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128 or 256)")
     ap.add_argument("--no-untiled", action="store_true")

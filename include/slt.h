@@ -174,9 +174,10 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
 int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                 double dt, int64_t nsteps, void* stream);
 /* slt_execute that also times every kernel launch with CUDA events recorded on `stream` and
-   synchronises before returning.  profile[0] = total ms of the chain kernels, [1] their number
-   of launches, [2] ms of the layout kernels (caller <-> work layout), [3] their launches,
-   [4] longest and [5] shortest chain-kernel launch in ms, [6..7] zero.  Not thread-safe:
+   synchronises before returning.  profile[0] = total ms of the chain kernels (the dataflow
+   executor's counter set-up included), [1] their number of kernel launches, [2] ms of the
+   layout kernels (caller <-> work layout), [3] their launches, [4] longest and [5] shortest
+   timed chain interval in ms, [6..7] zero.  Not thread-safe:
    one profiled call at a time per process. */
 int slt_execute_profiled(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                          double dt, int64_t nsteps, void* stream, double profile[8]);

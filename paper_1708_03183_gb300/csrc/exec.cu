@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(128) k_loop(Params a) {
 // (their loads are latency bound and more resident tiles overflow L2); one CTA is the minimum.
 template <int P, int BS>
 constexpr int tile_min_blocks() {
-  return 1;
+  return P <= 2 ? 768 / BS : 1;
 }
 
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every loop of the
@@ -406,18 +406,31 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_tiled(Params a
   }
 }
 
-// Persistent dataflow executor: nodes (step, sub-chain, tile) in topological order, taken from an
-// atomic queue; a tile waits only for the tiles it overlaps (lower colours of its sub-chain, the
-// previous sub-chain that touched its cells), then runs its slice of every loop of the sub-chain.
+// Field loads of the dataflow kernel go to L2 only (ld.global.cg).  Cacheable loads after the
+// acquire fence and CTA barrier below are also correct by the PTX memory model; they measured
+// no faster, so the conservative form is kept.
+constexpr bool DF_L2_ONLY = true;
+
+// Persistent dataflow executor with a ready queue.  A node is (step, tile); it depends on the
+// tiles it overlaps (lower colours of its sub-chain, the previous sub-chain's tiles on its
+// cells, wrapping to the previous step), a linear extension of the inspector's colour order.
+// Each node keeps a count of unfinished dependencies; finishing a tile decrements the counts of
+// its successors and publishes those that reach zero to the next queue slot.  CTAs take slots
+// in order and run whatever node was published there, so no CTA waits on one particular
+// dependency while other work is ready.  Every claimed slot is eventually filled (the graph is
+// acyclic and every published node is run), so the bounded waits only end early on an error.
 struct DF {
-  long long total, nps;           // nodes, nodes per step
+  long long total;                // nodes = nsteps * G
+  long long nsteps;
+  int32_t G;                      // tiles over all sub-chains
   int32_t cum[17];                // global tile id base of each sub-chain (cum[k] + local id)
   int32_t first[16], last[16];    // loop range of each sub-chain
-  const int32_t* order;           // [sum m] local tile ids, colour-sorted, per sub-chain concatenated
-  const int32_t* dep_ptr;         // [sum m + 1]
-  const int32_t* dep;             // (global tile << 1) | 1 when it is the previous step's tile
-  int32_t* done;                  // [sum m] steps completed by each tile
-  unsigned long long* head;       // next node
+  const int32_t* succ_ptr;        // [G + 1]
+  const int32_t* succ;            // (global tile << 1) | 1 when the successor is the next step's node
+  int32_t* pending;               // [nsteps * G] unfinished dependencies of each node
+  int32_t* queue;                 // [nsteps * G] node ids in publication order, -1 = not yet
+  unsigned long long* head;       // next slot to take
+  unsigned long long* tail;       // next slot to publish
   int32_t* err;                   // set when a wait gave up
   long long max_spins;
 };
@@ -430,6 +443,27 @@ __device__ __forceinline__ int ld_acquire(const int32_t* p) {
 __device__ __forceinline__ void st_release(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ int atom_add_acq_rel(int32_t* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__global__ void k_df_init(DF df, const int32_t* __restrict__ indeg0, const int32_t* __restrict__ indeg) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < df.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i % df.G);
+    df.pending[i] = i < df.G ? indeg0[g] : indeg[g];
+    df.queue[i] = -1;
+  }
+}
+__global__ void k_df_seed(DF df, const int32_t* __restrict__ indeg0) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < df.G; g += gridDim.x * blockDim.x)
+    if (indeg0[g] == 0) {
+      unsigned long long j = atomicAdd(df.tail, 1ull);
+      df.queue[j] = g;
+    }
+}
 
 template <int P, int BS>
 __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Params a, DF df) {
@@ -438,28 +472,21 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Param
   for (;;) {
     if (threadIdx.x == 0) {
       int stop = 0;
-      const long long node = (long long)atomicAdd(df.head, 1ull);
-      if (node >= df.total || ld_acquire(df.err)) {
+      long long node = -1;
+      const unsigned long long slot = atomicAdd(df.head, 1ull);
+      if ((long long)slot >= df.total || ld_acquire(df.err)) {
         stop = 1;
       } else {
-        const long long st = node / df.nps;
-        const int r = (int)(node % df.nps);
-        int k = 0;
-        while (r >= df.cum[k + 1]) ++k;
-        const int g = df.cum[k] + df.order[r];
-        for (int q = df.dep_ptr[g]; q < df.dep_ptr[g + 1] && !stop; ++q) {
-          const int e = df.dep[q];
-          const int need = (int)(st + 1 - (e & 1));
-          long long spins = 0;
-          while (ld_acquire(&df.done[e >> 1]) < need) {
-            if (++spins > df.max_spins || ld_acquire(df.err)) {
-              atomicExch(df.err, 1);
-              stop = 1;
-              break;
-            }
-            __nanosleep(128);
+        long long spins = 0;
+        while ((node = ld_acquire(&df.queue[slot])) < 0) {
+          if (++spins > df.max_spins || ld_acquire(df.err)) {
+            atomicExch(df.err, 1);
+            stop = 1;
+            break;
           }
+          __nanosleep(64);
         }
+        __threadfence();
       }
       s_node = node;
       s_stop = stop;
@@ -467,20 +494,29 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Param
     __syncthreads();
     if (s_stop) return;
     const long long node = s_node;
-    const long long st = node / df.nps;
-    const int r = (int)(node % df.nps);
+    const long long st = node / df.G;
+    const int g = (int)(node % df.G);
     int k = 0;
-    while (r >= df.cum[k + 1]) ++k;
-    const int t = df.order[r];
+    while (g >= df.cum[k + 1]) ++k;
+    const int t = g - df.cum[k];
     for (int J = df.first[k]; J < df.last[k]; ++J) {
       const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
       const int32_t* items = a.plan_items[J];
-      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, true>(a, J, items[i], st);
+      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, DF_L2_ONLY>(a, J, items[i], st);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
       __threadfence();
-      st_release(&df.done[df.cum[k] + t], (int)(st + 1));
+      for (int q = df.succ_ptr[g]; q < df.succ_ptr[g + 1]; ++q) {
+        const int e = df.succ[q];
+        const long long s2 = st + (e & 1);
+        if (s2 >= df.nsteps) continue;
+        const long long n2 = s2 * df.G + (e >> 1);
+        if (atom_add_acq_rel(&df.pending[n2], -1) == 1) {
+          const unsigned long long j = atomicAdd(df.tail, 1ull);
+          st_release(&df.queue[j], (int32_t)n2);
+        }
+      }
     }
   }
 }
@@ -538,9 +574,11 @@ __global__ void k_from_work(const double* __restrict__ in, int rows, const int32
 struct Recorder {
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)
   std::vector<int> cls;         // 0 = chain kernel, 1 = layout kernel
+  std::vector<int> nl;          // kernel launches inside each timed pair
   bool on = false;
-  void begin(int c, cudaStream_t s) {
+  void begin(int c, cudaStream_t s, int launches = 1) {
     if (!on) return;
+    nl.push_back(launches);
     cudaEvent_t a, b;
     SLT_CUDA(cudaEventCreate(&a));
     SLT_CUDA(cudaEventCreate(&b));
@@ -560,7 +598,7 @@ struct Recorder {
       float ms = 0;
       SLT_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
       tot[cls[i]] += ms;
-      cnt[cls[i]] += 1;
+      cnt[cls[i]] += nl[i];
       if (cls[i] == 0) { mx = std::max(mx, (double)ms); mn = std::min(mn, (double)ms); }
     }
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -620,8 +658,11 @@ template <int P>
 void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
   DataflowPlan& D = sched->df;
   DF df{};
-  df.nps = D.cum.back();
-  df.total = (long long)nsteps * df.nps;
+  df.G = D.cum.back();
+  df.nsteps = nsteps;
+  df.total = (long long)nsteps * df.G;
+  if (df.total == 0) return;
+  if (df.total >= (1ll << 31)) fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
   for (size_t k = 0; k < D.cum.size(); ++k) df.cum[k] = D.cum[k];
   for (size_t k = 0; k < sched->subs.size(); ++k) {
     const SubSched& sub = sched->subs[k];
@@ -632,17 +673,24 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
       a.plan_items[j] = sub.plan_items[j - sub.first].p;
     }
   }
-  df.order = D.order.p;
-  df.dep_ptr = D.dep_ptr.p;
-  df.dep = D.dep.p;
-  df.done = D.done.p;
+  if (D.pending.n < (size_t)df.total) {
+    D.pending.alloc(df.total);
+    D.queue.alloc(df.total);
+  }
+  df.succ_ptr = D.succ_ptr.p;
+  df.succ = D.succ.p;
+  df.pending = D.pending.p;
+  df.queue = D.queue.p;
   df.head = D.head.p;
+  df.tail = D.head.p + 1;
   df.err = D.err.p;
   df.max_spins = sched->wait_spins;
-  if (df.total == 0) return;
-  SLT_CUDA(cudaMemsetAsync(D.done.p, 0, D.done.n * sizeof(int32_t), s));
-  SLT_CUDA(cudaMemsetAsync(D.head.p, 0, sizeof(unsigned long long), s));
+  SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
   SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
+  g_rec.begin(0, s, 3);
+  k_df_init<<<(unsigned)std::min<long long>((df.total + 255) / 256, 152 * 16), 256, 0, s>>>(df, D.indeg0.p, D.indeg.p);
+  k_df_seed<<<(df.G + 255) / 256, 256, 0, s>>>(df, D.indeg0.p);
+  SLT_CUDA(cudaGetLastError());
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -651,7 +699,6 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
   else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 256>, 256, 0));
   long long grid = (long long)nsm * std::max(per, 1);
   if (grid > df.total) grid = df.total;
-  g_rec.begin(0, s);
   if (bs == 128) k_dataflow<P, 128><<<(unsigned)grid, 128, 0, s>>>(a, df);
   else k_dataflow<P, 256><<<(unsigned)grid, 256, 0, s>>>(a, df);
   g_rec.end(s);
@@ -659,7 +706,7 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
   int32_t herr = 0;
   SLT_CUDA(cudaMemcpyAsync(&herr, D.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaStreamSynchronize(s));
-  if (herr) fail(SLT_ERR_TIMEOUT, "a tile's dependency wait gave up (dataflow executor)");
+  if (herr) fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
 }
 
 template <int P>
@@ -750,7 +797,7 @@ void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const do
   const int Np = m->Np;
   int g;
   io_grid(m->nc, g);
-  g_rec.begin(1, s);
+  g_rec.begin(1, s, 2);
   k_to_work<<<g, 256, 0, s>>>(v, 2 * Np, m->d_perm.p, m->nc, m->ncp, a.buf[B_V]);
   k_to_work<<<g, 256, 0, s>>>(sigma, 3 * Np, m->d_perm.p, m->nc, m->ncp, a.buf[B_S]);
   g_rec.end(s);
@@ -761,7 +808,7 @@ void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const do
     case 3: run_steps<3>(m, sched, a, nsteps, s); break;
     case 4: run_steps<4>(m, sched, a, nsteps, s); break;
   }
-  g_rec.begin(1, s);
+  g_rec.begin(1, s, 2);
   k_from_work<<<g, 256, 0, s>>>(a.buf[B_V], 2 * Np, m->d_perm.p, m->nc, m->ncp, v);
   k_from_work<<<g, 256, 0, s>>>(a.buf[B_S], 3 * Np, m->d_perm.p, m->nc, m->ncp, sigma);
   g_rec.end(s);

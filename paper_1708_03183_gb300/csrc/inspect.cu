@@ -696,14 +696,13 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
   D.cum.assign(K + 1, 0);
   for (int k = 0; k < K; ++k) D.cum[k + 1] = D.cum[k] + sched->subs[k].m;
   const int32_t G = D.cum[K];
-  std::vector<int32_t> order(G), colour(G);
+  std::vector<int32_t> colour(G);
   std::vector<std::vector<int32_t>> touch(K, std::vector<int32_t>(nc * CAP));
   std::vector<std::vector<uint8_t>> ntouch(K, std::vector<uint8_t>(nc, 0));
   for (int k = 0; k < K; ++k) {
     SubSched& sub = sched->subs[k];
-    std::vector<int32_t> o = sub.tiles_by_colour.download(s, sub.m);
     std::vector<int32_t> col = sub.colour.download(s, sub.m);
-    for (int32_t i = 0; i < sub.m; ++i) { order[D.cum[k] + i] = o[i]; colour[D.cum[k] + i] = col[i]; }
+    for (int32_t i = 0; i < sub.m; ++i) colour[D.cum[k] + i] = col[i];
     for (int jj = 0; jj < sub.last - sub.first; ++jj) {
       const bool cell_loop = sched->loops[sub.first + jj].set == 0;
       std::vector<int32_t> ptr = sub.plan_ptr[jj].download(s, sub.m + 1);
@@ -745,23 +744,34 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
       }
     }
   }
-  std::vector<int32_t> ptr(G + 1, 0), flat;
+  // successors (dependency edges reversed) and in-degrees of first-step and later nodes
+  std::vector<std::vector<int32_t>> succ(G);
+  std::vector<int32_t> indeg0(G, 0), indeg(G, 0);
   for (int32_t g = 0; g < G; ++g) {
     std::sort(deps[g].begin(), deps[g].end());
     deps[g].erase(std::unique(deps[g].begin(), deps[g].end()), deps[g].end());
-    ptr[g + 1] = ptr[g] + (int32_t)deps[g].size();
-    flat.insert(flat.end(), deps[g].begin(), deps[g].end());
+    for (int32_t e : deps[g]) {
+      succ[e >> 1].push_back((g << 1) | (e & 1));
+      indeg[g] += 1;
+      indeg0[g] += (e & 1) ? 0 : 1;
+    }
+    D.ndeps += (int64_t)deps[g].size();
   }
-  D.ndeps = (int64_t)flat.size();
-  D.order.alloc(G);
-  D.order.upload(order.data(), G, s);
-  D.dep_ptr.alloc(G + 1);
-  D.dep_ptr.upload(ptr.data(), G + 1, s);
-  D.dep.alloc(std::max<size_t>(flat.size(), 1));
-  D.dep.upload(flat.data(), flat.size(), s);
-  D.done.alloc(G);
+  std::vector<int32_t> ptr(G + 1, 0), flat;
+  for (int32_t g = 0; g < G; ++g) {
+    ptr[g + 1] = ptr[g] + (int32_t)succ[g].size();
+    flat.insert(flat.end(), succ[g].begin(), succ[g].end());
+  }
+  D.succ_ptr.alloc(G + 1);
+  D.succ_ptr.upload(ptr.data(), G + 1, s);
+  D.succ.alloc(std::max<size_t>(flat.size(), 1));
+  D.succ.upload(flat.data(), flat.size(), s);
+  D.indeg0.alloc(G);
+  D.indeg0.upload(indeg0.data(), G, s);
+  D.indeg.alloc(G);
+  D.indeg.upload(indeg.data(), G, s);
   D.err.alloc(1);
-  D.head.alloc(1);
+  D.head.alloc(2);
   SLT_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -143,10 +143,11 @@ namespace slt {
 // dependencies of the persistent dataflow executor (elastic chains)
 struct DataflowPlan {
   std::vector<int32_t> cum;          // global tile id base per sub-chain, size nsub + 1
-  DevBuf<int32_t> order;             // colour-sorted local tile ids, per sub-chain concatenated
-  DevBuf<int32_t> dep_ptr, dep;      // CSR over global tiles: (global tile << 1) | previous step
-  DevBuf<int32_t> done, err;
-  DevBuf<unsigned long long> head;
+  DevBuf<int32_t> succ_ptr, succ;    // CSR over global tiles: (global tile << 1) | next step
+  DevBuf<int32_t> indeg0, indeg;     // dependencies of a tile's first-step node / later nodes
+  DevBuf<int32_t> pending, queue;    // per run: [nsteps * tiles]
+  DevBuf<unsigned long long> head;   // head, tail
+  DevBuf<int32_t> err;
   int64_t ndeps = 0;
 };
 }  // namespace slt
