@@ -207,6 +207,50 @@ def adjoint_timing(slt, synth, args, barrier):
             "note": "gradient = forward with checkpoints + segment recompute + reverse sweep"}
 
 
+def batched_timing(slt, synth, args, barrier):
+    """Multi-shot form: the 708x354 P2 layered mesh (501k cells) with `--shots` point sources on
+    the 8x8 grid x = (i+1/2) 300/8, y = (j+1/2) 150/8 (the first `--shots` of them), shots
+    innermost.  Untiled (17 launches per step) and the dataflow executor at each tile size of
+    `--batched-ts`; the fastest is the headline of this block."""
+    import numpy as np
+    import torch
+    S = args.shots
+    K = args.batched_steps
+    W = 3
+    cfg = synth.build_config("large", nx=708, ny=354, nsteps=W + K)
+    m = cfg["mesh"]
+    nc = m["cell2vert"].shape[0]
+    Np = (cfg["p"] + 1) * (cfg["p"] + 2) // 2
+    grid = np.array([((i + 0.5) * 300.0 / 8, (j + 0.5) * 150.0 / 8) for j in range(8) for i in range(8)])
+    pts = grid[np.arange(S) % 64]
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
+    chain = slt.slt_mesh_chain(mesh)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    v = torch.zeros((nc, 2, Np, S), dtype=torch.float64, device="cuda")
+    s = torch.zeros((nc, 3, Np, S), dtype=torch.float64, device="cuda")
+    units = 5 * Np * nc * S
+    res = {}
+    for ts in [0] + list(args.batched_ts):
+        sched = None if ts == 0 else slt.slt_inspect(chain, tile_size=ts, split=(9,), executor=0)
+        slt.slt_execute_batched(mesh, sched, pts, v, s, rk, cfg["dt"], W)
+        barrier()
+        with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            prof = slt.slt_execute_batched(mesh, sched, pts, v, s, rk[W:], cfg["dt"], K, profile=True)
+            barrier()
+        ms = prof["chain_ms"] / K
+        res["untiled" if ts == 0 else "ts%d" % ts] = {"ms_per_step": ms, "value": units / (ms * 1e-3),
+                                                       "launches": prof["chain_launches"] + prof["layout_launches"],
+                                                       "sm_mhz": clk.summary()["sm_mhz"]}
+        del sched
+    best = max(res, key=lambda k: res[k]["value"])
+    cost = slt.slt_mesh_cost(mesh)
+    fl = cost["flops_per_step"] * S
+    return {"workload": "708x354 squares on 300x150 (%d cells), P2 FP64, layered, %d shots on the 8x8 grid, "
+                        "%d steps, fields [cell][comp][node][shot] (%.1f GB)" % (nc, S, K, 5 * Np * nc * S * 8 / 1e9),
+            "value": res[best]["value"], "unit": "dof-updates/s", "best": best, "ms_per_step": res[best]["ms_per_step"],
+            "fp64_frac": fl / (res[best]["ms_per_step"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "runs": res}
+
+
 def workload_name(args):
     import synth
     c = synth.CONFIGS[args.config]
@@ -234,6 +278,10 @@ def main():
     ap.add_argument("--scale", type=int, default=1, help="divide nx, ny of the workload (small profiling cases)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=1000)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--shots", type=int, default=64)
+    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64, 128])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -368,6 +416,10 @@ def main():
 
     if not args.no_adjoint:
         out["adjoint"] = adjoint_timing(slt, synth, args, barrier)
+    if not args.no_batched:
+        del sched, mesh
+        torch.cuda.empty_cache()
+        out["batched"] = batched_timing(slt, synth, args, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, d = oracle_sample_rate(args.config, 10)

@@ -184,6 +184,17 @@ int slt_execute_profiled(slt_mesh mesh, slt_schedule sched, double* v, double* s
 /* The same with HOST fields and source series: copies in, runs, copies out, synchronises. */
 int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* host_sigma,
                      const double* host_ricker, double dt, int64_t nsteps, void* stream);
+/* Many shots of the same mesh and material at once (the batched form): nshots runs with their
+   own point sources src_xy [nshots][2] (host; NULL = no source), sharing the Ricker series.
+   Fields are device arrays with the shots innermost: v [ncell][2][Np][nshots],
+   sigma [ncell][3][Np][nshots], updated in place.  Each (cell, shot) computes exactly what a
+   single-field run of that shot computes.  sched = NULL: untiled chain (17 launches per step,
+   one thread per cell and shot); otherwise the dataflow executor (the schedule's executor must
+   be 0), each tile's items expanded over the shots.  profile (NULL = none) as in
+   slt_execute_profiled.  Synchronises.  Work memory: 15 Np ncell nshots doubles. */
+int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const double* src_xy, double* v,
+                        double* sigma, const double* ricker, double dt, int64_t nsteps, void* stream,
+                        double* profile);
 /* Apply one operator once (for tests): op 0 = A (stress -> velocity rate, device
    in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
    out [ncell][3][Np]).  Runs the untiled loops of that operator. */

@@ -52,6 +52,7 @@ _SIGS = {
     "slt_execute": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
+    "slt_execute_batched": (ctypes.c_int, [P, P, I32, P, P, P, P, F64, I64, P, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
@@ -279,6 +280,29 @@ def slt_execute_profiled(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None)
                                     _stream(stream), ctypes.c_void_p(prof.ctypes.data)))
     return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
                 max_launch_ms=prof[4], min_launch_ms=prof[5])
+
+
+def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, stream=None, profile=False):
+    """Many shots at once: src_xy [nshots, 2] (host; None = no sources, then nshots comes from v),
+    v [ncell, 2, Np, nshots] and sigma [ncell, 3, Np, nshots] CUDA float64 tensors (shots
+    innermost), updated in place.  sched None = untiled.  profile=True returns the kernel times."""
+    if src_xy is not None:
+        xy, xyp = _host(src_xy, np.float64)
+        if xy.ndim != 2 or xy.shape[1] != 2:
+            raise ValueError("src_xy must be [nshots, 2]")
+        S = xy.shape[0]
+    else:
+        xyp, S = None, int(v.shape[-1])
+    if v.dim() != 4 or v.shape[-1] != S or sigma.dim() != 4 or sigma.shape[-1] != S:
+        raise ValueError("v and sigma need the shots as their last dimension (%d)" % S)
+    _check_fields(mesh, _np_numel(np.empty(v.numel() // S)), _np_numel(np.empty(sigma.numel() // S)), ricker, nsteps)
+    prof = np.zeros(8, dtype=np.float64)
+    _check(lib.slt_execute_batched(mesh.ptr, sched.ptr if sched is not None else None, S, xyp, _dev(v, "float64"),
+                                   _dev(sigma, "float64"), _dev(ricker, "float64"), float(dt), int(nsteps),
+                                   _stream(stream), ctypes.c_void_p(prof.ctypes.data) if profile else None))
+    if profile:
+        return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
+                    max_launch_ms=prof[4], min_launch_ms=prof[5])
 
 
 def slt_execute_host(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None):

@@ -69,21 +69,28 @@ static int64_t locate(slt_mesh m, const double* xy, double* r, double* t) {
 }
 
 // Point source M_K^-1 phi(x_s) in the cell containing x_s (NULL: no source).
+// Point source at xy: its cell (caller numbering) and the coefficients M^{-1} phi(xy) / |det J|
+// of the nodal load in that cell (the DG form of a Dirac load, Section 7.1 source term).
+static int64_t source_coeffs(slt_mesh m, const double* xy, double* coef) {
+  REQUIRE(std::isfinite(xy[0]) && std::isfinite(xy[1]), "source position must be finite");
+  double r = 0, t = 0;
+  int64_t c = locate(m, xy, &r, &t);
+  REQUIRE(c >= 0, "a source lies outside the mesh");
+  std::vector<double> phi = m->ref.eval(r, t);
+  for (int i = 0; i < m->Np; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < m->Np; ++j) acc += m->ref.Minv[i * m->Np + j] * phi[j];
+    coef[i] = acc / m->affine[7 * c + 6];
+  }
+  return c;
+}
+
 static void set_source(slt_mesh m, const double* src_xy, cudaStream_t s) {
   std::vector<double> hsrc(m->Np, 0.0);
   m->src_cell = -1;
   m->src_w = -1;
   if (src_xy) {
-    REQUIRE(std::isfinite(src_xy[0]) && std::isfinite(src_xy[1]), "source position must be finite");
-    double r = 0, t = 0;
-    int64_t c = locate(m, src_xy, &r, &t);
-    REQUIRE(c >= 0, "the source lies outside the mesh");
-    std::vector<double> phi = m->ref.eval(r, t);
-    for (int i = 0; i < m->Np; ++i) {
-      double acc = 0.0;
-      for (int j = 0; j < m->Np; ++j) acc += m->ref.Minv[i * m->Np + j] * phi[j];
-      hsrc[i] = acc / m->affine[7 * c + 6];
-    }
+    int64_t c = source_coeffs(m, src_xy, hsrc.data());
     m->src_cell = c;
     m->src_w = m->iperm[c];
   }
@@ -437,6 +444,7 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
   m->src.alloc(m->Np);
   set_source(m.get(), src_xy, s);
   upload_constants(m->ref);
+  upload_constants_batched(m->ref);
   upload_adjoint_constants(m->ref);
   m->work.alloc(15 * (int64_t)m->Np * ncp);
   SLT_CUDA(cudaMemsetAsync(m->work.p, 0, 15 * (int64_t)m->Np * ncp * sizeof(double), s));
@@ -659,6 +667,29 @@ int slt_adjoint(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
   REQUIRE(checkpoint_every >= 1, "checkpoint_every must be >= 1");
   if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
   adjoint_run(m, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, as_stream(stream));
+  API_END
+}
+
+int slt_execute_batched(slt_mesh m, slt_schedule sched, int32_t nshots, const double* src_xy, double* v,
+                        double* sigma, const double* ricker, double dt, int64_t nsteps, void* stream,
+                        double* profile) {
+  API_BEGIN
+  REQUIRE(m && v && sigma, "null argument");
+  REQUIRE(nshots >= 1 && nshots <= 4096, "nshots must be in 1..4096");
+  REQUIRE(nsteps >= 0 && std::isfinite(dt), "nsteps >= 0 and finite dt required");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  cudaStream_t s = as_stream(stream);
+  const int Np = m->Np;
+  std::vector<int32_t> hw(nshots, -1);
+  std::vector<double> hs((size_t)nshots * Np, 0.0);
+  if (src_xy)
+    for (int32_t k = 0; k < nshots; ++k) hw[k] = m->iperm[source_coeffs(m, src_xy + 2 * k, hs.data() + (size_t)k * Np)];
+  if (m->bsrc_w.n < (size_t)nshots) m->bsrc_w.alloc(nshots);
+  if (m->bsrc.n < (size_t)nshots * Np) m->bsrc.alloc((size_t)nshots * Np);
+  m->bsrc_w.upload(hw.data(), nshots, s);
+  m->bsrc.upload(hs.data(), (size_t)nshots * Np, s);
+  exec_run_batched(m, sched, nshots, m->bsrc_w.p, m->bsrc.p, v, sigma, ricker, dt, nsteps, s, profile);
+  SLT_CUDA(cudaStreamSynchronize(s));
   API_END
 }
 

@@ -1,0 +1,192 @@
+// Multi-shot executor: S shots of the same mesh and material advance together, fields stored
+// with the shots innermost ([cell][comp][node][shot] for the caller, rows of ncp * S doubles in
+// the work layout).  Consecutive threads take consecutive shots of one cell, so field loads
+// coalesce over shots and per-cell geometry, neighbours and face masks are warp-uniform; every
+// shot has its own point source.  The loop bodies are those of exec_body.cuh; the arithmetic of
+// each (cell, shot) is exactly that of a single-field run with that shot's source.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "refmask.h"
+
+namespace slt {
+
+namespace {
+
+#include "exec_body.cuh"
+#include "dataflow.cuh"
+
+template <int P, int J>
+__global__ void __launch_bounds__(128) k_loop_b(Params a) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // over nc * S
+  if (t >= a.nc * a.S) return;
+  const int64_t c = t / a.S;
+  const int s = (int)(t % a.S);
+  int32_t item = (int32_t)c;
+  if (is_facet_loop(J)) {
+    int mask = 0;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      bool interior = a.nbr[f * a.ncp + c] >= 0;
+      if (is_int_loop(J) ? interior : !interior) mask |= 1 << f;
+    }
+    if (!mask) return;
+    item = (int32_t)((c << 3) | mask);
+  }
+  run_loop<P, false, true>(a, J, item, a.step, s);
+}
+
+template <int P>
+void launch_untiled_b(const Params& a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((a.nc * a.S + 127) / 128);
+  k_loop_b<P, 0><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 1><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 2><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 3><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 4><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 5><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 6><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 7><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 8><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 9><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 10><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 11><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 12><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 13><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 14><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 15><<<blocks, 128, 0, s>>>(a);
+  k_loop_b<P, 16><<<blocks, 128, 0, s>>>(a);
+  SLT_CUDA(cudaGetLastError());
+}
+
+// caller [cell][row][S] <-> work [(row * ncp + w) * S + s], shots fastest on both sides
+__global__ void k_to_work_b(const double* __restrict__ in, int rows, int S, const int32_t* __restrict__ perm,
+                            int64_t nc, int64_t ncp, double* __restrict__ out) {
+  const int64_t n = nc * rows * S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i % S, r = (i / S) % rows, w = i / ((int64_t)S * rows);
+    out[((int64_t)r * ncp + w) * S + s] = in[((int64_t)perm[w] * rows + r) * S + s];
+  }
+}
+__global__ void k_from_work_b(const double* __restrict__ in, int rows, int S, const int32_t* __restrict__ perm,
+                              int64_t nc, int64_t ncp, double* __restrict__ out) {
+  const int64_t n = nc * rows * S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i % S, r = (i / S) % rows, w = i / ((int64_t)S * rows);
+    out[((int64_t)perm[w] * rows + r) * S + s] = in[((int64_t)r * ncp + w) * S + s];
+  }
+}
+
+struct Timer {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> nl;
+  bool on = false;
+  void begin(cudaStream_t s, int n) {
+    if (!on) return;
+    cudaEvent_t e0, e1;
+    SLT_CUDA(cudaEventCreate(&e0));
+    SLT_CUDA(cudaEventCreate(&e1));
+    ev.push_back(e0);
+    ev.push_back(e1);
+    nl.push_back(n);
+    SLT_CUDA(cudaEventRecord(e0, s));
+  }
+  void end(cudaStream_t s) {
+    if (on) SLT_CUDA(cudaEventRecord(ev.back(), s));
+  }
+};
+
+template <int P>
+void run_batched(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s, Timer& tm) {
+  if (sched) {
+    launch_dataflow<P, true>(sched, a, nsteps, s, [&] { tm.begin(s, 3); }, [&] { tm.end(s); });
+    return;
+  }
+  for (int64_t step = 0; step < nsteps; ++step) {
+    a.step = step;
+    tm.begin(s, 17);
+    launch_untiled_b<P>(a, s);
+    tm.end(s);
+  }
+}
+
+}  // namespace
+
+void upload_constants_batched(const RefElem& r) { upload_ref(r); }
+
+void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* d_src_w, const double* d_src,
+                      double* v, double* sigma, const double* ricker, double dt, int64_t nsteps, cudaStream_t s,
+                      double* profile) {
+  if (sched && sched->executor != 0)
+    fail(SLT_ERR_UNSUPPORTED, "the multi-shot executor runs untiled or with the dataflow executor");
+  const int64_t Np = m->Np, ncp = m->ncp, fs = ncp * S;
+  const size_t need = 15 * Np * fs;
+  if (m->work_b.n < need) {
+    m->work_b.alloc(need);
+    SLT_CUDA(cudaMemsetAsync(m->work_b.p, 0, need * sizeof(double), s));
+  }
+  double* base = m->work_b.p;
+  Params a{};
+  a.ncp = ncp;
+  a.nc = m->nc;
+  a.geo = m->geo.p;
+  a.fgeo = m->fgeo.p;
+  a.mat = m->mat.p;
+  a.nbr = m->nbr.p;
+  a.buf[B_V] = base;
+  a.buf[B_S] = base + 2 * Np * fs;
+  a.buf[B_U1] = base + 5 * Np * fs;
+  a.buf[B_U2] = base + 7 * Np * fs;
+  a.buf[B_E] = base + 9 * Np * fs;
+  a.buf[B_S1] = base + 12 * Np * fs;
+  a.ricker = ricker;
+  a.src = nullptr;
+  a.src_w = -1;
+  a.dt = dt;
+  a.c24 = dt * dt / 24.0;
+  a.S = S;
+  a.fs = fs;
+  a.src_wb = d_src_w;
+  a.src_b = d_src;
+  Timer tm;
+  tm.on = profile != nullptr;
+  const int g = (int)std::min<int64_t>((m->nc * 5 * Np * S + 255) / 256, 152 * 32);
+  tm.begin(s, 2);
+  k_to_work_b<<<g, 256, 0, s>>>(v, 2 * Np, S, m->d_perm.p, m->nc, ncp, a.buf[B_V]);
+  k_to_work_b<<<g, 256, 0, s>>>(sigma, 3 * Np, S, m->d_perm.p, m->nc, ncp, a.buf[B_S]);
+  tm.end(s);
+  SLT_CUDA(cudaGetLastError());
+  switch (m->p) {
+    case 1: run_batched<1>(m, sched, a, nsteps, s, tm); break;
+    case 2: run_batched<2>(m, sched, a, nsteps, s, tm); break;
+    case 3: run_batched<3>(m, sched, a, nsteps, s, tm); break;
+    case 4: run_batched<4>(m, sched, a, nsteps, s, tm); break;
+  }
+  tm.begin(s, 2);
+  k_from_work_b<<<g, 256, 0, s>>>(a.buf[B_V], 2 * Np, S, m->d_perm.p, m->nc, ncp, v);
+  k_from_work_b<<<g, 256, 0, s>>>(a.buf[B_S], 3 * Np, S, m->d_perm.p, m->nc, ncp, sigma);
+  tm.end(s);
+  SLT_CUDA(cudaGetLastError());
+  if (tm.on) {
+    SLT_CUDA(cudaStreamSynchronize(s));
+    double tot[2] = {0, 0}, cnt[2] = {0, 0}, mx = 0, mn = 1e300;
+    const size_t npairs = tm.nl.size();
+    for (size_t i = 0; i < npairs; ++i) {
+      float ms = 0;
+      SLT_CUDA(cudaEventElapsedTime(&ms, tm.ev[2 * i], tm.ev[2 * i + 1]));
+      const int cls = (i == 0 || i + 1 == npairs) ? 1 : 0;  // first and last pairs: layout kernels
+      tot[cls] += ms;
+      cnt[cls] += tm.nl[i];
+      if (!cls) { mx = std::max(mx, (double)ms); mn = std::min(mn, (double)ms); }
+    }
+    for (cudaEvent_t e : tm.ev) cudaEventDestroy(e);
+    profile[0] = tot[0]; profile[1] = cnt[0]; profile[2] = tot[1]; profile[3] = cnt[1];
+    profile[4] = cnt[0] ? mx : 0; profile[5] = cnt[0] ? mn : 0; profile[6] = 0; profile[7] = 0;
+  }
+}
+
+}  // namespace slt

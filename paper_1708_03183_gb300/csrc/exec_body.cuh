@@ -1,0 +1,398 @@
+// Loop bodies of the DG elastic chain, shared by the single-field executor (exec.cu) and the
+// multi-shot executor (exec_batched.cu).  Included inside an anonymous namespace of each
+// translation unit, which therefore holds its own copy of the reference matrices.
+//
+// One thread computes one (cell, shot) work item.  Per-cell data (geometry, material,
+// neighbours) is indexed by the cell's work id; fields are rows of `fs` doubles indexed by the
+// item's column: the cell itself for one field (fs = ncp), cell * S + shot for S shots stored
+// innermost (fs = ncp * S).  With BATCH = false, S = 1 and the column is the cell.
+//
+// Operators in nodal strong form (the mass matrix cancels in the volume terms):
+//   A sigma = (1/rho) div(sigma) - sum_f (F_f / 2 rho) Lift_f ((sigma - sigma_nb) n_f)
+//             - sum_{exterior f} (F_f / rho) Lift_f (sigma n_f)
+//   E(v)    = (dvx/dx, dvy/dy, dvx/dy + dvy/dx) - sum_f (F_f / 2) Lift_f sym((v - v_nb) (x) n_f)
+//   B v     = C E(v),  C the isotropic Hooke law on (xx, yy, 2xy)
+// with F_f = |face f| / |det J| and n_f the outward unit normal of face f.  The reference
+// matrices live in constant memory (warp-uniform operands); structural zeros of Dr, Ds are
+// skipped through the generated dr_nz / ds_nz tables.
+#pragma once
+
+constexpr int MAXNP = 15, MAXNFP = 5;
+struct RefC {
+  double Dr[MAXNP * MAXNP];
+  double Ds[MAXNP * MAXNP];
+  double Lift[3 * MAXNP * MAXNFP];
+};
+__constant__ RefC c_ref[5];  // indexed by degree 1..4
+
+__host__ __device__ constexpr int np_of(int P) { return (P + 1) * (P + 2) / 2; }
+__host__ __device__ constexpr int nidx(int P, int i, int j) { return j * (P + 1) - j * (j - 1) / 2 + i; }
+// node index of face node k of face f (face f runs from local vertex f to f+1)
+template <int P>
+__device__ __forceinline__ int fnode(int f, int k) {
+  return f == 0 ? nidx(P, k, 0) : (f == 1 ? nidx(P, P - k, k) : nidx(P, 0, P - k));
+}
+
+// Field loads: plain (L1-cached) in the per-loop and colour-phase kernels; L2-only (ld.global.cg)
+// in the persistent dataflow kernel, where other SMs write the fields during the launch.
+template <bool CG>
+__device__ __forceinline__ double ld(const double* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// buffers of the work layout, each `rows` rows of fs doubles
+enum Buf { B_V = 0, B_S = 1, B_U1 = 2, B_U2 = 3, B_E = 4, B_S1 = 5 };
+
+struct Params {
+  int64_t ncp, nc;
+  const double* __restrict__ geo;   // [4][ncp]: rx ry sx sy
+  const double* __restrict__ fgeo;  // [9][ncp]: nx ny F for faces 0, 1, 2
+  const double* __restrict__ mat;   // [3][ncp]: 1/rho, lambda, mu
+  const int32_t* __restrict__ nbr;  // [3][ncp]: (w_nb << 3) | (face_nb << 1) | flip, or -1
+  double* buf[6];
+  const double* ricker;             // [nsteps] or null
+  const double* src;                // [Np] source coefficients (one field)
+  int32_t src_w;                    // source cell (one field)
+  int64_t step;
+  double dt, c24;
+  const int32_t* plan_ptr[17];
+  const int32_t* plan_items[17];
+  // multi-shot layout
+  int32_t S;                        // shots per cell (1 for one field)
+  int64_t fs;                       // field row stride: ncp * S
+  const int32_t* src_wb;            // [S] source cell of every shot
+  const double* src_b;              // [S][Np] source coefficients of every shot
+};
+
+// one (cell, shot) work item: c = cell work id, f = field column, s = shot
+struct Pos {
+  int64_t c, f;
+  int s;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ int64_t fstride(const Params& a) {
+  if constexpr (BATCH) return a.fs;
+  else return a.ncp;
+}
+template <bool BATCH>
+__device__ __forceinline__ int64_t ncol(const Params& a, int64_t wn, int s) {  // column of a neighbour
+  if constexpr (BATCH) return wn * a.S + s;
+  else return wn;
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const double* S, double* U, double rx,
+                                        double ry, double sx, double sy) {
+  // U = div(S) scaled (rx.. already divided by rho): x row uses (sxx, sxy), y row (sxy, syy)
+  constexpr int Np = np_of(P);
+  const RefC& R = c_ref[P];
+  const int64_t fs = fstride<BATCH>(a), w = q.f;
+#pragma unroll
+  for (int comp = 0; comp < 2; ++comp) {
+    double A[Np], B[Np];
+#pragma unroll
+    for (int j = 0; j < Np; ++j) {
+      double s1 = ld<CG>(&S[(int64_t)((comp == 0 ? 0 : 2) * Np + j) * fs + w]);
+      double s2 = ld<CG>(&S[(int64_t)((comp == 0 ? 2 : 1) * Np + j) * fs + w]);
+      A[j] = fma(ry, s2, rx * s1);
+      B[j] = fma(sy, s2, sx * s1);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < Np; ++j) {
+        if ((dr_nz(P, i) >> j) & 1u) acc = fma(R.Dr[i * MAXNP + j], A[j], acc);
+        if ((ds_nz(P, i) >> j) & 1u) acc = fma(R.Ds[i * MAXNP + j], B[j], acc);
+      }
+      U[(int64_t)(comp * Np + i) * fs + w] = acc;
+    }
+  }
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void volB(const Params& a, const Pos& q, const double* S, double* U) {
+  const int64_t n = a.ncp, c = q.c;
+  double ir = a.mat[c];
+  vol_div<P, CG, BATCH>(a, q, S, U, a.geo[c] * ir, a.geo[n + c] * ir, a.geo[2 * n + c] * ir, a.geo[3 * n + c] * ir);
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void volD(const Params& a, const Pos& q, const double* V, double* E) {
+  constexpr int Np = np_of(P);
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  double rx = a.geo[c], ry = a.geo[n + c], sx = a.geo[2 * n + c], sy = a.geo[3 * n + c];
+  double vx[Np], vy[Np];
+#pragma unroll
+  for (int j = 0; j < Np; ++j) {
+    vx[j] = ld<CG>(&V[(int64_t)j * fs + w]);
+    vy[j] = ld<CG>(&V[(int64_t)(Np + j) * fs + w]);
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i) {
+    double drx = 0.0, dsx = 0.0, dry = 0.0, dsy = 0.0;
+#pragma unroll
+    for (int j = 0; j < Np; ++j) {
+      if ((dr_nz(P, i) >> j) & 1u) {
+        drx = fma(R.Dr[i * MAXNP + j], vx[j], drx);
+        dry = fma(R.Dr[i * MAXNP + j], vy[j], dry);
+      }
+      if ((ds_nz(P, i) >> j) & 1u) {
+        dsx = fma(R.Ds[i * MAXNP + j], vx[j], dsx);
+        dsy = fma(R.Ds[i * MAXNP + j], vy[j], dsy);
+      }
+    }
+    E[(int64_t)i * fs + w] = fma(sx, dsx, rx * drx);
+    E[(int64_t)(Np + i) * fs + w] = fma(sy, dsy, ry * dry);
+    E[(int64_t)(2 * Np + i) * fs + w] = fma(sx, dsy, fma(rx, dry, fma(sy, dsx, ry * drx)));
+  }
+}
+
+// S1 = C E at the nodes, then U = div(S1)/rho
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void hookeB(const Params& a, const Pos& q, const double* E, double* S1, double* U) {
+  constexpr int Np = np_of(P);
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
+  double l2m = fma(2.0, mu, lam);
+#pragma unroll
+  for (int j = 0; j < Np; ++j) {
+    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
+           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
+    S1[(int64_t)j * fs + w] = fma(lam, eyy, l2m * exx);
+    S1[(int64_t)(Np + j) * fs + w] = fma(lam, exx, l2m * eyy);
+    S1[(int64_t)(2 * Np + j) * fs + w] = mu * g;
+  }
+  volB<P, CG, BATCH>(a, q, S1, U);
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void intB(const Params& a, const Pos& q, int mask, const double* S, double* U) {
+  constexpr int Np = np_of(P), Nfp = P + 1;
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const double ir = a.mat[c];
+  double ax[Np], ay[Np];
+#pragma unroll
+  for (int i = 0; i < Np; ++i) ax[i] = ay[i] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const int32_t nb = a.nbr[f * n + c];
+    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
+    const int fn = (nb >> 1) & 3, flip = nb & 1;
+    const double sc = -0.5 * a.fgeo[(3 * f + 2) * n + c] * ir;
+    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
+    double gx[Nfp], gy[Nfp];
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int i0 = fnode<P>(f, k);
+      const int i1 = fnode<P>(fn, flip ? P - k : k);
+      double dxx = ld<CG>(&S[(int64_t)i0 * fs + w]) - ld<CG>(&S[(int64_t)i1 * fs + wn]);
+      double dyy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(Np + i1) * fs + wn]);
+      double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * fs + wn]);
+      gx[k] = fma(dxy, ny, dxx * nx);
+      gy[k] = fma(dyy, ny, dxy * nx);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i)
+#pragma unroll
+      for (int k = 0; k < Nfp; ++k) {
+        ax[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], ax[i]);
+        ay[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], ay[i]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i) {
+    U[(int64_t)i * fs + w] = ld<CG>(&U[(int64_t)i * fs + w]) + ax[i];
+    U[(int64_t)(Np + i) * fs + w] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]) + ay[i];
+  }
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void extB(const Params& a, const Pos& q, int mask, const double* S, double* U) {
+  constexpr int Np = np_of(P), Nfp = P + 1;
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const double ir = a.mat[c];
+  double ax[Np], ay[Np];
+#pragma unroll
+  for (int i = 0; i < Np; ++i) ax[i] = ay[i] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const double sc = -a.fgeo[(3 * f + 2) * n + c] * ir;
+    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
+    double gx[Nfp], gy[Nfp];
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int i0 = fnode<P>(f, k);
+      double sxx = ld<CG>(&S[(int64_t)i0 * fs + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]),
+             sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]);
+      gx[k] = fma(sxy, ny, sxx * nx);
+      gy[k] = fma(syy, ny, sxy * nx);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i)
+#pragma unroll
+      for (int k = 0; k < Nfp; ++k) {
+        ax[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], ax[i]);
+        ay[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], ay[i]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i) {
+    U[(int64_t)i * fs + w] = ld<CG>(&U[(int64_t)i * fs + w]) + ax[i];
+    U[(int64_t)(Np + i) * fs + w] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]) + ay[i];
+  }
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void intD(const Params& a, const Pos& q, int mask, const double* V, double* E) {
+  constexpr int Np = np_of(P), Nfp = P + 1;
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  double exx[Np], eyy[Np], eg[Np];
+#pragma unroll
+  for (int i = 0; i < Np; ++i) exx[i] = eyy[i] = eg[i] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const int32_t nb = a.nbr[f * n + c];
+    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
+    const int fn = (nb >> 1) & 3, flip = nb & 1;
+    const double h = -0.5 * a.fgeo[(3 * f + 2) * n + c];
+    const double cx = h * a.fgeo[(3 * f) * n + c], cy = h * a.fgeo[(3 * f + 1) * n + c];
+    double dx[Nfp], dy[Nfp];
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int i0 = fnode<P>(f, k);
+      const int i1 = fnode<P>(fn, flip ? P - k : k);
+      dx[k] = ld<CG>(&V[(int64_t)i0 * fs + w]) - ld<CG>(&V[(int64_t)i1 * fs + wn]);
+      dy[k] = ld<CG>(&V[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&V[(int64_t)(Np + i1) * fs + wn]);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i) {
+      double lx = R.Lift[(f * MAXNP + i) * MAXNFP] * dx[0], ly = R.Lift[(f * MAXNP + i) * MAXNFP] * dy[0];
+#pragma unroll
+      for (int k = 1; k < Nfp; ++k) {
+        lx = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dx[k], lx);
+        ly = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dy[k], ly);
+      }
+      exx[i] = fma(cx, lx, exx[i]);
+      eyy[i] = fma(cy, ly, eyy[i]);
+      eg[i] = fma(cy, lx, fma(cx, ly, eg[i]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i) {
+    E[(int64_t)i * fs + w] = ld<CG>(&E[(int64_t)i * fs + w]) + exx[i];
+    E[(int64_t)(Np + i) * fs + w] = ld<CG>(&E[(int64_t)(Np + i) * fs + w]) + eyy[i];
+    E[(int64_t)(2 * Np + i) * fs + w] = ld<CG>(&E[(int64_t)(2 * Np + i) * fs + w]) + eg[i];
+  }
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void updV(const Params& a, const Pos& q) {
+  constexpr int Np = np_of(P);
+  const int64_t fs = fstride<BATCH>(a), w = q.f;
+  double* V = a.buf[B_V];
+  const double* U1 = a.buf[B_U1];
+  const double* U2 = a.buf[B_U2];
+#pragma unroll
+  for (int r = 0; r < 2 * Np; ++r) {
+    int64_t o = (int64_t)r * fs + w;
+    V[o] = fma(a.dt, fma(a.c24, ld<CG>(&U2[o]), ld<CG>(&U1[o])), ld<CG>(&V[o]));
+  }
+}
+
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void updS(const Params& a, const Pos& q, int64_t step) {
+  constexpr int Np = np_of(P);
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  double* S = a.buf[B_S];
+  const double* S1 = a.buf[B_S1];
+  const double* E = a.buf[B_E];
+  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
+  double l2m = fma(2.0, mu, lam);
+  int32_t sw;
+  const double* sv;
+  if constexpr (BATCH) {
+    sw = a.src_wb ? a.src_wb[q.s] : -1;
+    sv = a.src_b + (int64_t)q.s * Np;
+  } else {
+    sw = a.src_w;
+    sv = a.src;
+  }
+  const bool src = (c == sw) && a.ricker != nullptr;
+  const double gs = src ? a.dt * a.ricker[step] : 0.0;
+#pragma unroll
+  for (int j = 0; j < Np; ++j) {
+    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
+           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
+    double cxx = fma(lam, eyy, l2m * exx), cyy = fma(lam, exx, l2m * eyy), cxy = mu * g;
+    int64_t oxx = (int64_t)j * fs + w, oyy = (int64_t)(Np + j) * fs + w, oxy = (int64_t)(2 * Np + j) * fs + w;
+    double nxx = fma(a.dt, fma(a.c24, cxx, ld<CG>(&S1[oxx])), ld<CG>(&S[oxx]));
+    double nyy = fma(a.dt, fma(a.c24, cyy, ld<CG>(&S1[oyy])), ld<CG>(&S[oyy]));
+    S[oxy] = fma(a.dt, fma(a.c24, cxy, ld<CG>(&S1[oxy])), ld<CG>(&S[oxy]));
+    if (src) {
+      nxx += gs * sv[j];
+      nyy += gs * sv[j];
+    }
+    S[oxx] = nxx;
+    S[oyy] = nyy;
+  }
+}
+
+__host__ __device__ constexpr bool is_int_loop(int J) { return J == 1 || J == 4 || J == 6 || J == 10 || J == 12 || J == 15; }
+__host__ __device__ constexpr bool is_ext_loop(int J) { return J == 2 || J == 7 || J == 13; }
+__host__ __device__ constexpr bool is_facet_loop(int J) { return is_int_loop(J) || is_ext_loop(J); }
+
+// one iteration of loop J for shot s; item = cell work id (cell loops) or (work id << 3) | face
+// mask (facet loops)
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void run_loop(const Params& a, int J, int32_t item, int64_t step, int s = 0) {
+  double* const* b = a.buf;
+  Pos q;
+  q.c = is_facet_loop(J) ? (int64_t)(item >> 3) : (int64_t)item;
+  q.s = s;
+  q.f = BATCH ? q.c * a.S + s : q.c;
+  const int mask = item & 7;
+  switch (J) {
+    case 0: volB<P, CG, BATCH>(a, q, b[B_S], b[B_U1]); break;
+    case 1: intB<P, CG, BATCH>(a, q, mask, b[B_S], b[B_U1]); break;
+    case 2: extB<P, CG, BATCH>(a, q, mask, b[B_S], b[B_U1]); break;
+    case 3: volD<P, CG, BATCH>(a, q, b[B_U1], b[B_E]); break;
+    case 4: intD<P, CG, BATCH>(a, q, mask, b[B_U1], b[B_E]); break;
+    case 5: hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U2]); break;
+    case 6: intB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U2]); break;
+    case 7: extB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U2]); break;
+    case 8: updV<P, CG, BATCH>(a, q); break;
+    case 9: volD<P, CG, BATCH>(a, q, b[B_V], b[B_E]); break;
+    case 10: intD<P, CG, BATCH>(a, q, mask, b[B_V], b[B_E]); break;
+    case 11: hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U1]); break;
+    case 12: intB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U1]); break;
+    case 13: extB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U1]); break;
+    case 14: volD<P, CG, BATCH>(a, q, b[B_U1], b[B_E]); break;
+    case 15: intD<P, CG, BATCH>(a, q, mask, b[B_U1], b[B_E]); break;
+    case 16: updS<P, CG, BATCH>(a, q, step); break;
+    default: break;
+  }
+}
+
+// reference matrices of one degree into this translation unit's constant memory
+inline void upload_ref(const slt::RefElem& r) {
+  RefC h{};
+  for (int i = 0; i < r.Np; ++i)
+    for (int j = 0; j < r.Np; ++j) {
+      h.Dr[i * MAXNP + j] = r.Dr[i * r.Np + j];
+      h.Ds[i * MAXNP + j] = r.Ds[i * r.Np + j];
+    }
+  for (int f = 0; f < 3; ++f)
+    for (int i = 0; i < r.Np; ++i)
+      for (int k = 0; k < r.Nfp; ++k) h.Lift[(f * MAXNP + i) * MAXNFP + k] = r.Lift[(f * r.Np + i) * r.Nfp + k];
+  SLT_CUDA(cudaMemcpyToSymbol(c_ref, &h, sizeof(RefC), r.p * sizeof(RefC)));
+}

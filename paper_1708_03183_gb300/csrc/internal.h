@@ -205,6 +205,8 @@ struct slt_mesh_s {
   slt::DevBuf<double> ricker_buf;   // for host-buffer execution
   slt::DevBuf<double> io_v, io_s;
   slt::DevBuf<double> adet;         // |det J| per cell, work order
+  slt::DevBuf<double> work_b, bsrc;  // multi-shot work fields; per-shot source coefficients
+  slt::DevBuf<int32_t> bsrc_w;       // per-shot source cell (work id, -1 = none)
 };
 
 struct slt_receivers_s {
@@ -226,6 +228,11 @@ void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, doubl
 // A: stress-like [3Np][ncp] -> velocity rate [2Np][ncp]; E: velocity-like -> strain [3Np][ncp]
 void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s);
 void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s);
+// exec_batched.cu
+void upload_constants_batched(const RefElem& r);
+void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* d_src_w, const double* d_src,
+                      double* v, double* sigma, const double* ricker, double dt, int64_t nsteps, cudaStream_t s,
+                      double* profile);
 // adjoint.cu
 void upload_adjoint_constants(const RefElem& r);
 void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,
