@@ -71,8 +71,9 @@ int slt_chain_info(slt_chain chain, int32_t* nsets, int32_t* nmaps, int32_t* nlo
 /* ------------------------------------------------------------------ inspector (Section 5.1)
  * slt_inspect runs Algorithm 1 (with Algorithms 2 and 3) as GPU kernels on every sub-chain
  * [split_k, split_{k+1}) of the chain (a fusion scheme: sub-chains are tiled independently and
- * executed one after the other).  The seed loop of a sub-chain is its first loop.
+ * executed one after the other).
  *
+ *  seed loop  : the sub-chain's first loop, or seed_loop[k] loops after it (backward tiling).
  *  partition  : seed iterations ranked by identity (renumber = 0) or by a stable sort of the
  *               order-16 Hilbert index of their points quantised on a 65536^2 grid over the
  *               bounding box (renumber = 1); iteration of rank r goes to tile r / tile_size.
@@ -96,10 +97,17 @@ typedef struct {
   int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
   int32_t block_threads; /* threads per tile CTA: 128 or 256 (0 = 256) */
+  int32_t sub_tile_size[16]; /* seed tile size of sub-chain k (0 = tile_size): a fusion scheme
+                                with its own tile size per sub-chain (Section 7.2) */
+  int32_t seed_loop[16];     /* seed loop of sub-chain k, counted from its first loop (0 = the
+                                first loop, forward tiling only); > 0 selects backward tiling
+                                for the loops before it (Section 5.1.1): MIN projections from
+                                the seed towards the first loop, then MAX projections over the
+                                loops up to the seed and forward tiling after it */
 } slt_options;
 
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
-   no split, dataflow executor. */
+   no split, dataflow executor, no per-sub-chain tile sizes. */
 int slt_options_default(slt_options* opt);
 int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
 int slt_schedule_destroy(slt_schedule sched);
@@ -195,6 +203,20 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
 int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const double* src_xy, double* v,
                         double* sigma, const double* ricker, double dt, int64_t nsteps, void* stream,
                         double* profile);
+/* Autotuner over tile size, tile shape and CTA size (Section 7.3 searches them empirically).
+   Times the untiled chain, then every candidate (tile_sizes[i], renumber, block_threads[b]):
+   renumber 1 (Hilbert tiles) only, or also 0 (chunks of the mesh numbering) when shapes != 0.
+   Each candidate is inspected with `base` for every other option (split points, executor ...),
+   run 2 untimed steps and `steps` timed steps (CUDA events around the executor kernels) with
+   zero fields and no source, nshots = 1: the single-field executor, nshots > 1: the
+   multi-shot executor.  *best = base with the fastest candidate's tile_size, renumber and
+   block_threads; best->tile_size = 0 when the untiled chain was fastest.  table (host, may be
+   NULL): rows (tile_size, renumber, block_threads, ms per step), the untiled chain first (0, 0,
+   0, ms); 1 + ntile * (shapes ? 2 : 1) * nblock rows.  Allocates the candidate fields
+   (5 Np ncell nshots doubles) for the call; synchronises. */
+int slt_autotune(slt_mesh mesh, const slt_options* base, int32_t nshots, const int32_t* tile_sizes,
+                 int32_t ntile, int32_t shapes, const int32_t* block_threads, int32_t nblock, int32_t steps,
+                 void* stream, slt_options* best, double* table);
 /* Apply one operator once (for tests): op 0 = A (stress -> velocity rate, device
    in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
    out [ncell][3][Np]).  Runs the untiled loops of that operator. */

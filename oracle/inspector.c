@@ -28,6 +28,14 @@
  *    loop of the chain is projected once more only to detect conflicts.  On conflicts the pairs
  *    become fake edges and inspection restarts from colouring (partition kept).  After
  *    max_rounds restarts the colouring falls back to sequential mode, which cannot conflict.
+ *  - backward tiling (Section 5.1.1: a seed loop in the middle of the chain, tiles grown
+ *    towards the first loop with MIN in place of MAX): with seed loop s > 0, the seed loop is
+ *    projected with MIN, then loops s-1, ..., 0 are tiled and projected in that order with MIN
+ *    (smallest colour wins, earlier candidate kept on ties; no projection: tile 0).  Each
+ *    earlier-loop iteration thereby runs in a tile of colour no larger than every later loop
+ *    (up to s) touching its data.  Then a fresh MAX projection is built from loops 0, ..., s in
+ *    order and loops s+1, ... are tiled forward as above, so they follow every earlier access.
+ *    Conflicts are recorded in both phases with the same rule.  s = 0 is plain forward tiling.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -150,8 +158,14 @@ typedef struct {
   int nloops; const int* loop_set; const int* desc_ptr; const int* desc_map; const char* desc_mode;
 } chain_t;
 
+/* does tile t win over the current tile cur?  MAX (dir > 0) or MIN (dir < 0) colour, strictly */
+static int wins(int dir, const int32_t* col, int32_t t, int32_t cur) {
+  return dir > 0 ? col[t] > col[cur] : col[t] < col[cur];
+}
+
 /* Projection of loop j (Algorithm 2) into phi[] (per set), recording conflicts. */
-static void project(const chain_t* L, int j, const int32_t* sig, int32_t** phi, const int32_t* col, pairvec* C) {
+static void project(const chain_t* L, int j, const int32_t* sig, int32_t** phi, const int32_t* col, pairvec* C,
+                    int dir) {
   int Sj = L->loop_set[j];
   for (int d = L->desc_ptr[j]; d < L->desc_ptr[j + 1]; ++d) {
     int mid = L->desc_map[d];
@@ -160,7 +174,7 @@ static void project(const chain_t* L, int j, const int32_t* sig, int32_t** phi, 
       if (!phi[Sj]) { phi[Sj] = malloc(n * sizeof(int32_t)); for (int64_t e = 0; e < n; ++e) phi[Sj][e] = -1; }
       for (int64_t e = 0; e < n; ++e) {
         int32_t old = phi[Sj][e], t = sig[e];
-        if (old < 0 || col[t] > col[old]) phi[Sj][e] = t;
+        if (old < 0 || wins(dir, col, t, old)) phi[Sj][e] = t;
         else if (t != old && col[t] == col[old]) pv_push(C, old < t ? old : t, old < t ? t : old);
       }
       continue;
@@ -180,7 +194,7 @@ static void project(const chain_t* L, int j, const int32_t* sig, int32_t** phi, 
       for (int64_t k = off[e]; k < off[e + 1]; ++k) {
         int32_t t = sig[val[k]];
         cand[nc++] = t;
-        if (cur < 0 || col[t] > col[cur]) cur = t;
+        if (cur < 0 || wins(dir, col, t, cur)) cur = t;
       }
       phi[S][e] = cur;
       for (int x = 0; x < nc; ++x)
@@ -193,7 +207,8 @@ static void project(const chain_t* L, int j, const int32_t* sig, int32_t** phi, 
 }
 
 /* Tiling function of loop j (Algorithm 3). */
-static void tile_loop(const chain_t* L, int j, int32_t* const* phi, const int32_t* col, int32_t* sig, int64_t* nbottom) {
+static void tile_loop(const chain_t* L, int j, int32_t* const* phi, const int32_t* col, int32_t* sig, int64_t* nbottom,
+                      int dir) {
   int Sj = L->loop_set[j];
   int64_t n = L->set_size[Sj];
   for (int64_t e = 0; e < n; ++e) sig[e] = -1;
@@ -204,7 +219,7 @@ static void tile_loop(const chain_t* L, int j, int32_t* const* phi, const int32_
       if (!p) continue;
       for (int64_t e = 0; e < n; ++e) {
         int32_t t = p[e];
-        if (t >= 0 && (sig[e] < 0 || col[t] > col[sig[e]])) sig[e] = t;
+        if (t >= 0 && (sig[e] < 0 || wins(dir, col, t, sig[e]))) sig[e] = t;
       }
     } else {
       int S = L->map_to[mid], a = L->map_arity[mid];
@@ -214,7 +229,7 @@ static void tile_loop(const chain_t* L, int j, int32_t* const* phi, const int32_
       for (int64_t e = 0; e < n; ++e)
         for (int k = 0; k < a; ++k) {
           int32_t t = p[m[e * a + k]];
-          if (t >= 0 && (sig[e] < 0 || col[t] > col[sig[e]])) sig[e] = t;
+          if (t >= 0 && (sig[e] < 0 || wins(dir, col, t, sig[e]))) sig[e] = t;
         }
     }
   }
@@ -293,33 +308,43 @@ int oracle_inspect(int nsets, const int64_t* set_size,
                    const int32_t* const* map_val,
                    int nloops, const int* loop_set, const int* desc_ptr, const int* desc_map, const char* desc_mode,
                    int ts, int sequential, uint64_t prio_seed, int renumber, const double* seed_xy, int max_rounds,
-                   int32_t* rank, int32_t* colour, int32_t* sigma, int64_t* stats) {
-  if (ts <= 0 || nloops <= 0) return -1;
+                   int seed, int32_t* rank, int32_t* colour, int32_t* sigma, int64_t* stats) {
+  if (ts <= 0 || nloops <= 0 || seed < 0 || seed >= nloops) return -1;
   chain_t L = {nsets, set_size, nmaps, map_from, map_to, map_arity, map_val, nloops, loop_set, desc_ptr, desc_map, desc_mode};
-  int seed_set = loop_set[0];
+  int seed_set = loop_set[seed];
   int64_t nseed = set_size[seed_set];
   int32_t m = (int32_t)((nseed + ts - 1) / ts);
   oracle_seed_rank(nseed, renumber, seed_xy, rank);
   int64_t* sig_off = malloc((nloops + 1) * sizeof(int64_t));
   sig_off[0] = 0;
   for (int j = 0; j < nloops; ++j) sig_off[j + 1] = sig_off[j] + set_size[loop_set[j]];
-  for (int64_t e = 0; e < nseed; ++e) sigma[e] = rank[e] / ts;
+  int32_t* sig_seed = sigma + sig_off[seed];
+  for (int64_t e = 0; e < nseed; ++e) sig_seed[e] = rank[e] / ts;
   pairvec fake = {0};
   int restarts = 0, fell_back = 0;
   int64_t last_conflicts = 0, nbottom = 0;
   for (;;) {
     int64_t* aoff; int32_t* adj;
-    adjacency(&L, seed_set, sigma, m, &fake, &aoff, &adj);
+    adjacency(&L, seed_set, sig_seed, m, &fake, &aoff, &adj);
     colour_tiles(m, aoff, adj, sequential || fell_back, prio_seed, colour);
     free(aoff); free(adj);
     int32_t** phi = calloc(nsets, sizeof(int32_t*));
     pairvec C = {0};
     nbottom = 0;
-    for (int j = 1; j < nloops; ++j) {
-      project(&L, j - 1, sigma + sig_off[j - 1], phi, colour, &C);
-      tile_loop(&L, j, phi, colour, sigma + sig_off[j], &nbottom);
+    if (seed > 0) { /* backward: MIN from the seed loop towards loop 0 */
+      project(&L, seed, sig_seed, phi, colour, &C, -1);
+      for (int j = seed - 1; j >= 0; --j) {
+        tile_loop(&L, j, phi, colour, sigma + sig_off[j], &nbottom, -1);
+        project(&L, j, sigma + sig_off[j], phi, colour, &C, -1);
+      }
+      for (int s = 0; s < nsets; ++s) { free(phi[s]); phi[s] = NULL; }
     }
-    project(&L, nloops - 1, sigma + sig_off[nloops - 1], phi, colour, &C);
+    /* forward: MAX over loops 0..seed, then tile and project the loops after the seed */
+    for (int j = 0; j <= seed; ++j) project(&L, j, sigma + sig_off[j], phi, colour, &C, 1);
+    for (int j = seed + 1; j < nloops; ++j) {
+      tile_loop(&L, j, phi, colour, sigma + sig_off[j], &nbottom, 1);
+      project(&L, j, sigma + sig_off[j], phi, colour, &C, 1);
+    }
     for (int s = 0; s < nsets; ++s) free(phi[s]);
     free(phi);
     pv_sort_unique(&C);

@@ -39,7 +39,7 @@ def _load():
         _lib.oracle_inspect.restype = ctypes.c_int
         _lib.oracle_inspect.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, ctypes.c_int, P, P, P, P,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P, ctypes.c_int,
-                                        P, P, P, P]
+                                        ctypes.c_int, P, P, P, P]
         _lib.oracle_hilbert_index.restype = ctypes.c_uint32
         _lib.oracle_hilbert_index.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]
         _lib.oracle_splitmix64.restype = ctypes.c_uint64
@@ -136,9 +136,11 @@ def _midpoints(X, cells, faces):
     return np.ascontiguousarray((a + b) * 0.5)
 
 
-def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=None, max_rounds=16):
-    """Run Algorithm 1 on `chain` (seed loop = its first loop).  Returns a dict with
-    rank, colour, sigma (list, one tiling function per loop), stats, lists and local maps."""
+def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=None, max_rounds=16, seed=0):
+    """Run Algorithm 1 on `chain` with seed loop `seed` (0: forward tiling from the first loop;
+    > 0: backward tiling, MIN projections, for the loops before it).  Returns a dict with
+    rank, colour, sigma (list, one tiling function per loop), stats, lists and local maps.
+    xy: points of the seed loop's set (renumber)."""
     lib = _load()
     nsets = len(chain.set_size)
     set_size = np.array(chain.set_size, dtype=np.int64)
@@ -150,7 +152,7 @@ def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=No
     dptr = np.cumsum([0] + [len(l[1]) for l in chain.loops]).astype(np.int32)
     dmap = np.array([d[0] for l in chain.loops for d in l[1]], dtype=np.int32)
     dmode = np.frombuffer("".join(d[1] for l in chain.loops for d in l[1]).encode(), dtype=np.uint8).copy()
-    seed_set = chain.loops[0][0]
+    seed_set = chain.loops[seed][0]
     nseed = set_size[seed_set]
     if renumber:
         xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -165,7 +167,7 @@ def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=No
     rc = lib.oracle_inspect(nsets, _ptr(set_size), len(chain.maps), _ptr(mf), _ptr(mt), _ptr(ma),
                             ctypes.cast(mv, ctypes.c_void_p), len(chain.loops), _ptr(ls), _ptr(dptr), _ptr(dmap),
                             _ptr(dmode), int(ts), int(bool(sequential)), ctypes.c_uint64(prio_seed),
-                            int(bool(renumber)), _ptr(xy) if renumber else None, int(max_rounds),
+                            int(bool(renumber)), _ptr(xy) if renumber else None, int(max_rounds), int(seed),
                             _ptr(rank), _ptr(colour), _ptr(sigma), _ptr(stats))
     if rc != 0:
         raise ValueError("oracle_inspect failed (%d)" % rc)

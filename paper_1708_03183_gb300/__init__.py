@@ -26,7 +26,8 @@ I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 class slt_options(ctypes.Structure):
     _fields_ = [("tile_size", I32), ("colouring", I32), ("renumber", I32), ("max_rounds", I32),
                 ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15), ("executor", I32),
-                ("wait_spins", I32), ("block_threads", I32)]
+                ("wait_spins", I32), ("block_threads", I32), ("sub_tile_size", I32 * 16),
+                ("seed_loop", I32 * 16)]
 
 
 _SIGS = {
@@ -53,6 +54,7 @@ _SIGS = {
     "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
     "slt_execute_batched": (ctypes.c_int, [P, P, I32, P, P, P, P, F64, I64, P, P]),
+    "slt_autotune": (ctypes.c_int, [P, P, I32, P, I32, I32, P, I32, I32, P, P, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
@@ -184,6 +186,10 @@ def slt_options_default(**kw):
     o = slt_options()
     _check(lib.slt_options_default(ctypes.byref(o)))
     split = kw.pop("split", ())
+    for i, t in enumerate(kw.pop("sub_tile_size", ())):
+        o.sub_tile_size[i] = t
+    for i, t in enumerate(kw.pop("seed_loop", ())):
+        o.seed_loop[i] = t
     for k, v in kw.items():
         setattr(o, k, v)
     o.nsplit = len(split)
@@ -303,6 +309,21 @@ def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, strea
     if profile:
         return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
                     max_launch_ms=prof[4], min_launch_ms=prof[5])
+
+
+def slt_autotune(mesh, tile_sizes, nshots=1, shapes=False, block_threads=(256,), steps=5, base=None, stream=None,
+                 **kw):
+    """Time the untiled chain and every (tile size, shape, CTA size) candidate on this mesh;
+    returns (best slt_options, table rows (tile_size, renumber, block_threads, ms/step))."""
+    base = base if base is not None else slt_options_default(**kw)
+    ts, tsp = _host(np.asarray(tile_sizes, dtype=np.int32), np.int32)
+    bt, btp = _host(np.asarray(block_threads, dtype=np.int32), np.int32)
+    rows = 1 + len(ts) * (2 if shapes else 1) * len(bt)
+    table = np.zeros((rows, 4), dtype=np.float64)
+    best = slt_options()
+    _check(lib.slt_autotune(mesh.ptr, ctypes.byref(base), int(nshots), tsp, len(ts), int(bool(shapes)), btp, len(bt),
+                            int(steps), _stream(stream), ctypes.byref(best), ctypes.c_void_p(table.ctypes.data)))
+    return best, table
 
 
 def slt_execute_host(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None):

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libslt.so")
-SOURCES = ["api.cpp", "refelem.cpp", "sort.cu", "inspect.cu", "exec.cu", "exec_batched.cu", "adjoint.cu",
-           "noalloc.cu"]
+SOURCES = ["api.cpp", "refelem.cpp", "tune.cpp", "sort.cu", "inspect.cu", "exec.cu", "exec_batched.cu",
+           "adjoint.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

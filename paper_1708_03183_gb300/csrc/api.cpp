@@ -207,6 +207,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   *out = nullptr;
   REQUIRE(!c->loops.empty(), "the chain has no loop");
   REQUIRE(opt->tile_size >= 1, "tile_size must be >= 1");
+  for (int k = 0; k < 16; ++k) REQUIRE(opt->sub_tile_size[k] >= 0, "sub_tile_size entries must be >= 0");
   REQUIRE(opt->colouring == 0 || opt->colouring == 1, "colouring must be 0 or 1");
   REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
   REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
@@ -223,7 +224,11 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   }
   std::vector<int> starts = {0};
   for (int k = 0; k < opt->nsplit; ++k) starts.push_back(opt->split[k]);
-  for (int st : starts) {
+  for (size_t k = 0; k < starts.size(); ++k) {
+    const int end = k + 1 < starts.size() ? starts[k + 1] : nl;
+    REQUIRE(opt->seed_loop[k] >= 0 && opt->seed_loop[k] < end - starts[k],
+            "seed_loop[k] must lie inside sub-chain k");
+    const int st = starts[k] + opt->seed_loop[k];
     int seed_set = c->loops[st].set;
     if (opt->renumber)
       REQUIRE((int64_t)c->points[seed_set].size() == 2 * c->set_size[seed_set],
@@ -690,6 +695,23 @@ int slt_execute_batched(slt_mesh m, slt_schedule sched, int32_t nshots, const do
   m->bsrc.upload(hs.data(), (size_t)nshots * Np, s);
   exec_run_batched(m, sched, nshots, m->bsrc_w.p, m->bsrc.p, v, sigma, ricker, dt, nsteps, s, profile);
   SLT_CUDA(cudaStreamSynchronize(s));
+  API_END
+}
+
+int slt_autotune(slt_mesh m, const slt_options* base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,
+                 int32_t shapes, const int32_t* block_threads, int32_t nblock, int32_t steps, void* stream,
+                 slt_options* best, double* table) {
+  API_BEGIN
+  REQUIRE(m && base && best && tile_sizes && block_threads, "null argument");
+  REQUIRE(nshots >= 1 && nshots <= 4096, "nshots must be in 1..4096");
+  REQUIRE(ntile >= 0 && ntile <= 64 && nblock >= 1 && nblock <= 4, "0..64 tile sizes and 1..4 block sizes");
+  REQUIRE(steps >= 1 && steps <= 1000, "steps must be in 1..1000");
+  for (int i = 0; i < ntile; ++i) REQUIRE(tile_sizes[i] >= 1, "tile sizes must be >= 1");
+  for (int b = 0; b < nblock; ++b)
+    REQUIRE(block_threads[b] == 128 || block_threads[b] == 256, "block_threads must be 128 or 256");
+  if (nshots > 1) REQUIRE(base->executor == 0, "the multi-shot executor runs with executor 0");
+  autotune(m, *base, nshots, tile_sizes, ntile, shapes, block_threads, nblock, steps, as_stream(stream), best,
+           table);
   API_END
 }
 

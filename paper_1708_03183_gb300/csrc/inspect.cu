@@ -148,24 +148,30 @@ __device__ __forceinline__ void push_conflict(int32_t x, int32_t y, int2* buf, i
   if (i < cap) buf[i] = make_int2(x < y ? x : y, x < y ? y : x);
 }
 
+// MAX projection (dir > 0, forward tiling) or MIN (dir < 0, backward tiling): does tile t
+// strictly win over the current tile cur?
+__device__ __forceinline__ bool wins(int dir, const int32_t* __restrict__ col, int32_t t, int32_t cur) {
+  return dir > 0 ? col[t] > col[cur] : col[t] < col[cur];
+}
+
 __global__ void k_project_direct(int64_t n, const int32_t* __restrict__ sig, const int32_t* __restrict__ col,
-                                 int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap) {
+                                 int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap, int dir) {
   GRID_STRIDE(e, n) {
     int32_t old = phi[e], t = sig[e];
-    if (old < 0 || col[t] > col[old]) phi[e] = t;
+    if (old < 0 || wins(dir, col, t, old)) phi[e] = t;
     else if (t != old && col[t] == col[old]) push_conflict(old, t, cbuf, ccnt, cap);
   }
 }
 __global__ void k_project_indirect(int64_t n, const int32_t* __restrict__ ioff, const uint32_t* __restrict__ islot,
                                    int a, const int32_t* __restrict__ sig, const int32_t* __restrict__ col,
-                                   int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap) {
+                                   int32_t* __restrict__ phi, int2* cbuf, int32_t* ccnt, int32_t cap, int dir) {
   GRID_STRIDE(e, n) {
     const int32_t b = ioff[e], d = ioff[e + 1] - b;
     const int32_t old = phi[e];
     int32_t cur = old;
     for (int k = 0; k < d; ++k) {
       int32_t t = sig[islot[b + k] / a];
-      if (cur < 0 || col[t] > col[cur]) cur = t;
+      if (cur < 0 || wins(dir, col, t, cur)) cur = t;
     }
     phi[e] = cur;
     // conflicts: distinct same-colour tiles among {old} + touching iterations' tiles
@@ -188,7 +194,7 @@ struct TileDescs {
   const int32_t* phi[MAXD];  // projection of the target set (null: none yet)
 };
 __global__ void k_tile(int64_t n, TileDescs D, const int32_t* __restrict__ col, int32_t* __restrict__ sig,
-                       int32_t* __restrict__ nbottom) {
+                       int32_t* __restrict__ nbottom, int dir) {
   GRID_STRIDE(e, n) {
     int32_t cur = -1;
     for (int d = 0; d < D.nd; ++d) {
@@ -196,12 +202,12 @@ __global__ void k_tile(int64_t n, TileDescs D, const int32_t* __restrict__ col, 
       if (!p) continue;
       if (!D.map[d]) {
         int32_t t = p[e];
-        if (t >= 0 && (cur < 0 || col[t] > col[cur])) cur = t;
+        if (t >= 0 && (cur < 0 || wins(dir, col, t, cur))) cur = t;
       } else {
         const int a = D.arity[d];
         for (int k = 0; k < a; ++k) {
           int32_t t = p[D.map[d][e * a + k]];
-          if (t >= 0 && (cur < 0 || col[t] > col[cur])) cur = t;
+          if (t >= 0 && (cur < 0 || wins(dir, col, t, cur))) cur = t;
         }
       }
     }
@@ -572,9 +578,12 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     sub.first = bounds[sc];
     sub.last = bounds[sc + 1];
     const int nl = sub.last - sub.first;
-    const int seed_set = c->loops[sub.first].set;
+    const int sl = opt.seed_loop[sc];  // seed loop, relative to the sub-chain's first loop
+    sub.seed = sl;
+    const int seed_set = c->loops[sub.first + sl].set;
     const int64_t nseed = c->set_size[seed_set];
-    const int32_t m = (int32_t)std::max<int64_t>((nseed + opt.tile_size - 1) / opt.tile_size, 1);
+    const int32_t ts = opt.sub_tile_size[sc] > 0 ? opt.sub_tile_size[sc] : opt.tile_size;
+    const int32_t m = (int32_t)std::max<int64_t>((nseed + ts - 1) / ts, 1);
     sub.m = m;
     sub.rank.alloc(std::max<int64_t>(nseed, 1));
     {
@@ -587,7 +596,7 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     }
     sub.sigma.resize(nl);
     for (int jj = 0; jj < nl; ++jj) sub.sigma[jj].alloc(std::max<int64_t>(c->set_size[c->loops[sub.first + jj].set], 1));
-    k_div<<<grid_for(nseed), 256, 0, s>>>(sub.rank.p, nseed, opt.tile_size, sub.sigma[0].p);
+    k_div<<<grid_for(nseed), 256, 0, s>>>(sub.rank.p, nseed, ts, sub.sigma[sl].p);
     SLT_CUDA(cudaGetLastError());
     sub.colour.alloc(m);
     std::vector<DevBuf<int32_t>> phi(nsets);
@@ -596,12 +605,12 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     bool fell_back = false;
     for (;;) {
       DevBuf<int32_t> aoff, adj;
-      build_adjacency(X, sub.first, sub.last, seed_set, sub.sigma[0].p, m, fake, aoff, adj);
+      build_adjacency(X, sub.first, sub.last, seed_set, sub.sigma[sl].p, m, fake, aoff, adj);
       colour_tiles(X, m, opt.colouring == 1 || fell_back, aoff, adj, sub.colour);
       for (int k = 0; k < nsets; ++k) has_phi[k] = false;
       SLT_CUDA(cudaMemsetAsync(ccnt.p, 0, 4, s));
       SLT_CUDA(cudaMemsetAsync(nbottom.p, 0, 4, s));
-      auto project = [&](int jj) {
+      auto project = [&](int jj, int dir) {
         const LoopH& L = c->loops[sub.first + jj];
         for (const DescH& d : L.descs) {
           int S = d.map < 0 ? L.set : c->maps[d.map].to;
@@ -613,17 +622,18 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
           }
           if (n == 0) continue;
           if (d.map < 0) {
-            k_project_direct<<<grid_for(n), 256, 0, s>>>(n, sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap);
+            k_project_direct<<<grid_for(n), 256, 0, s>>>(n, sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap,
+                                                        dir);
           } else {
             const InverseMap& inv = inverse_of(X, d.map);
             k_project_indirect<<<grid_for(n), 256, 0, s>>>(n, inv.off.p, inv.slot.p, c->maps[d.map].arity,
-                                                          sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap);
+                                                          sub.sigma[jj].p, sub.colour.p, phi[S].p, cbuf.p, ccnt.p, cap,
+                                                          dir);
           }
           SLT_CUDA(cudaGetLastError());
         }
       };
-      for (int jj = 1; jj < nl; ++jj) {
-        project(jj - 1);
+      auto tile = [&](int jj, int dir) {
         const LoopH& L = c->loops[sub.first + jj];
         TileDescs D{};
         D.nd = (int)L.descs.size();
@@ -636,10 +646,23 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
           D.phi[d] = has_phi[S] ? phi[S].p : nullptr;
         }
         int64_t n = c->set_size[L.set];
-        if (n) k_tile<<<grid_for(n), 256, 0, s>>>(n, D, sub.colour.p, sub.sigma[jj].p, nbottom.p);
+        if (n) k_tile<<<grid_for(n), 256, 0, s>>>(n, D, sub.colour.p, sub.sigma[jj].p, nbottom.p, dir);
         SLT_CUDA(cudaGetLastError());
+      };
+      if (sl > 0) {  // backward tiling: MIN from the seed loop towards the first loop
+        project(sl, -1);
+        for (int jj = sl - 1; jj >= 0; --jj) {
+          tile(jj, -1);
+          project(jj, -1);
+        }
+        for (int k = 0; k < nsets; ++k) has_phi[k] = false;
       }
-      project(nl - 1);
+      // forward tiling: MAX over the loops up to the seed, then the loops after it
+      for (int jj = 0; jj <= sl; ++jj) project(jj, 1);
+      for (int jj = sl + 1; jj < nl; ++jj) {
+        tile(jj, 1);
+        project(jj, 1);
+      }
       int32_t nconf = 0, nbot = 0;
       SLT_CUDA(cudaMemcpyAsync(&nconf, ccnt.p, 4, cudaMemcpyDeviceToHost, s));
       SLT_CUDA(cudaMemcpyAsync(&nbot, nbottom.p, 4, cudaMemcpyDeviceToHost, s));

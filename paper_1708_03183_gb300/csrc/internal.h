@@ -126,6 +126,7 @@ struct LocalMap {
 };
 struct SubSched {
   int32_t first = 0, last = 0;
+  int32_t seed = 0;  // seed loop relative to first (> 0: backward tiling before it)
   int32_t m = 0, ncolours = 0;
   int64_t restarts = 0, fell_back = 0, conflicts = 0, unprojected = 0;
   DevBuf<int32_t> rank, colour;
@@ -233,6 +234,10 @@ void upload_constants_batched(const RefElem& r);
 void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* d_src_w, const double* d_src,
                       double* v, double* sigma, const double* ricker, double dt, int64_t nsteps, cudaStream_t s,
                       double* profile);
+// tune.cpp
+void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,
+              int32_t shapes, const int32_t* blocks, int32_t nblock, int32_t steps, cudaStream_t s,
+              slt_options* best, double* table);
 // adjoint.cu
 void upload_adjoint_constants(const RefElem& r);
 void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,

@@ -236,3 +236,82 @@ def test_local_maps_address_each_tile_footprint():
                 assert np.all(np.diff(seg) > 0)
                 for k in range(a):
                     assert seg[lmap[e * a + k]] == vals[e * a + k]
+
+
+# ---------------------------------------------------------------- backward tiling (Section 5.1.1)
+
+def test_backward_tiling_worked_line_example():
+    # A path of 8 vertices and 7 edges.  Loop 0 increments both end vertices of every edge,
+    # loop 1 (the seed) writes every vertex, loop 2 reads the end vertices of every edge and
+    # writes the edge.  Seed tiles of 4 vertices, sequential colours: tile 0 = {0..3},
+    # tile 1 = {4..7}.  Backward (MIN): edge (3, 4) touches vertices of tiles 0 and 1 and must
+    # run in the earlier tile 0.  Forward (MAX, over loops 0 and 1): edge (3, 4) reads vertex
+    # 4, last written by tile 1, so loop 2's edge 3 runs in tile 1.
+    ch = I.Chain()
+    E, V = ch.set("edges", 7), ch.set("verts", 8)
+    e2v = ch.map(E, V, 2, np.array([(i, i + 1) for i in range(7)]))
+    ch.loop(E, [(-1, "r"), (e2v, "i")])
+    ch.loop(V, [(-1, "w")])
+    ch.loop(E, [(-1, "w"), (e2v, "r")])
+    s = I.inspect(ch, 4, sequential=True, seed=1)
+    assert list(s["colour"]) == [0, 1]
+    assert list(s["sigma"][1]) == [0, 0, 0, 0, 1, 1, 1, 1]
+    assert list(s["sigma"][0]) == [0, 0, 0, 0, 1, 1, 1]
+    assert list(s["sigma"][2]) == [0, 0, 0, 1, 1, 1, 1]
+    assert s["restarts"] == 0 and s["unprojected"] == 0
+    assert checker.check(ch, s["sigma"], s["colour"]) == []
+    # seeded at loop 0 instead, the edges are partitioned ({0..3}, {4..6}) and vertex 4, which
+    # edge 4 of tile 1 increments, is written by tile 1 in loop 1 (MAX)
+    f = I.inspect(ch, 4, sequential=True)
+    assert list(f["sigma"][0]) == [0, 0, 0, 0, 1, 1, 1]
+    assert list(f["sigma"][1]) == [0, 0, 0, 0, 1, 1, 1, 1]
+
+
+def test_backward_conflicts_are_detected_and_repaired():
+    # the strip of Section 3.2 seeded at its last loop: same-colour tiles grow backwards towards
+    # each other; the MIN rule must see those meetings as conflicts
+    ch = _strip_chain(nedges=10, nloops=4)
+    seen = 0
+    for ps in range(64):
+        first = I.inspect(ch, 2, prio_seed=ps, max_rounds=-1, seed=3)
+        fixed = I.inspect(ch, 2, prio_seed=ps, seed=3)
+        assert checker.check(ch, fixed["sigma"], fixed["colour"]) == []
+        if first["conflicts"]:
+            seen += 1
+            assert checker.check(ch, first["sigma"], first["colour"]) != []
+        else:
+            assert checker.check(ch, first["sigma"], first["colour"]) == []
+    assert seen > 0
+
+
+@pytest.mark.parametrize("ts", [1, 3, 8, 40])
+@pytest.mark.parametrize("seed_loop", [1, 4, 8])
+def test_backward_elastic_schedules_are_legal(ts, seed_loop):
+    m = synth.make_mesh(6, 5, seed=ts + seed_loop)
+    ch, xy, _, _ = I.elastic_chain(m)
+    sub = ch.sub(0, 9)
+    pts = ch.points[sub.loops[seed_loop][0]]
+    s = I.inspect(sub, ts, renumber=True, xy=pts, prio_seed=ts * 11 + seed_loop, seed=seed_loop)
+    assert checker.check(sub, s["sigma"], s["colour"]) == []
+    assert s["rank"].shape == (sub.set_size[sub.loops[seed_loop][0]],)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_backward_tiled_replay_equals_untiled_chain(seed):
+    rng = np.random.default_rng(1000 + seed)
+    ch = _random_chain(rng, int(rng.integers(2, 7)))
+    ts = int(rng.integers(1, 8))
+    sl = int(rng.integers(0, len(ch.loops)))
+    s = I.inspect(ch, ts, prio_seed=seed, seed=sl)
+    assert checker.check(ch, s["sigma"], s["colour"]) == []
+    ref = _replay(ch, [(j, e) for j in range(len(ch.loops)) for e in range(ch.set_size[ch.loops[j][0]])])
+    order = []
+    for c in range(s["ncolours"]):
+        tiles = [t for t in range(s["ntiles"]) if s["colour"][t] == c]
+        rng.shuffle(tiles)
+        for t in tiles:
+            for j, (ptr, its) in enumerate(s["lists"]):
+                order += [(j, int(e)) for e in its[ptr[t]:ptr[t + 1]]]
+    out = _replay(ch, order)
+    for a, b in zip(ref, out):
+        assert np.array_equal(a, b)
