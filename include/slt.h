@@ -83,8 +83,8 @@ int slt_chain_info(slt_chain chain, int32_t* nsets, int32_t* nmaps, int32_t* nlo
  *               colouring = 1: tile t gets colour t.
  *  projection : MAX colour, previous projection kept on ties, all descriptors projected.
  *  conflicts  : two distinct same-colour tiles touching one element; they become fake edges and
- *               the sub-chain is re-coloured, up to max_rounds times, then colouring falls
- *               back to sequential.
+ *               the sub-chain is re-coloured, up to max_rounds times or until the fake edges
+ *               exceed 16 per tile, then colouring falls back to sequential.
  * The output is bit-identical to a sequential execution of the same rules. */
 typedef struct {
   int32_t tile_size;     /* seed tile size ts >= 1 */
@@ -209,7 +209,8 @@ int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const
    Each candidate is inspected with `base` for every other option (split points, executor ...),
    run 2 untimed steps and `steps` timed steps (CUDA events around the executor kernels) with
    zero fields and no source, nshots = 1: the single-field executor, nshots > 1: the
-   multi-shot executor.  *best = base with the fastest candidate's tile_size, renumber and
+   multi-shot executor.  A candidate whose colouring fell back to sequential (its tiles would
+   run one after another) is not timed: its row holds ms = -1.  *best = base with the fastest candidate's tile_size, renumber and
    block_threads; best->tile_size = 0 when the untiled chain was fastest.  table (host, may be
    NULL): rows (tile_size, renumber, block_threads, ms per step), the untiled chain first (0, 0,
    0, ms); 1 + ntile * (shapes ? 2 : 1) * nblock rows.  Allocates the candidate fields

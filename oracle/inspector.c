@@ -27,7 +27,10 @@
  *    iterations' tiles) holds two distinct tiles of equal colour records that pair.  The last
  *    loop of the chain is projected once more only to detect conflicts.  On conflicts the pairs
  *    become fake edges and inspection restarts from colouring (partition kept).  After
- *    max_rounds restarts the colouring falls back to sequential mode, which cannot conflict.
+ *    max_rounds restarts, or as soon as the fake edges number more than 16 per tile (tiles
+ *    scattered over the whole set, e.g. chunks of a random numbering, would otherwise make
+ *    each round denser and slower), the colouring falls back to sequential mode, which cannot
+ *    conflict.
  *  - backward tiling (Section 5.1.1: a seed loop in the middle of the chain, tiles grown
  *    towards the first loop with MIN in place of MAX): with seed loop s > 0, the seed loop is
  *    projected with MIN, then loops s-1, ..., 0 are tiled and projected in that order with MIN
@@ -355,7 +358,7 @@ int oracle_inspect(int nsets, const int64_t* set_size,
     pv_sort_unique(&fake);
     free(C.v);
     ++restarts;
-    if (restarts > max_rounds) fell_back = 1;
+    if (restarts > max_rounds || fake.n > 16 * (int64_t)m) fell_back = 1;
   }
   int32_t nc = 0;
   for (int32_t t = 0; t < m; ++t) if (colour[t] + 1 > nc) nc = colour[t] + 1;

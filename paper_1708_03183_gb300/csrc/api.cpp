@@ -288,7 +288,7 @@ int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc
   int64_t len = 0;
   const LoopH* L = kind >= 2 ? &s->loops[loop] : nullptr;
   switch (kind) {
-    case 0: src = S->rank.p; len = s->set_size[s->loops[S->first].set]; break;
+    case 0: src = S->rank.p; len = s->set_size[s->loops[S->first + S->seed].set]; break;
     case 1: src = S->colour.p; len = S->m; break;
     case 2: src = S->sigma[jj].p; len = s->set_size[L->set]; break;
     case 3: src = S->list_ptr[jj].p; len = S->m + 1; break;

@@ -175,9 +175,12 @@ __device__ __forceinline__ void intB(const Params& a, const Pos& q, int mask, co
   const RefC& R = c_ref[P];
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
   const double ir = a.mat[c];
-  double ax[Np], ay[Np];
+  double ax[Np], ay[Np];  // the increments accumulate onto the current values of U
 #pragma unroll
-  for (int i = 0; i < Np; ++i) ax[i] = ay[i] = 0.0;
+  for (int i = 0; i < Np; ++i) {
+    ax[i] = ld<CG>(&U[(int64_t)i * fs + w]);
+    ay[i] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]);
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!((mask >> f) & 1)) continue;
@@ -207,8 +210,8 @@ __device__ __forceinline__ void intB(const Params& a, const Pos& q, int mask, co
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * fs + w] = ld<CG>(&U[(int64_t)i * fs + w]) + ax[i];
-    U[(int64_t)(Np + i) * fs + w] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]) + ay[i];
+    U[(int64_t)i * fs + w] = ax[i];
+    U[(int64_t)(Np + i) * fs + w] = ay[i];
   }
 }
 
@@ -218,9 +221,12 @@ __device__ __forceinline__ void extB(const Params& a, const Pos& q, int mask, co
   const RefC& R = c_ref[P];
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
   const double ir = a.mat[c];
-  double ax[Np], ay[Np];
+  double ax[Np], ay[Np];  // the increments accumulate onto the current values of U
 #pragma unroll
-  for (int i = 0; i < Np; ++i) ax[i] = ay[i] = 0.0;
+  for (int i = 0; i < Np; ++i) {
+    ax[i] = ld<CG>(&U[(int64_t)i * fs + w]);
+    ay[i] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]);
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!((mask >> f) & 1)) continue;
@@ -245,8 +251,8 @@ __device__ __forceinline__ void extB(const Params& a, const Pos& q, int mask, co
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * fs + w] = ld<CG>(&U[(int64_t)i * fs + w]) + ax[i];
-    U[(int64_t)(Np + i) * fs + w] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]) + ay[i];
+    U[(int64_t)i * fs + w] = ax[i];
+    U[(int64_t)(Np + i) * fs + w] = ay[i];
   }
 }
 
@@ -255,9 +261,13 @@ __device__ __forceinline__ void intD(const Params& a, const Pos& q, int mask, co
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  double exx[Np], eyy[Np], eg[Np];
+  double exx[Np], eyy[Np], eg[Np];  // the increments accumulate onto the current values of E
 #pragma unroll
-  for (int i = 0; i < Np; ++i) exx[i] = eyy[i] = eg[i] = 0.0;
+  for (int i = 0; i < Np; ++i) {
+    exx[i] = ld<CG>(&E[(int64_t)i * fs + w]);
+    eyy[i] = ld<CG>(&E[(int64_t)(Np + i) * fs + w]);
+    eg[i] = ld<CG>(&E[(int64_t)(2 * Np + i) * fs + w]);
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!((mask >> f) & 1)) continue;
@@ -289,9 +299,9 @@ __device__ __forceinline__ void intD(const Params& a, const Pos& q, int mask, co
   }
 #pragma unroll
   for (int i = 0; i < Np; ++i) {
-    E[(int64_t)i * fs + w] = ld<CG>(&E[(int64_t)i * fs + w]) + exx[i];
-    E[(int64_t)(Np + i) * fs + w] = ld<CG>(&E[(int64_t)(Np + i) * fs + w]) + eyy[i];
-    E[(int64_t)(2 * Np + i) * fs + w] = ld<CG>(&E[(int64_t)(2 * Np + i) * fs + w]) + eg[i];
+    E[(int64_t)i * fs + w] = exx[i];
+    E[(int64_t)(Np + i) * fs + w] = eyy[i];
+    E[(int64_t)(2 * Np + i) * fs + w] = eg[i];
   }
 }
 

@@ -262,6 +262,10 @@ __global__ void k_plan_facet_emit(const uint32_t* __restrict__ tile, const uint3
     utile[pos[p]] = tile[p];
   }
 }
+// facet pull items: full masks (7) first, then by decreasing mask
+__global__ void k_mask_key(const int32_t* __restrict__ items, int64_t n, uint32_t* __restrict__ key) {
+  GRID_STRIDE(p, n) key[p] = 7u - (uint32_t)(items[p] & 7);
+}
 __global__ void k_gather_iperm(const int32_t* __restrict__ iperm, const uint32_t* __restrict__ e, int64_t n,
                                int32_t* __restrict__ out) {
   GRID_STRIDE(p, n) out[p] = iperm[e[p]];
@@ -550,6 +554,18 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
       DevBuf<uint32_t> utile(std::max(nu, 1));
       k_plan_facet_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, swid.p, order.p, face, flag.p, pos.p, ns,
                                                      sub.plan_items[jj].p, utile.p);
+      // inside each tile, items with the same face mask side by side (stable, so work-id order
+      // within a mask): a warp then runs only the faces its lanes have
+      {
+        DevBuf<uint32_t> mk(nu), ord;
+        k_mask_key<<<grid_for(nu), 256, 0, s>>>(sub.plan_items[jj].p, nu, mk.p);
+        DevBuf<uint32_t> ut(nu);
+        SLT_CUDA(cudaMemcpyAsync(ut.p, utile.p, (size_t)nu * 4, cudaMemcpyDeviceToDevice, s));
+        sort_by_two(ut, tbits, mk, 3, nu, ord, s);
+        DevBuf<int32_t> sorted(std::max(nu, 1));
+        k_gather_div<<<grid_for(nu), 256, 0, s>>>(sub.plan_items[jj].p, ord.p, nu, 1, (uint32_t*)sorted.p);
+        std::swap(sub.plan_items[jj], sorted);
+      }
       lower_bound_offsets(utile.p, nu, m, sub.plan_ptr[jj].p, s);
     }
     SLT_CUDA(cudaGetLastError());
@@ -680,7 +696,10 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
       all.insert(pairs.begin(), pairs.end());
       fake.assign(all.begin(), all.end());
       ++sub.restarts;
-      if (opt.max_rounds >= 0 && sub.restarts > opt.max_rounds) fell_back = true;
+      // sequential colouring after max_rounds restarts, or once the fake edges exceed 16 per
+      // tile (scattered tiles would make every further round denser and slower)
+      if ((opt.max_rounds >= 0 && sub.restarts > opt.max_rounds) || (int64_t)fake.size() > 16 * (int64_t)m)
+        fell_back = true;
     }
     sub.fell_back = fell_back;
     {

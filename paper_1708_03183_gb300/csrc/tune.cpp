@@ -81,7 +81,12 @@ void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t
         int rc = slt_inspect(chain, &o, s, &sched);
         if (rc != SLT_OK) fail(rc, "autotune: inspection of a candidate failed");
         std::unique_ptr<slt_schedule_s, int (*)(slt_schedule)> guard(sched, slt_schedule_destroy);
-        sched->mesh = m;
+        bool serial = false;
+        for (const SubSched& sub : sched->subs) serial |= sub.fell_back != 0 && sub.m > 1;
+        if (serial && o.colouring == 0) {
+          put(o.tile_size, o.renumber, o.block_threads, -1.0);
+          continue;
+        }
         double ms = time_candidate(m, sched, nshots, f, src_w.p, src.p, steps, warm, s);
         put(o.tile_size, o.renumber, o.block_threads, ms);
         if (ms < best_ms) {

@@ -39,8 +39,9 @@ def test_autotune_table_and_tuned_run(lib, nshots):
     assert tuple(table[0, :3]) == (0, 0, 0)
     assert {(int(r[0]), int(r[1]), int(r[2])) for r in table[1:]} == {
         (t, r, b) for t in (32, 96) for r in (0, 1) for b in (128, 256)}
-    assert np.all(table[:, 3] > 0)
-    k = int(np.argmin(table[:, 3]))
+    assert np.all((table[:, 3] > 0) | (table[:, 3] == -1))
+    ms = np.where(table[:, 3] > 0, table[:, 3], np.inf)
+    k = int(np.argmin(ms))
     assert best.tile_size == int(table[k, 0])
     if best.tile_size:
         assert (best.renumber, best.block_threads) == (int(table[k, 1]), int(table[k, 2]))
