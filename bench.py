@@ -251,6 +251,49 @@ def batched_timing(slt, synth, args, barrier):
             "fp64_frac": fl / (res[best]["ms_per_step"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "runs": res}
 
 
+def multi_timing(slt, synth, args, barrier):
+    """Many uneven meshes: 16 meshes with cell counts log-uniform in [20k, 400k] (seed 4), degree
+    1 + (i mod 3), each sparse-tiled (ts 256, dataflow executor) and advanced `--multi-steps`
+    steps as one group (one combined ready queue per degree) against the same meshes run one
+    after another with slt_execute."""
+    import torch
+    K, W = args.multi_steps, 3
+    cfgs = synth.multi_configs(16, nsteps=W + K)
+    meshes, scheds, fields = [], [], []
+    for c in cfgs:
+        m = c["mesh"]
+        mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], c["p"], c["rho"], c["lam"], c["mu"], c["src"])
+        meshes.append(mesh)
+        scheds.append(slt.slt_inspect(slt.slt_mesh_chain(mesh), tile_size=256, split=(9,)))
+        nc, Np = m["cell2vert"].shape[0], (c["p"] + 1) * (c["p"] + 2) // 2
+        fields.append((torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda"),
+                       torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda"),
+                       torch.tensor(c["ricker"], device="cuda")))
+    units = sum(5 * ((c["p"] + 1) * (c["p"] + 2) // 2) * c["mesh"]["cell2vert"].shape[0] for c in cfgs)
+    vs, ss, rs = [list(x) for x in zip(*fields)]
+    dts = [c["dt"] for c in cfgs]
+    grp = slt.slt_group_create(meshes, scheds)
+    slt.slt_group_execute(grp, vs, ss, rs, dts, W)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    slt.slt_group_execute(grp, vs, ss, [r[W:] for r in rs], dts, K)
+    e1.record()
+    barrier()
+    t_many = e0.elapsed_time(e1)
+    e0.record()
+    for mesh, sc, (v, s, r), dt in zip(meshes, scheds, fields, dts):
+        slt.slt_execute(mesh, sc, v, s, r[W:], dt, K)
+    e1.record()
+    barrier()
+    t_seq = e0.elapsed_time(e1)
+    ncs = [c["mesh"]["cell2vert"].shape[0] for c in cfgs]
+    return {"workload": "16 meshes, %d..%d cells (%d in all), degrees 1-3, ts 256, %d steps" % (
+                min(ncs), max(ncs), sum(ncs), K),
+            "value": units * K / (t_many * 1e-3), "unit": "dof-updates/s", "ms_per_step": t_many / K,
+            "one_after_another_ms_per_step": t_seq / K, "overlap_speedup": t_seq / t_many}
+
+
 def workload_name(args):
     import synth
     c = synth.CONFIGS[args.config]
@@ -279,6 +322,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--multi-steps", type=int, default=20)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64, 128])
@@ -420,6 +465,9 @@ def main():
         del sched, mesh
         torch.cuda.empty_cache()
         out["batched"] = batched_timing(slt, synth, args, barrier)
+    if not args.no_multi:
+        torch.cuda.empty_cache()
+        out["multi"] = multi_timing(slt, synth, args, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, d = oracle_sample_rate(args.config, 10)

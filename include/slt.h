@@ -41,6 +41,7 @@ typedef struct slt_chain_s* slt_chain;       /* loop chain description (host) */
 typedef struct slt_schedule_s* slt_schedule; /* inspector output (device resident) */
 typedef struct slt_mesh_s* slt_mesh;         /* DG elastic mesh (device resident) */
 typedef struct slt_receivers_s* slt_receivers; /* point receivers on a mesh */
+typedef struct slt_group_s* slt_group;       /* meshes advanced together (device resident) */
 
 const char* slt_last_error(void);
 /* Library version and the compute capability it was built for (e.g. 103). */
@@ -203,6 +204,25 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
 int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const double* src_xy, double* v,
                         double* sigma, const double* ricker, double dt, int64_t nsteps, void* stream,
                         double* profile);
+/* Several independent meshes (uneven sizes, any degrees) advanced together: the batched form
+   over uneven meshes.  slt_group_create binds meshes[i] to scheds[i] (NULL = untiled; a schedule
+   must come from its mesh's chain; a mesh may appear once; n in 1..256) and builds, for each
+   degree, one combined dataflow plan over the tiled meshes of that degree: the disjoint union
+   of their dependency graphs, tiles renumbered by a base per mesh.  slt_group_execute advances
+   every mesh i by nsteps steps on its own device fields v[i], sigma[i] (caller layout), with
+   source series ricker[i] (device, may be NULL) and time step dt[i] (host arrays of length n):
+   one persistent kernel per degree runs the tiles of all its meshes from one ready queue
+   (per-mesh dependency counters, no barrier across meshes), the degrees one after the other;
+   untiled meshes run side by side on private streams forked from `stream`.  Synchronises;
+   SLT_ERR_TIMEOUT if a wait gave up.  The meshes and schedules must outlive the group.
+   slt_execute_many = create, execute once, destroy. */
+int slt_group_create(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, slt_group* out);
+int slt_group_destroy(slt_group group);
+int slt_group_execute(slt_group group, double* const* v, double* const* sigma, const double* const* ricker,
+                      const double* dt, int64_t nsteps, void* stream);
+int slt_execute_many(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, double* const* v,
+                     double* const* sigma, const double* const* ricker, const double* dt, int64_t nsteps,
+                     void* stream);
 /* Autotuner over tile size, tile shape and CTA size (Section 7.3 searches them empirically).
    Times the untiled chain, then every candidate (tile_sizes[i], renumber, block_threads[b]):
    renumber 1 (Hilbert tiles) only, or also 0 (chunks of the mesh numbering) when shapes != 0.

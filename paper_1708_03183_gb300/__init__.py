@@ -55,6 +55,10 @@ _SIGS = {
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
     "slt_execute_batched": (ctypes.c_int, [P, P, I32, P, P, P, P, F64, I64, P, P]),
     "slt_autotune": (ctypes.c_int, [P, P, I32, P, I32, I32, P, I32, I32, P, P, P]),
+    "slt_execute_many": (ctypes.c_int, [I32, P, P, P, P, P, P, I64, P]),
+    "slt_group_create": (ctypes.c_int, [I32, P, P, P]),
+    "slt_group_destroy": (ctypes.c_int, [P]),
+    "slt_group_execute": (ctypes.c_int, [P, P, P, P, P, I64, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
@@ -309,6 +313,54 @@ def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, strea
     if profile:
         return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
                     max_launch_ms=prof[4], min_launch_ms=prof[5])
+
+
+def _group_args(meshes, vs, sigmas, rickers, dts, nsteps):
+    n = len(meshes)
+    if not (len(vs) == len(sigmas) == len(rickers) == len(dts) == n):
+        raise ValueError("one field pair, source series and dt per mesh")
+    for m, v, s_, r in zip(meshes, vs, sigmas, rickers):
+        _check_fields(m, v, s_, r, nsteps)
+    arr = lambda xs: (ctypes.c_void_p * n)(*xs)
+    return (arr([_dev(v, "float64") for v in vs]), arr([_dev(x, "float64") for x in sigmas]),
+            arr([_dev(r, "float64") for r in rickers]), (ctypes.c_double * n)(*[float(d) for d in dts]))
+
+
+class Group(_Handle):
+    _destroy = "slt_group_destroy"
+
+
+def slt_group_create(meshes, scheds):
+    """Bind meshes to their schedules (None = untiled) for joint execution."""
+    n = len(meshes)
+    if len(scheds) != n:
+        raise ValueError("one schedule (or None) per mesh")
+    arr = lambda xs: (ctypes.c_void_p * n)(*xs)
+    h = ctypes.c_void_p()
+    _check(lib.slt_group_create(n, arr([m.ptr for m in meshes]), arr([s.ptr if s is not None else None for s in scheds]),
+                                ctypes.byref(h)))
+    g = Group(h)
+    g.meshes = list(meshes)   # keep the members alive as long as the group
+    g.scheds = list(scheds)
+    return g
+
+
+def slt_group_execute(group, vs, sigmas, rickers, dts, nsteps, stream=None):
+    """Advance every mesh of the group; per mesh: v [ncell, 2, Np] and sigma [ncell, 3, Np] CUDA
+    float64 tensors updated in place, ricker (CUDA float64 or None), dt."""
+    v, s_, r, d = _group_args(group.meshes, vs, sigmas, rickers, dts, nsteps)
+    _check(lib.slt_group_execute(group.ptr, v, s_, r, d, int(nsteps), _stream(stream)))
+
+
+def slt_execute_many(meshes, scheds, vs, sigmas, rickers, dts, nsteps, stream=None):
+    """One-off joint execution (slt_group_create + slt_group_execute)."""
+    n = len(meshes)
+    if len(scheds) != n:
+        raise ValueError("one schedule (or None) per mesh")
+    v, s_, r, d = _group_args(meshes, vs, sigmas, rickers, dts, nsteps)
+    arr = lambda xs: (ctypes.c_void_p * n)(*xs)
+    _check(lib.slt_execute_many(n, arr([m.ptr for m in meshes]), arr([s.ptr if s is not None else None for s in scheds]),
+                                v, s_, r, d, int(nsteps), _stream(stream)))
 
 
 def slt_autotune(mesh, tile_sizes, nshots=1, shapes=False, block_threads=(256,), steps=5, base=None, stream=None,

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <set>
 #include <vector>
 
 #include "internal.h"
@@ -696,6 +697,57 @@ int slt_execute_batched(slt_mesh m, slt_schedule sched, int32_t nshots, const do
   exec_run_batched(m, sched, nshots, m->bsrc_w.p, m->bsrc.p, v, sigma, ricker, dt, nsteps, s, profile);
   SLT_CUDA(cudaStreamSynchronize(s));
   API_END
+}
+
+int slt_group_create(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, slt_group* out) {
+  API_BEGIN
+  REQUIRE(out, "null argument");
+  *out = nullptr;
+  REQUIRE(n >= 1 && n <= 256, "n must be in 1..256");
+  REQUIRE(meshes && scheds, "null argument");
+  std::set<slt_mesh> seen;
+  std::unique_ptr<slt_group_s> g(new slt_group_s());
+  for (int32_t i = 0; i < n; ++i) {
+    REQUIRE(meshes[i], "null mesh");
+    REQUIRE(seen.insert(meshes[i]).second, "a mesh appears twice");
+    if (scheds[i] && scheds[i]->mesh != meshes[i])
+      fail(SLT_ERR_STATE, "a schedule was not inspected on its mesh's chain");
+    g->meshes.push_back(meshes[i]);
+    g->scheds.push_back(scheds[i]);
+  }
+  group_build(g.get());
+  *out = g.release();
+  API_END
+}
+
+int slt_group_destroy(slt_group g) {
+  API_BEGIN
+  delete g;
+  API_END
+}
+
+int slt_group_execute(slt_group g, double* const* v, double* const* sigma, const double* const* ricker,
+                      const double* dt, int64_t nsteps, void* stream) {
+  API_BEGIN
+  REQUIRE(g && v && sigma && ricker && dt, "null argument");
+  REQUIRE(nsteps >= 0, "nsteps must be >= 0");
+  for (size_t i = 0; i < g->meshes.size(); ++i) {
+    REQUIRE(v[i] && sigma[i], "null field");
+    REQUIRE(std::isfinite(dt[i]), "dt must be finite");
+  }
+  group_run(g, v, sigma, ricker, dt, nsteps, as_stream(stream));
+  API_END
+}
+
+int slt_execute_many(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, double* const* v,
+                     double* const* sigma, const double* const* ricker, const double* dt, int64_t nsteps,
+                     void* stream) {
+  slt_group g = nullptr;
+  int rc = slt_group_create(n, meshes, scheds, &g);
+  if (rc != SLT_OK) return rc;
+  rc = slt_group_execute(g, v, sigma, ricker, dt, nsteps, stream);
+  slt_group_destroy(g);
+  return rc;
 }
 
 int slt_autotune(slt_mesh m, const slt_options* base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,

@@ -23,12 +23,10 @@ constexpr bool DF_L2_ONLY = true;
 // in order and run whatever node was published there, so no CTA waits on one particular
 // dependency while other work is ready.  Every claimed slot is eventually filled (the graph is
 // acyclic and every published node is run), so the bounded waits only end early on an error.
-struct DF {
+struct DFQ {
   long long total;                // nodes = nsteps * G
   long long nsteps;
-  int32_t G;                      // tiles over all sub-chains
-  int32_t cum[17];                // global tile id base of each sub-chain (cum[k] + local id)
-  int32_t first[16], last[16];    // loop range of each sub-chain
+  int32_t G;                      // tiles over all sub-chains (of all meshes of a group)
   const int32_t* succ_ptr;        // [G + 1]
   const int32_t* succ;            // (global tile << 1) | 1 when the successor is the next step's node
   int32_t* pending;               // [nsteps * G] unfinished dependencies of each node
@@ -37,6 +35,22 @@ struct DF {
   unsigned long long* tail;       // next slot to publish
   int32_t* err;                   // set when a wait gave up
   long long max_spins;
+};
+// one mesh: sub-chain table by value
+struct DF {
+  DFQ q;
+  int32_t cum[17];                // global tile id base of each sub-chain (cum[k] + local id)
+  int32_t first[16], last[16];    // loop range of each sub-chain
+};
+// a group of meshes of one degree: (mesh, sub-chain) table and per-mesh parameters in memory
+struct DFM {
+  DFQ q;
+  int32_t K;                      // (mesh, sub-chain) entries
+  const int32_t* cum;             // [K + 1] global tile id base of each entry
+  const int32_t* first;           // [K] loop range of each entry
+  const int32_t* last;
+  const int32_t* mesh_of;         // [K] index into params
+  const Params* params;           // per mesh of the group
 };
 
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {
@@ -53,84 +67,128 @@ __device__ __forceinline__ int atom_add_acq_rel(int32_t* p, int v) {
   return old;
 }
 
-__global__ void k_df_init(DF df, const int32_t* __restrict__ indeg0, const int32_t* __restrict__ indeg) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < df.total;
+__global__ void k_df_init(DFQ q, const int32_t* __restrict__ indeg0, const int32_t* __restrict__ indeg) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < q.total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int g = (int)(i % df.G);
-    df.pending[i] = i < df.G ? indeg0[g] : indeg[g];
-    df.queue[i] = -1;
+    const int g = (int)(i % q.G);
+    q.pending[i] = i < q.G ? indeg0[g] : indeg[g];
+    q.queue[i] = -1;
   }
 }
-__global__ void k_df_seed(DF df, const int32_t* __restrict__ indeg0) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < df.G; g += gridDim.x * blockDim.x)
+__global__ void k_df_seed(DFQ q, const int32_t* __restrict__ indeg0) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < q.G; g += gridDim.x * blockDim.x)
     if (indeg0[g] == 0) {
-      unsigned long long j = atomicAdd(df.tail, 1ull);
-      df.queue[j] = g;
+      unsigned long long j = atomicAdd(q.tail, 1ull);
+      q.queue[j] = g;
     }
+}
+
+// Thread 0: claim the next slot and wait (bounded) until a node is published there.  Returns
+// the node, or -1 when the run is over or a wait gave up (the error flag is then set).
+__device__ __forceinline__ long long df_take(const DFQ& q) {
+  const unsigned long long slot = atomicAdd(q.head, 1ull);
+  if ((long long)slot >= q.total || ld_acquire(q.err)) return -1;
+  long long node;
+  long long spins = 0;
+  while ((node = ld_acquire(&q.queue[slot])) < 0) {
+    if (++spins > q.max_spins || ld_acquire(q.err)) {
+      atomicExch(q.err, 1);
+      return -1;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  return node;
+}
+
+// Thread 0, after the CTA finished node (st, g): release its successors.
+__device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
+  __threadfence();
+  for (int i = q.succ_ptr[g]; i < q.succ_ptr[g + 1]; ++i) {
+    const int e = q.succ[i];
+    const long long s2 = st + (e & 1);
+    if (s2 >= q.nsteps) continue;
+    const long long n2 = s2 * q.G + (e >> 1);
+    if (atom_add_acq_rel(&q.pending[n2], -1) == 1) {
+      const unsigned long long j = atomicAdd(q.tail, 1ull);
+      st_release(&q.queue[j], (int32_t)n2);
+    }
+  }
+}
+
+// One tile's slice of the loops [first, last) at step st, loops separated by CTA barriers.
+template <int P, int BS, bool BATCH>
+__device__ __forceinline__ void run_tile(const Params& a, int first, int last, int t, long long st) {
+  for (int J = first; J < last; ++J) {
+    const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
+    const int32_t* items = a.plan_items[J];
+    if constexpr (BATCH) {  // every item for every shot, consecutive threads on consecutive shots
+      const int64_t nwork = (int64_t)(e - b) * a.S;
+      for (int64_t i = threadIdx.x; i < nwork; i += BS)
+        run_loop<P, DF_L2_ONLY, true>(a, J, items[b + i / a.S], st, (int)(i % a.S));
+    } else {
+      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
+    }
+    __syncthreads();
+  }
 }
 
 template <int P, int BS, bool BATCH>
 __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Params a, DF df) {
   __shared__ long long s_node;
-  __shared__ int s_stop;
   for (;;) {
-    if (threadIdx.x == 0) {
-      int stop = 0;
-      long long node = -1;
-      const unsigned long long slot = atomicAdd(df.head, 1ull);
-      if ((long long)slot >= df.total || ld_acquire(df.err)) {
-        stop = 1;
-      } else {
-        long long spins = 0;
-        while ((node = ld_acquire(&df.queue[slot])) < 0) {
-          if (++spins > df.max_spins || ld_acquire(df.err)) {
-            atomicExch(df.err, 1);
-            stop = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-        __threadfence();
-      }
-      s_node = node;
-      s_stop = stop;
-    }
+    if (threadIdx.x == 0) s_node = df_take(df.q);
     __syncthreads();
-    if (s_stop) return;
     const long long node = s_node;
-    const long long st = node / df.G;
-    const int g = (int)(node % df.G);
+    if (node < 0) return;
+    const long long st = node / df.q.G;
+    const int g = (int)(node % df.q.G);
     int k = 0;
     while (g >= df.cum[k + 1]) ++k;
-    const int t = g - df.cum[k];
-    for (int J = df.first[k]; J < df.last[k]; ++J) {
-      const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
-      const int32_t* items = a.plan_items[J];
-      if constexpr (BATCH) {  // every item for every shot, consecutive threads on consecutive shots
-        const int64_t nwork = (int64_t)(e - b) * a.S;
-        for (int64_t i = threadIdx.x; i < nwork; i += BS)
-          run_loop<P, DF_L2_ONLY, true>(a, J, items[b + i / a.S], st, (int)(i % a.S));
-      } else {
-        for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      __threadfence();
-      for (int q = df.succ_ptr[g]; q < df.succ_ptr[g + 1]; ++q) {
-        const int e = df.succ[q];
-        const long long s2 = st + (e & 1);
-        if (s2 >= df.nsteps) continue;
-        const long long n2 = s2 * df.G + (e >> 1);
-        if (atom_add_acq_rel(&df.pending[n2], -1) == 1) {
-          const unsigned long long j = atomicAdd(df.tail, 1ull);
-          st_release(&df.queue[j], (int32_t)n2);
-        }
-      }
-    }
+    run_tile<P, BS, BATCH>(a, df.first[k], df.last[k], g - df.cum[k], st);
+    if (threadIdx.x == 0) df_publish(df.q, g, st);
   }
 }
 
+// The same executor over the tiles of several meshes of one degree: one queue, per-mesh
+// dependency counters (the graphs are disjoint), each tile run with its mesh's parameters
+// (copied to shared memory when the CTA takes the tile).
+template <int P, int BS>
+__global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group(DFM df) {
+  __shared__ long long s_node;
+  __shared__ Params sp;
+  static_assert(sizeof(Params) % 4 == 0, "Params is copied as 32-bit words");
+  for (;;) {
+    if (threadIdx.x == 0) s_node = df_take(df.q);
+    __syncthreads();
+    const long long node = s_node;
+    if (node < 0) return;
+    const long long st = node / df.q.G;
+    const int g = (int)(node % df.q.G);
+    int lo = 0, hi = df.K;  // entry k with cum[k] <= g < cum[k + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (df.cum[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    const int k = lo;
+    const int32_t* src = reinterpret_cast<const int32_t*>(&df.params[df.mesh_of[k]]);
+    int32_t* dst = reinterpret_cast<int32_t*>(&sp);
+    for (int i = threadIdx.x; i < (int)(sizeof(Params) / 4); i += BS) dst[i] = src[i];
+    __syncthreads();
+    run_tile<P, BS, false>(sp, df.first[k], df.last[k], g - df.cum[k], st);
+    if (threadIdx.x == 0) df_publish(df.q, g, st);
+  }
+}
+
+// Error flag of the schedule's last dataflow run (synchronises s): SLT_ERR_TIMEOUT if a wait
+// gave up.
+inline void dataflow_check(::slt_schedule_s* sched, cudaStream_t s) {
+  int32_t herr = 0;
+  SLT_CUDA(cudaMemcpyAsync(&herr, sched->df.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  if (herr) slt::fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
+}
 
 // Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin` / `rec_end` bracket
 // the three kernels for the caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
@@ -138,11 +196,12 @@ template <int P, bool BATCH, class RB, class RE>
 void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end) {
   slt::DataflowPlan& D = sched->df;
   DF df{};
-  df.G = D.cum.back();
-  df.nsteps = nsteps;
-  df.total = (long long)nsteps * df.G;
-  if (df.total == 0) return;
-  if (df.total >= (1ll << 31)) slt::fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
+  DFQ& q = df.q;
+  q.G = D.cum.back();
+  q.nsteps = nsteps;
+  q.total = (long long)nsteps * q.G;
+  if (q.total == 0) return;
+  if (q.total >= (1ll << 31)) slt::fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
   for (size_t k = 0; k < D.cum.size(); ++k) df.cum[k] = D.cum[k];
   for (size_t k = 0; k < sched->subs.size(); ++k) {
     const slt::SubSched& sub = sched->subs[k];
@@ -153,24 +212,24 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
       a.plan_items[j] = sub.plan_items[j - sub.first].p;
     }
   }
-  if (D.pending.n < (size_t)df.total) {
-    D.pending.alloc(df.total);
-    D.queue.alloc(df.total);
+  if (D.pending.n < (size_t)q.total) {
+    D.pending.alloc(q.total);
+    D.queue.alloc(q.total);
   }
-  df.succ_ptr = D.succ_ptr.p;
-  df.succ = D.succ.p;
-  df.pending = D.pending.p;
-  df.queue = D.queue.p;
-  df.head = D.head.p;
-  df.tail = D.head.p + 1;
-  df.err = D.err.p;
-  df.max_spins = sched->wait_spins;
+  q.succ_ptr = D.succ_ptr.p;
+  q.succ = D.succ.p;
+  q.pending = D.pending.p;
+  q.queue = D.queue.p;
+  q.head = D.head.p;
+  q.tail = D.head.p + 1;
+  q.err = D.err.p;
+  q.max_spins = sched->wait_spins;
   SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
   SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
   rec_begin();
-  k_df_init<<<(unsigned)std::min<long long>((df.total + 255) / 256, 152 * 16), 256, 0, s>>>(df, D.indeg0.p,
+  k_df_init<<<(unsigned)std::min<long long>((q.total + 255) / 256, 152 * 16), 256, 0, s>>>(q, D.indeg0.p,
                                                                                           D.indeg.p);
-  k_df_seed<<<(df.G + 255) / 256, 256, 0, s>>>(df, D.indeg0.p);
+  k_df_seed<<<(q.G + 255) / 256, 256, 0, s>>>(q, D.indeg0.p);
   SLT_CUDA(cudaGetLastError());
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
@@ -179,13 +238,10 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
   if (bs == 128) SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 128, BATCH>, 128, 0));
   else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 256, BATCH>, 256, 0));
   long long grid = (long long)nsm * std::max(per, 1);
-  if (grid > df.total) grid = df.total;
+  if (grid > q.total) grid = q.total;
   if (bs == 128) k_dataflow<P, 128, BATCH><<<(unsigned)grid, 128, 0, s>>>(a, df);
   else k_dataflow<P, 256, BATCH><<<(unsigned)grid, 256, 0, s>>>(a, df);
   rec_end();
   SLT_CUDA(cudaGetLastError());
-  int32_t herr = 0;
-  SLT_CUDA(cudaMemcpyAsync(&herr, D.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  SLT_CUDA(cudaStreamSynchronize(s));
-  if (herr) slt::fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
+  dataflow_check(sched, s);
 }

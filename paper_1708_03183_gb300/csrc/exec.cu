@@ -24,6 +24,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -52,8 +54,11 @@ __global__ void __launch_bounds__(128) k_loop(Params a) {
     if (!mask) return;
     item = (int32_t)((w << 3) | mask);
   }
-  run_loop<P, false, false>(a, J, item, a.step);
+  run_loop<P, false, false>(a, J, item, (J == 16 && a.step_dev) ? (int64_t)*a.step_dev : a.step);
 }
+
+// advances the device step counter at the end of a graph-captured step
+__global__ void k_step_inc(long long* step) { *step += 1; }
 
 #include "dataflow.cuh"
 
@@ -211,10 +216,56 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
   launch_dataflow<P, false>(sched, a, nsteps, s, [&] { g_rec.begin(0, s, 3); }, [&] { g_rec.end(s); });
 }
 
+// The untiled step as one CUDA graph (17 loop kernels and the step-counter increment), captured
+// on the mesh's private stream and launched nsteps times on s: the host issues one launch per
+// step instead of seventeen.  The step index comes from a device counter the graph advances.
+template <int P>
+void run_untiled_graph(slt_mesh m, Params a, int64_t nsteps, cudaStream_t s) {
+  if (!m->step_dev.p) m->step_dev.alloc(1);
+  if (!m->capture) SLT_CUDA(cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking));
+  a.step_dev = m->step_dev.p;
+  SLT_CUDA(cudaMemsetAsync(m->step_dev.p, 0, sizeof(long long), s));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const bool rec = g_rec.on;
+  g_rec.on = false;  // no events inside the capture
+  SLT_CUDA(cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal));
+  try {
+    launch_untiled_range<P>(a, 0, 17, m->capture);
+    k_step_inc<<<1, 1, 0, m->capture>>>(m->step_dev.p);
+    SLT_CUDA(cudaGetLastError());
+  } catch (...) {
+    cudaStreamEndCapture(m->capture, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    g_rec.on = rec;
+    throw;
+  }
+  SLT_CUDA(cudaStreamEndCapture(m->capture, &graph));
+  g_rec.on = rec;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  SLT_CUDA(e);
+  cudaError_t err = cudaSuccess;
+  for (int64_t step = 0; step < nsteps && err == cudaSuccess; ++step) {
+    g_rec.begin(0, s, 18);
+    err = cudaGraphLaunch(exec, s);
+    g_rec.end(s);
+  }
+  cudaGraphExecDestroy(exec);
+  SLT_CUDA(err);
+}
+
+// untiled steps of at least this count run as a captured graph
+constexpr int64_t kGraphMinSteps = 4;
+
 template <int P>
 void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
   if (sched && sched->executor == 0) {
     run_dataflow<P>(sched, a, nsteps, s);
+    return;
+  }
+  if (!sched && nsteps >= kGraphMinSteps) {
+    run_untiled_graph<P>(m, a, nsteps, s);
     return;
   }
   for (int64_t step = 0; step < nsteps; ++step) {
@@ -306,6 +357,208 @@ void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const do
   SLT_CUDA(cudaGetLastError());
   g_rec.finish(s, profile);
   g_rec = Recorder();
+}
+
+// ------------------------------------------------------------------ groups of meshes
+// The combined plan of each degree: tiles of member i renumbered by base_i (the sum of the
+// earlier members' tiles), successor lists shifted accordingly; dependency counts copied.
+void group_build(slt_group grp) {
+  std::map<int, std::vector<int32_t>> by_degree;
+  for (size_t i = 0; i < grp->meshes.size(); ++i) {
+    slt_schedule sc = grp->scheds[i];
+    if (sc && sc->executor == 0) by_degree[grp->meshes[i]->p].push_back((int32_t)i);
+    else grp->untiled.push_back((int32_t)i);  // untiled, or the colour-phase executor
+  }
+  for (auto& kv : by_degree) {
+    grp->parts.emplace_back();
+    slt_group_s::Part& part = grp->parts.back();
+    part.p = kv.first;
+    part.members = kv.second;
+    std::vector<int32_t> cum, first, last, mesh_of, succ_ptr, succ, indeg0, indeg;
+    int32_t base = 0;
+    part.block = grp->scheds[part.members[0]]->block;
+    for (size_t mi = 0; mi < part.members.size(); ++mi) {
+      slt_schedule sc = grp->scheds[part.members[mi]];
+      if (sc->block != part.block) fail(SLT_ERR_UNSUPPORTED, "tiled meshes of one degree need one block size");
+      part.wait_spins = std::max<int64_t>(part.wait_spins, sc->wait_spins);
+      const DataflowPlan& D = sc->df;
+      const int32_t G = D.cum.back();
+      for (size_t k = 0; k < sc->subs.size(); ++k) {
+        cum.push_back(base + D.cum[k]);
+        first.push_back(sc->subs[k].first);
+        last.push_back(sc->subs[k].last);
+        mesh_of.push_back((int32_t)mi);
+      }
+      std::vector<int32_t> sp = D.succ_ptr.download(nullptr, G + 1);
+      std::vector<int32_t> sv = D.succ.download(nullptr, std::max<int32_t>(sp[G], 1));
+      std::vector<int32_t> i0 = D.indeg0.download(nullptr, G), i1 = D.indeg.download(nullptr, G);
+      const int32_t off = succ_ptr.empty() ? 0 : (int32_t)succ.size();
+      for (int32_t g = 0; g < G; ++g) succ_ptr.push_back(off + sp[g]);
+      for (int32_t q = 0; q < sp[G]; ++q) succ.push_back((((sv[q] >> 1) + base) << 1) | (sv[q] & 1));
+      indeg0.insert(indeg0.end(), i0.begin(), i0.end());
+      indeg.insert(indeg.end(), i1.begin(), i1.end());
+      base += G;
+    }
+    cum.push_back(base);
+    succ_ptr.push_back((int32_t)succ.size());
+    part.G = base;
+    part.K = (int32_t)first.size();
+    auto up = [](DevBuf<int32_t>& d, const std::vector<int32_t>& h) {
+      d.alloc(std::max<size_t>(h.size(), 1));
+      d.upload(h.data(), h.size(), nullptr);
+    };
+    up(part.cum, cum);
+    up(part.first, first);
+    up(part.last, last);
+    up(part.mesh_of, mesh_of);
+    up(part.succ_ptr, succ_ptr);
+    up(part.succ, succ);
+    up(part.indeg0, indeg0);
+    up(part.indeg, indeg);
+    part.err.alloc(1);
+    part.head.alloc(2);
+    part.params.alloc(part.members.size() * sizeof(Params));
+  }
+  SLT_CUDA(cudaDeviceSynchronize());
+}
+
+namespace {
+
+template <int P>
+void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) {
+  DFM df{};
+  DFQ& q = df.q;
+  q.G = part.G;
+  q.nsteps = nsteps;
+  q.total = (long long)nsteps * part.G;
+  if (q.total == 0) return;
+  if (q.total >= (1ll << 31)) fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
+  if (part.pending.n < (size_t)q.total) {
+    part.pending.alloc(q.total);
+    part.queue.alloc(q.total);
+  }
+  q.succ_ptr = part.succ_ptr.p;
+  q.succ = part.succ.p;
+  q.pending = part.pending.p;
+  q.queue = part.queue.p;
+  q.head = part.head.p;
+  q.tail = part.head.p + 1;
+  q.err = part.err.p;
+  q.max_spins = part.wait_spins;
+  df.K = part.K;
+  df.cum = part.cum.p;
+  df.first = part.first.p;
+  df.last = part.last.p;
+  df.mesh_of = part.mesh_of.p;
+  df.params = reinterpret_cast<const Params*>(part.params.p);
+  SLT_CUDA(cudaMemsetAsync(part.head.p, 0, 2 * sizeof(unsigned long long), s));
+  SLT_CUDA(cudaMemsetAsync(part.err.p, 0, sizeof(int32_t), s));
+  k_df_init<<<(unsigned)std::min<long long>((q.total + 255) / 256, 152 * 16), 256, 0, s>>>(q, part.indeg0.p,
+                                                                                         part.indeg.p);
+  k_df_seed<<<(q.G + 255) / 256, 256, 0, s>>>(q, part.indeg0.p);
+  SLT_CUDA(cudaGetLastError());
+  int dev = 0, nsm = 0, per = 0;
+  SLT_CUDA(cudaGetDevice(&dev));
+  SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (part.block == 128) SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow_group<P, 128>, 128, 0));
+  else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow_group<P, 256>, 256, 0));
+  long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
+  if (part.block == 128) k_dataflow_group<P, 128><<<(unsigned)grid, 128, 0, s>>>(df);
+  else k_dataflow_group<P, 256><<<(unsigned)grid, 256, 0, s>>>(df);
+  SLT_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// One call: every member's fields into its work layout; each degree's tiled members as one
+// persistent kernel over their combined queue (one degree after the other, each with the whole
+// GPU); the untiled members side by side on private streams; fields back.
+void group_run(slt_group grp, double* const* v, double* const* sigma, const double* const* ricker, const double* dt,
+               int64_t nsteps, cudaStream_t s) {
+  g_rec = Recorder();
+  const int32_t n = (int32_t)grp->meshes.size();
+  std::vector<Params> prm(n);
+  for (int32_t i = 0; i < n; ++i) {
+    slt_mesh m = grp->meshes[i];
+    Params& a = prm[i];
+    a = make_params(m);
+    a.dt = dt[i];
+    a.c24 = dt[i] * dt[i] / 24.0;
+    a.ricker = ricker[i];
+    if (slt_schedule sc = grp->scheds[i])
+      for (auto& sub : sc->subs)
+        for (int j = sub.first; j < sub.last; ++j) {
+          a.plan_ptr[j] = sub.plan_ptr[j - sub.first].p;
+          a.plan_items[j] = sub.plan_items[j - sub.first].p;
+        }
+    int g;
+    io_grid(m->nc, g);
+    k_to_work<<<g, 256, 0, s>>>(v[i], 2 * m->Np, m->d_perm.p, m->nc, m->ncp, a.buf[B_V]);
+    k_to_work<<<g, 256, 0, s>>>(sigma[i], 3 * m->Np, m->d_perm.p, m->nc, m->ncp, a.buf[B_S]);
+  }
+  SLT_CUDA(cudaGetLastError());
+  for (auto& part : grp->parts) {
+    std::vector<Params> pp;
+    for (int32_t i : part.members) pp.push_back(prm[i]);
+    SLT_CUDA(cudaMemcpyAsync(part.params.p, pp.data(), pp.size() * sizeof(Params), cudaMemcpyHostToDevice, s));
+    switch (part.p) {
+      case 1: launch_group_part<1>(part, nsteps, s); break;
+      case 2: launch_group_part<2>(part, nsteps, s); break;
+      case 3: launch_group_part<3>(part, nsteps, s); break;
+      case 4: launch_group_part<4>(part, nsteps, s); break;
+    }
+  }
+  if (!grp->untiled.empty()) {  // fork, run side by side, join
+    const size_t u = grp->untiled.size();
+    std::vector<cudaStream_t> st(u, nullptr);
+    std::vector<cudaEvent_t> ev(u + 1, nullptr);
+    auto cleanup = [&] {
+      for (cudaStream_t x : st)
+        if (x) {
+          cudaStreamSynchronize(x);
+          cudaStreamDestroy(x);
+        }
+      for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    };
+    try {
+      SLT_CUDA(cudaEventCreateWithFlags(&ev[u], cudaEventDisableTiming));
+      SLT_CUDA(cudaEventRecord(ev[u], s));
+      for (size_t k = 0; k < u; ++k) {
+        const int32_t i = grp->untiled[k];
+        slt_mesh m = grp->meshes[i];
+        SLT_CUDA(cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking));
+        SLT_CUDA(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+        SLT_CUDA(cudaStreamWaitEvent(st[k], ev[u], 0));
+        switch (m->p) {
+          case 1: run_steps<1>(m, grp->scheds[i], prm[i], nsteps, st[k]); break;
+          case 2: run_steps<2>(m, grp->scheds[i], prm[i], nsteps, st[k]); break;
+          case 3: run_steps<3>(m, grp->scheds[i], prm[i], nsteps, st[k]); break;
+          case 4: run_steps<4>(m, grp->scheds[i], prm[i], nsteps, st[k]); break;
+        }
+        SLT_CUDA(cudaEventRecord(ev[k], st[k]));
+      }
+      for (size_t k = 0; k < u; ++k) SLT_CUDA(cudaStreamWaitEvent(s, ev[k], 0));
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    slt_mesh m = grp->meshes[i];
+    int g;
+    io_grid(m->nc, g);
+    k_from_work<<<g, 256, 0, s>>>(prm[i].buf[B_V], 2 * m->Np, m->d_perm.p, m->nc, m->ncp, v[i]);
+    k_from_work<<<g, 256, 0, s>>>(prm[i].buf[B_S], 3 * m->Np, m->d_perm.p, m->nc, m->ncp, sigma[i]);
+  }
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(s));
+  for (auto& part : grp->parts) {
+    int32_t herr = 0;
+    SLT_CUDA(cudaMemcpy(&herr, part.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr && nsteps > 0) fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
+  }
 }
 
 void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t s) {

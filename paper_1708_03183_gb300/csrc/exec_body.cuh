@@ -55,6 +55,7 @@ struct Params {
   const double* src;                // [Np] source coefficients (one field)
   int32_t src_w;                    // source cell (one field)
   int64_t step;
+  const long long* step_dev;        // if set, the step index is read here (graph-captured steps)
   double dt, c24;
   const int32_t* plan_ptr[17];
   const int32_t* plan_items[17];

@@ -208,6 +208,31 @@ struct slt_mesh_s {
   slt::DevBuf<double> adet;         // |det J| per cell, work order
   slt::DevBuf<double> work_b, bsrc;  // multi-shot work fields; per-shot source coefficients
   slt::DevBuf<int32_t> bsrc_w;       // per-shot source cell (work id, -1 = none)
+  slt::DevBuf<long long> step_dev;   // step counter read by graph-captured untiled steps
+  cudaStream_t capture = nullptr;    // private stream the untiled step is captured on
+  ~slt_mesh_s() {
+    if (capture) cudaStreamDestroy(capture);
+  }
+};
+
+// A group of meshes advanced together.  The tiled meshes of each degree share one combined
+// dataflow plan (the disjoint union of their dependency graphs, tiles renumbered by a base per
+// mesh), run by one persistent kernel; untiled meshes run side by side on private streams.
+struct slt_group_s {
+  struct Part {
+    int p = 0, block = 256;
+    int64_t wait_spins = 0;
+    std::vector<int32_t> members;            // indices into meshes
+    int32_t G = 0, K = 0;
+    slt::DevBuf<int32_t> cum, first, last, mesh_of;   // (mesh, sub-chain) table
+    slt::DevBuf<int32_t> succ_ptr, succ, indeg0, indeg, pending, queue, err;
+    slt::DevBuf<unsigned long long> head;
+    slt::DevBuf<unsigned char> params;       // per member: the executor's parameter block
+  };
+  std::vector<slt_mesh> meshes;
+  std::vector<slt_schedule> scheds;
+  std::vector<Part> parts;
+  std::vector<int32_t> untiled;
 };
 
 struct slt_receivers_s {
@@ -222,6 +247,9 @@ namespace slt {
 void upload_constants(const RefElem& r);
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile = nullptr);
+void group_build(slt_group g);
+void group_run(slt_group g, double* const* v, double* const* sigma, const double* const* ricker, const double* dt,
+               int64_t nsteps, cudaStream_t s);
 void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t s);
 // time steps on the mesh's work buffers V, S (work layout), source series entry step0 + n
 void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, double dt, int64_t step0,

@@ -9,7 +9,7 @@ element matrices, schedules) independently from these arrays.
 from .mesh import make_mesh, cell_centroids_for_materials
 from .materials import homogeneous, layered, perturb
 from .source import ricker_series, cfl_dt
-from .configs import CONFIGS, build_config
+from .configs import CONFIGS, build_config, multi_configs
 
 __all__ = ["make_mesh", "cell_centroids_for_materials", "homogeneous", "layered", "perturb",
-           "ricker_series", "cfl_dt", "CONFIGS", "build_config"]
+           "ricker_series", "cfl_dt", "CONFIGS", "build_config", "multi_configs"]

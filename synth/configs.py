@@ -51,3 +51,16 @@ def build_config(name, **override):
     return dict(name=name, mesh=mesh, p=c["p"], rho=rho, lam=lam, mu=mu, dt=dt,
                 ricker=ricker, src=np.array(c["src"], dtype=np.float64), nsteps=c["nsteps"],
                 ts=c["ts"])
+
+
+def multi_configs(n=16, seed=4, lo=20000, hi=400000, nsteps=20):
+    """Uneven meshes for the many-mesh form: cell counts log-uniform in [lo, hi] (seeded), degree
+    1 + (i mod 3), each an nx x nx/2 grid of squares on 300x150 with its own mesh seed, layered
+    material and the large workload's source."""
+    rng = np.random.default_rng(seed)
+    ncells = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+    out = []
+    for i, nc in enumerate(ncells):
+        nx = max(int(round(np.sqrt(nc))), 4)
+        out.append(build_config("large", nx=nx, ny=max(nx // 2, 2), p=1 + i % 3, nsteps=nsteps, seed=100 + i))
+    return out
