@@ -1,7 +1,8 @@
 """Benchmark: dof-updates/s of the sparse-tiled DG elastic time step on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config large] [--tile-size 1024] [--no-untiled] [--no-cpu]
+                    [--config large] [--tile-size 256] [--block 256] [--no-untiled] [--no-cpu]
+                    [--no-adjoint] [--no-batched] [--no-multi] [--no-p4]
 
 One step = one full time step of the DG elastic chain (seventeen loops: velocity sub-chain then
 stress sub-chain) over the whole mesh.  The default workload is the 1000x500-square mesh of the
@@ -10,7 +11,9 @@ with the seed tile size given, fusion scheme {velocity, stress}.  Inputs are res
 larger than L2 (no flush needed).  The JSON line carries the tiled throughput (value), the plain
 untiled chain on the same GPU, the inspection time, the roofline of the dominant kernel, the
 oracle timed on the host cores (cpu_baseline) and an end-to-end number through the C ABI with
-host buffers (e2e).  --impl reference times the oracle itself on the host cores.
+host buffers (e2e).  Further keys time the other configurations of the same path: the P4
+mesh (p4), the seismogram gradient (adjoint), 64 shots at once (batched) and 16 uneven meshes
+as one group (multi).  --impl reference times the oracle itself on the host cores.
 
 Multi-GPU: the workload does not shard in this library; --gpus N runs N independent replicas
 (one per rank, launched by torchrun) and reports the sum over ranks / the slowest rank's time.
@@ -44,7 +47,7 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("exec.cu", "internal.h"):
+    for f in ("exec.cu", "exec_body.cuh", "dataflow.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_1708_03183_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -294,6 +297,33 @@ def multi_timing(slt, synth, args, barrier):
             "one_after_another_ms_per_step": t_seq / K, "overlap_speedup": t_seq / t_many}
 
 
+def p4_timing(slt, synth, args, barrier):
+    """The high-order configuration: 500x250 squares on 300x150 (250k cells), P4, layered,
+    sparse-tiled at ts 256 with 384-thread tiles (the autotuner's pick) against the untiled
+    chain, `--p4-steps` steps each."""
+    import torch
+    K, W = args.p4_steps, 3
+    cfg = synth.build_config("p4", nsteps=W + K)
+    m = cfg["mesh"]
+    nc, Np = m["cell2vert"].shape[0], 15
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], 4, cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
+    sched = slt.slt_inspect(slt.slt_mesh_chain(mesh), tile_size=256, split=(9,), block_threads=384)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    flops = slt.slt_mesh_cost(mesh)["flops_per_step"]
+    out = {"workload": "p4: 500x250 squares on 300x150 (%d cells), DG P4 FP64, layered, %d steps" % (nc, K)}
+    for name, sc in (("tiled_ts256_bt384", sched), ("untiled", None)):
+        v = torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda")
+        s = torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda")
+        slt.slt_execute(mesh, sc, v, s, rk, cfg["dt"], W)
+        barrier()
+        prof = slt.slt_execute_profiled(mesh, sc, v, s, rk[W:], cfg["dt"], K)
+        barrier()
+        ms = prof["chain_ms"] / K
+        out[name] = {"ms_per_step": ms, "value": 5 * Np * nc / (ms * 1e-3),
+                     "fp64_frac": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    return out
+
+
 def workload_name(args):
     import synth
     c = synth.CONFIGS[args.config]
@@ -314,7 +344,7 @@ def main():
     ap.add_argument("--config", default="large")
     ap.add_argument("--tile-size", type=int, default=256)
     ap.add_argument("--executor", type=int, default=0, help="0 dataflow (persistent), 1 colour phases")
-    ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128 or 256)")
+    ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128, 256 or 384)")
     ap.add_argument("--no-untiled", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -323,6 +353,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-p4", action="store_true")
+    ap.add_argument("--p4-steps", type=int, default=20)
     ap.add_argument("--multi-steps", type=int, default=20)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10)
@@ -459,6 +491,8 @@ def main():
                   "h2d_bytes_per_step": 5 * Np * nc * 8 + 8, "d2h_bytes_per_step": 5 * Np * nc * 8,
                   "steps": args.e2e_steps}
 
+    if not args.no_p4:
+        out["p4"] = p4_timing(slt, synth, args, barrier)
     if not args.no_adjoint:
         out["adjoint"] = adjoint_timing(slt, synth, args, barrier)
     if not args.no_batched:

@@ -97,7 +97,7 @@ typedef struct {
   int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
   int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
-  int32_t block_threads; /* threads per tile CTA: 128 or 256 (0 = 256) */
+  int32_t block_threads; /* threads per tile CTA: 128, 256 or 384 (0 = 256) */
   int32_t sub_tile_size[16]; /* seed tile size of sub-chain k (0 = tile_size): a fusion scheme
                                 with its own tile size per sub-chain (Section 7.2) */
   int32_t seed_loop[16];     /* seed loop of sub-chain k, counted from its first loop (0 = the

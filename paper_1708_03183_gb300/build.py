@@ -60,7 +60,9 @@ def build(verbose=False, force=False):
         obj = os.path.join(OUT, src + ".o")
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + common
         if src.endswith(".cu"):
-            cmd += ["-Xptxas", "-v"] if verbose else []
+            # device code of a translation unit compiled by parallel jobs (the executor's many
+            # template instances dominate the build)
+            cmd += ["--split-compile=0"] + (["-Xptxas", "-v"] if verbose else [])
         else:
             cmd += ["-x", "c++"]
         r = subprocess.run(cmd, capture_output=True, text=True)

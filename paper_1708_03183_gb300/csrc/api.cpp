@@ -215,8 +215,9 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
   REQUIRE(opt->executor == 0 || opt->executor == 1, "executor must be 0 or 1");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
-  REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256,
-          "block_threads must be 0, 128 or 256");
+  REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
+              opt->block_threads == 384,
+          "block_threads must be 0, 128, 256 or 384");
   const int nl = (int)c->loops.size();
   int prev = 0;
   for (int k = 0; k < opt->nsplit; ++k) {
@@ -760,7 +761,8 @@ int slt_autotune(slt_mesh m, const slt_options* base, int32_t nshots, const int3
   REQUIRE(steps >= 1 && steps <= 1000, "steps must be in 1..1000");
   for (int i = 0; i < ntile; ++i) REQUIRE(tile_sizes[i] >= 1, "tile sizes must be >= 1");
   for (int b = 0; b < nblock; ++b)
-    REQUIRE(block_threads[b] == 128 || block_threads[b] == 256, "block_threads must be 128 or 256");
+    REQUIRE(block_threads[b] == 128 || block_threads[b] == 256 || block_threads[b] == 384,
+            "block_threads must be 128, 256 or 384");
   if (nshots > 1) REQUIRE(base->executor == 0, "the multi-shot executor runs with executor 0");
   autotune(m, *base, nshots, tile_sizes, ntile, shapes, block_threads, nblock, steps, as_stream(stream), best,
            table);

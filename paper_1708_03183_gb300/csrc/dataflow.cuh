@@ -235,12 +235,14 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int bs = sched->block;
-  if (bs == 128) SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 128, BATCH>, 128, 0));
-  else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<P, 256, BATCH>, 256, 0));
-  long long grid = (long long)nsm * std::max(per, 1);
-  if (grid > q.total) grid = q.total;
-  if (bs == 128) k_dataflow<P, 128, BATCH><<<(unsigned)grid, 128, 0, s>>>(a, df);
-  else k_dataflow<P, 256, BATCH><<<(unsigned)grid, 256, 0, s>>>(a, df);
+  auto launch = [&](auto kernel, int threads) {
+    SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
+    const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
+    kernel<<<(unsigned)grid, threads, 0, s>>>(a, df);
+  };
+  if (bs == 128) launch(k_dataflow<P, 128, BATCH>, 128);
+  else if (bs == 384) launch(k_dataflow<P, 384, BATCH>, 384);
+  else launch(k_dataflow<P, 256, BATCH>, 256);
   rec_end();
   SLT_CUDA(cudaGetLastError());
   dataflow_check(sched, s);

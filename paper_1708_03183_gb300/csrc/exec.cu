@@ -201,6 +201,7 @@ void launch_tiled_colour(const Params& a, int first, int last, const int32_t* ti
   if (ntiles <= 0) return;
   g_rec.begin(0, s);
   if (bs == 128) k_tiled<P, 128><<<ntiles, 128, 0, s>>>(a, first, last, tiles);
+  else if (bs == 384) k_tiled<P, 384><<<ntiles, 384, 0, s>>>(a, first, last, tiles);
   else k_tiled<P, 256><<<ntiles, 256, 0, s>>>(a, first, last, tiles);
   g_rec.end(s);
   SLT_CUDA(cudaGetLastError());
@@ -460,11 +461,14 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  if (part.block == 128) SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow_group<P, 128>, 128, 0));
-  else SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow_group<P, 256>, 256, 0));
-  long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
-  if (part.block == 128) k_dataflow_group<P, 128><<<(unsigned)grid, 128, 0, s>>>(df);
-  else k_dataflow_group<P, 256><<<(unsigned)grid, 256, 0, s>>>(df);
+  auto launch = [&](auto kernel, int threads) {
+    SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
+    const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
+    kernel<<<(unsigned)grid, threads, 0, s>>>(df);
+  };
+  if (part.block == 128) launch(k_dataflow_group<P, 128>, 128);
+  else if (part.block == 384) launch(k_dataflow_group<P, 384>, 384);
+  else launch(k_dataflow_group<P, 256>, 256);
   SLT_CUDA(cudaGetLastError());
 }
 

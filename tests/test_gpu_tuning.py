@@ -89,3 +89,4 @@ def test_backward_tiling_on_the_p2_workload(lib):
     v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
     vo, so = oracle_run("small_p2")
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL
+
