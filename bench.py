@@ -53,16 +53,17 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel source; otherwise None."""
+def ncu_traffic(kernel, workload, steps):
+    """DRAM bytes (read + write) of one launch of `kernel` running `steps` time steps, from the
+    committed ncu capture (bytes per step of a launch of that kernel on the same workload), if it
+    was taken on the current kernel source; otherwise None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d[kernel][workload]
         if e.get("source_hash") != kernel_hash():
             return None
-        return float(e["bytes_per_launch"])
+        return float(e["bytes_per_step"]) * steps
     except Exception:
         return None
 
@@ -435,7 +436,7 @@ def main():
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
     kname = ("k_dataflow<%d,%d>" if args.executor == 0 else "k_tiled<%d,%d>") % (p, args.block)
-    traffic = ncu_traffic(kname, args.config)
+    traffic = ncu_traffic(kname, args.config, args.steps) if args.scale == 1 and args.block == 256 else None
     tiled_bytes = cost["tiled_bytes_per_step"]
 
     out = {"metric": METRIC, "value": value, "unit": "dof-updates/s", "n_gpus": world, "steps": args.steps,

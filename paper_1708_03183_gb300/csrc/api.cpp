@@ -495,8 +495,8 @@ int slt_mesh_cost(slt_mesh m, double cost[4]) {
   const double cell = volB + 2 * hookeB + 3 * volD + 8 * Np + 19 * Np + 2;
   const double side = (4 + 9 * Nfp + 4 * Np * Nfp) + (3 + 2 * Nfp + Np * (4 * Nfp + 6));
   const double ext = 3 + 6 * Nfp + 4 * Np * Nfp;
-  cost[0] = m->nc * cell + 2.0 * m->nfi * 3 * side + m->cells_int * 15 * Np + m->nfe * 3 * ext +
-            m->cells_ext * 6 * Np;
+  // (the facet loops accumulate onto the loaded field values: no separate increment adds)
+  cost[0] = m->nc * cell + 2.0 * m->nfi * 3 * side + m->nfe * 3 * ext;
   cost[1] = m->nc * (80 * Np + 140);
   cost[2] = m->nc * (808 * Np + 808);
   cost[3] = nnz;

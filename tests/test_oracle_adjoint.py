@@ -39,7 +39,7 @@ def test_adjoint_gradient_matches_central_differences(p):
     assert J > 0
     assert np.isclose(J, _J(m, p, model, dt, nsteps, ricker, xs, rec, data), rtol=1e-14)
     rng = np.random.default_rng(7)
-    for _ in range(3):
+    for _ in range(10):   # ten seeded random directions
         d = [a * rng.uniform(-1, 1, a.shape) for a in model]
         # central differences: truncation error O(eps^2) (1e-9 here), far below a wrong term
         eps = 1e-5
