@@ -103,6 +103,10 @@ def test_host_buffers_and_no_source(lib):
     lib.slt_execute_host(mesh, sched, v, s, np.ascontiguousarray(cfg["ricker"]), cfg["dt"], 5)
     vd, sd = gpu_run(lib, cfg, nsteps=5, sched=sched, mesh=mesh)
     assert np.array_equal(v, vd) and np.array_equal(s, sd)
+    # page-locked buffers (the end-to-end bench's case) give the same bits
+    vp, sp = torch.tensor(cfg["v0"]).pin_memory(), torch.tensor(cfg["s0"]).pin_memory()
+    lib.slt_execute_host(mesh, sched, vp, sp, np.ascontiguousarray(cfg["ricker"]), cfg["dt"], 5)
+    assert np.array_equal(vp.numpy(), vd) and np.array_equal(sp.numpy(), sd)
     # no source: compare with the oracle without the source term
     dg = ElasticDG(cfg["mesh"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"])
     vo, so = dg.run(cfg["v0"].copy(), cfg["s0"].copy(), cfg["dt"], 4)
