@@ -36,6 +36,22 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA
 HBM_FALLBACK_GBS = 6800.0
 
 
+def max_over_ranks(dist, x, device):
+    """The largest value of x over all ranks (x itself when there is no process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Weak scaling: every rank processes units_per_rank units; the job takes the slowest rank's
+    time `seconds`."""
+    return units_per_rank * world / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -421,15 +437,11 @@ def main():
             prof = slt.slt_execute_profiled(mesh, schedule, v, s, ricker[W:], cfg["dt"], K)
             e1.record(stream)
             barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, e0.elapsed_time(e1), "cuda")
         return ms, prof, clk.summary()
 
     ms, prof, clocks = timed(sched, args.steps, args.warmup)
-    value = units_per_step * args.steps * world / (ms * 1e-3)
+    value = whole_job_rate(units_per_step * args.steps, world, ms * 1e-3)
     cost = slt.slt_mesh_cost(mesh)   # the library's own count of the work its kernels do
     flops = cost["flops_per_step"]
     kern_s = prof["chain_ms"] * 1e-3
@@ -466,7 +478,8 @@ def main():
         ums, uprof, uclk = timed(None, K, args.warmup)
         ub = cost["untiled_bytes_per_step"]
         uk = uprof["chain_ms"] * 1e-3
-        out["untiled"] = {"value": units_per_step * K * world / (ums * 1e-3), "ms_per_step": ums / K, "steps": K,
+        out["untiled"] = {"value": whole_job_rate(units_per_step * K, world, ums * 1e-3), "ms_per_step": ums / K,
+                          "steps": K,
                           "roofline_frac_fp64": flops * K / uk / 1e12 / FP64_PEAK_TFLOPS,
                           "hbm_frac": ub * K / uk / 1e9 / hbm_peak, "algorithmic_bytes_per_step": ub,
                           "launches_per_step": uprof["chain_launches"] / K, "clocks": uclk}
@@ -483,12 +496,8 @@ def main():
     for n in range(args.e2e_steps):
         slt.slt_execute_host(mesh, sched, hv, hs, hr[n:n + 1], cfg["dt"], 1)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    out["e2e"] = {"value": units_per_step * args.e2e_steps * world / e2e_s, "unit": "dof-updates/s",
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    out["e2e"] = {"value": whole_job_rate(units_per_step * args.e2e_steps, world, e2e_s), "unit": "dof-updates/s",
                   "h2d_bytes_per_step": 5 * Np * nc * 8 + 8, "d2h_bytes_per_step": 5 * Np * nc * 8,
                   "steps": args.e2e_steps}
 
