@@ -3,8 +3,9 @@
 // anonymous namespace.
 #pragma once
 
-// No register cap: forcing 24 warps per SM (80 registers at p = 2) made the tiled kernels slower
-// (their loads are latency bound and more resident tiles overflow L2); one CTA is the minimum.
+// Resident tiles per SM: at p <= 2, 768 threads (three 256-thread tiles, 80 registers; the
+// heaviest loop bodies spill a little, which measured faster than two tiles at 128 registers);
+// at p >= 3 the loop bodies need their registers and one tile is the minimum.
 template <int P, int BS>
 constexpr int tile_min_blocks() {
   return P <= 2 ? 768 / BS : 1;

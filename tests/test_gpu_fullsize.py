@@ -1,7 +1,8 @@
-"""Parity at the full size of the benchmarked workload (1.0M cells, P2), in the launch
-configuration bench.py times (dataflow executor, ts 256, fusion {velocity, stress}): the whole
-schedule bit for bit against the oracle inspector, and two time steps of the tiled chain against
-the oracle's untiled chain.  Minutes of oracle time: marked slow."""
+"""Parity at the full sizes of the benchmarked workloads, in the launch configurations bench.py
+times: the large P2 mesh (1.0M cells; the whole schedule bit for bit against the oracle inspector
+and two tiled steps against the oracle's chain), the P4 mesh, sampled shots of the 64-shot
+batched run, sampled members of the 16-mesh group, and the adjoint workload's gradient against
+central differences of its misfit.  Minutes of oracle time: marked slow."""
 import numpy as np
 import pytest
 
@@ -51,3 +52,113 @@ def test_fullsize_tiled_steps_match_oracle(lib, large):
     dg = ElasticDG(cfg["mesh"], 2, cfg["rho"], cfg["lam"], cfg["mu"])
     vo, so = dg.run(v0, s0, cfg["dt"], 2, cfg["ricker"], cfg["src"])
     assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
+
+
+def test_fullsize_p4_tiled_steps_match_oracle(lib):
+    # the P4 configuration in the bench's launch configuration: ts 256, 384-thread tiles
+    import torch
+    cfg = synth.build_config("p4")
+    mesh = gpu_mesh(lib, cfg)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=256, split=(9,), block_threads=384)
+    nc = cfg["mesh"]["cell2vert"].shape[0]
+    rng = np.random.default_rng(19)
+    v0 = 1e-3 * rng.standard_normal((nc, 2, 15))
+    s0 = 1e-3 * rng.standard_normal((nc, 3, 15))
+    v, s = torch.tensor(v0, device="cuda"), torch.tensor(s0, device="cuda")
+    lib.slt_execute(mesh, sched, v, s, torch.tensor(cfg["ricker"], device="cuda"), cfg["dt"], 2)
+    dg = ElasticDG(cfg["mesh"], 4, cfg["rho"], cfg["lam"], cfg["mu"])
+    vo, so = dg.run(v0, s0, cfg["dt"], 2, cfg["ricker"], cfg["src"])
+    assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
+
+
+@pytest.mark.parametrize("ts", [0, 16])
+def test_fullsize_batched_sampled_shots_match_oracle(lib, ts):
+    # the bench's batched configuration: 708x354 squares (501k cells), P2, 64 shots on the 8x8
+    # grid, untiled and dataflow at ts 16; two sampled shots start from seeded random fields
+    import torch
+    cfg = synth.build_config("large", nx=708, ny=354)
+    mesh = gpu_mesh(lib, cfg)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=(9,)) if ts else None
+    nc = cfg["mesh"]["cell2vert"].shape[0]
+    S = 64
+    grid = np.array([((i + 0.5) * 300.0 / 8, (j + 0.5) * 150.0 / 8) for j in range(8) for i in range(8)])
+    v = torch.zeros((nc, 2, 6, S), dtype=torch.float64, device="cuda")
+    s = torch.zeros((nc, 3, 6, S), dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(23)
+    init = {}
+    for k in (5, 58):
+        init[k] = (1e-3 * rng.standard_normal((nc, 2, 6)), 1e-3 * rng.standard_normal((nc, 3, 6)))
+        v[..., k] = torch.tensor(init[k][0], device="cuda")
+        s[..., k] = torch.tensor(init[k][1], device="cuda")
+    lib.slt_execute_batched(mesh, sched, grid, v, s, torch.tensor(cfg["ricker"], device="cuda"), cfg["dt"], 2)
+    dg = ElasticDG(cfg["mesh"], 2, cfg["rho"], cfg["lam"], cfg["mu"])
+    for k, (v0, s0) in init.items():
+        vo, so = dg.run(v0.copy(), s0.copy(), cfg["dt"], 2, cfg["ricker"], grid[k])
+        assert rel_l2(v[..., k].cpu().numpy(), vo) < TOL and rel_l2(s[..., k].cpu().numpy(), so) < TOL, k
+    # every other shot started from rest: only its own source has acted
+    assert torch.isfinite(s).all() and float(s[..., 0].abs().max()) > 0
+
+
+def test_fullsize_group_of_uneven_meshes(lib):
+    # the bench's 16 uneven meshes (2.75M cells, P1-P3, ts 256) as one group for 2 steps: sampled
+    # members equal their single-mesh runs bit for bit; the smallest equals the oracle
+    import torch
+    cfgs = synth.multi_configs(16, nsteps=2)
+    meshes = [gpu_mesh(lib, c) for c in cfgs]
+    scheds = [lib.slt_inspect(lib.slt_mesh_chain(m), tile_size=256, split=(9,)) for m in meshes]
+    rng = np.random.default_rng(29)
+    init = []
+    for c in cfgs:
+        nc, Np = c["mesh"]["cell2vert"].shape[0], (c["p"] + 1) * (c["p"] + 2) // 2
+        init.append((1e-3 * rng.standard_normal((nc, 2, Np)), 1e-3 * rng.standard_normal((nc, 3, Np))))
+    vs = [torch.tensor(a, device="cuda") for a, _ in init]
+    ss = [torch.tensor(b, device="cuda") for _, b in init]
+    rs = [torch.tensor(c["ricker"], device="cuda") for c in cfgs]
+    grp = lib.slt_group_create(meshes, scheds)
+    lib.slt_group_execute(grp, vs, ss, rs, [c["dt"] for c in cfgs], 2)
+    small = int(np.argmin([c["mesh"]["cell2vert"].shape[0] for c in cfgs]))
+    for k in sorted({0, 7, small}):
+        v1, s1 = torch.tensor(init[k][0], device="cuda"), torch.tensor(init[k][1], device="cuda")
+        lib.slt_execute(meshes[k], scheds[k], v1, s1, rs[k], cfgs[k]["dt"], 2)
+        assert torch.equal(vs[k], v1) and torch.equal(ss[k], s1), k
+    c = cfgs[small]
+    dg = ElasticDG(c["mesh"], c["p"], c["rho"], c["lam"], c["mu"])
+    vo, so = dg.run(init[small][0].copy(), init[small][1].copy(), c["dt"], 2, c["ricker"], c["src"])
+    assert rel_l2(vs[small].cpu().numpy(), vo) < TOL and rel_l2(ss[small].cpu().numpy(), so) < TOL
+
+
+def test_fullsize_adjoint_gradient_matches_central_differences(lib):
+    # the bench's adjoint configuration: 448x224 squares (200k cells), P2, +-5 % perturbed layers,
+    # one top-row shot, 50 receivers, 1000 steps, checkpoints every 50; two seeded directions
+    import torch
+    n = 1000
+    cfg = synth.build_config("adjoint", nsteps=n)
+    m = cfg["mesh"]
+    shot = np.array([(0 + 0.5) * 300.0 / 8, (7 + 0.5) * 150.0 / 8])
+    rec = np.stack([(np.arange(50) + 0.5) * 6.0, np.full(50, 149.0)], 1)
+    base = synth.layered(m)
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], 2, *base, shot)
+    r = lib.slt_receivers_create(mesh, rec)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    data = torch.zeros((n, 50, 2), dtype=torch.float64, device="cuda")
+    lib.slt_record(mesh, None, r, rk, cfg["dt"], n, data)
+    model = (cfg["rho"], cfg["lam"], cfg["mu"])
+    lib.slt_mesh_set_material(mesh, *model)
+    g = torch.zeros((3, m["cell2vert"].shape[0]), dtype=torch.float64, device="cuda")
+    J = lib.slt_adjoint(mesh, None, r, rk, cfg["dt"], n, data, 50, g)
+    g = g.cpu().numpy()
+    tr = torch.zeros_like(data)
+
+    def misfit(mod):
+        lib.slt_mesh_set_material(mesh, *mod)
+        lib.slt_record(mesh, None, r, rk, cfg["dt"], n, tr)
+        return 0.5 * cfg["dt"] * float(((tr - data) ** 2).sum())
+
+    assert abs(misfit(model) - J) <= 1e-12 * J
+    rng = np.random.default_rng(31)
+    for _ in range(2):
+        d = [a * rng.uniform(-1, 1, a.shape) for a in model]
+        eps = 1e-5   # truncation ~ (eps / 0.05)^2 = 4e-8 of the derivative, round-off ~1e-9
+        fd = (misfit([a + eps * b for a, b in zip(model, d)]) - misfit([a - eps * b for a, b in zip(model, d)])) / (2 * eps)
+        ad = sum(g[k] @ d[k] for k in range(3))
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
