@@ -33,7 +33,7 @@ typedef enum {
   SLT_ERR_CUDA = -3,         /* a CUDA runtime call or kernel launch failed */
   SLT_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
   SLT_ERR_CONFLICT_CAP = -5, /* conflict buffer of the inspector overflowed */
-  SLT_ERR_UNSUPPORTED = -6,  /* valid request outside what this build implements */
+  SLT_ERR_UNSUPPORTED = -6,  /* valid request outside what this library implements */
   SLT_ERR_STATE = -7         /* object used in the wrong state (e.g. schedule of another mesh) */
 } slt_status;
 
@@ -244,7 +244,7 @@ int slt_autotune(slt_mesh mesh, const slt_options* base, int32_t nshots, const i
 int slt_apply_operator(slt_mesh mesh, int32_t op, const double* in, double* out, void* stream);
 
 /* ------------------------------------------------------------------ misfit and gradient
- * The spec extension of the paper's forward chain: the gradient of a seismogram misfit
+ * An extension of the paper's forward chain: the gradient of a seismogram misfit
  * with respect to per-cell rho, lambda, mu by the discrete adjoint of the time step.
  *
  * Replace the material (host arrays, caller numbering; mu > 0, lambda + mu > 0, rho > 0) or

@@ -6,7 +6,7 @@ What it follows.  The paper fixes the method only in prose (Section 7.1: velocit
 formulation, DG in space, fourth-order explicit leapfrog built from a truncated Taylor series,
 non-dissipative; Section 7.2: eight cell-local solves with block-diagonal mass matrices and
 twenty-five loops over cells, interior facets and exterior facets per time step).  The
-reading implemented here (listed in the design doc) is:
+reading implemented here is:
 
   rho dv/dt = div(sigma),   dsigma/dt = lambda tr(eps(v)) I + 2 mu eps(v) + g(t) delta(x - xs) I
 

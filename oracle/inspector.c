@@ -4,7 +4,7 @@
  * (inspection), Algorithm 2 (projection of a tiled loop) and Algorithm 3 (tiling function),
  * Section 5.1, in shared-memory mode (every set is a single core region).
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - partition (Section 5.1.2): seed iterations are ranked (identity, or a stable sort by the
  *    order-16 Hilbert index of a per-element point quantised on a 65536x65536 grid over its
  *    bounding box); tile of rank r is r / ts.

@@ -1,4 +1,4 @@
-"""The synthetic workloads: sizes, materials and source placement (see the table in the design doc).
+"""The synthetic workloads: sizes, materials and source placement.
 
 Meshes use seed 0 (renumbering seed 1); material perturbation seed 2.  Every workload is an
 explosive point source with a Ricker time function, a free surface on the whole boundary,
