@@ -396,7 +396,10 @@ def main():
         dist.init_process_group("nccl")
 
     import __graft_entry__
-    __graft_entry__.build()
+    if rank == 0:
+        __graft_entry__.build()          # one rank compiles; the others wait for the library
+    if dist:
+        dist.barrier()
     import paper_1708_03183_gb300 as slt
     import synth
 
