@@ -1,0 +1,53 @@
+"""Degenerate and boundary cases of the GPU path: meshes of one and two cells (no or one interior
+facet: empty facet loops, a single tile), and the queue-size limit of the dataflow executor."""
+import numpy as np
+import pytest
+
+from oracle.dg import ElasticDG
+from tests.helpers import TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _tiny_mesh(ncell):
+    # one triangle, or two sharing the diagonal of the unit square (counter-clockwise)
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    c2v = np.array([[0, 1, 2], [0, 2, 3]][:ncell], dtype=np.int32)
+    return {"cell2vert": c2v, "cellxy": V[c2v], "coords": V, "nvert": 4}
+
+
+@pytest.mark.parametrize("ncell", [1, 2])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_one_and_two_cell_meshes_match_oracle(lib, ncell, p):
+    import torch
+    m = _tiny_mesh(ncell)
+    rng = np.random.default_rng(10 * ncell + p)
+    mat = (rng.uniform(1, 2, ncell), rng.uniform(1, 2, ncell), rng.uniform(1, 2, ncell))
+    Np = (p + 1) * (p + 2) // 2
+    v0, s0 = rng.standard_normal((ncell, 2, Np)), rng.standard_normal((ncell, 3, Np))
+    dt = 0.01
+    vo, so = ElasticDG(m, p, *mat).run(v0.copy(), s0.copy(), dt, 5)
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], p, *mat)
+    info = lib.slt_mesh_info(mesh)
+    assert (info["nfi"], info["nfe"]) == (ncell - 1, 3 * ncell - 2 * (ncell - 1))
+    for ex in (0, 1):
+        for sched in (None, lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=1, split=(9,), executor=ex)):
+            v, s = torch.tensor(v0, device="cuda"), torch.tensor(s0, device="cuda")
+            lib.slt_execute(mesh, sched, v, s, None, dt, 5)
+            assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
+
+
+def test_dataflow_queue_limit_is_refused(lib):
+    # steps x tiles must stay below 2^31 (the queue holds int32 node ids): refused, nothing hangs
+    import torch
+    m = _tiny_mesh(2)
+    mat = (np.ones(2), np.ones(2), np.ones(2))
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], 1, *mat)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=1, split=(9,))
+    G = sum(lib.slt_schedule_info(sched, k)["ntiles"] for k in range(2))
+    v = torch.zeros((2, 2, 3), dtype=torch.float64, device="cuda")
+    s = torch.zeros((2, 3, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.SltError) as e:
+        lib.slt_execute(mesh, sched, v, s, None, 0.01, (1 << 31) // G + 1)
+    assert e.value.code == -6
+    lib.slt_execute(mesh, sched, v, s, None, 0.01, 2)   # the context is still usable
