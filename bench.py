@@ -236,8 +236,9 @@ def adjoint_timing(slt, synth, args, barrier):
 def batched_timing(slt, synth, args, barrier):
     """Multi-shot form: the 708x354 P2 layered mesh (501k cells) with `--shots` point sources on
     the 8x8 grid x = (i+1/2) 300/8, y = (j+1/2) 150/8 (the first `--shots` of them), shots
-    innermost.  Untiled (17 launches per step) and the dataflow executor at each tile size of
-    `--batched-ts`; the fastest is the headline of this block."""
+    innermost.  The library's autotuner picks among the untiled chain and the dataflow executor
+    at each tile size of `--batched-ts` with `--shots-per-cta` shots per tile CTA (3 timed steps
+    each); the pick is then timed over `--batched-steps` steps."""
     import numpy as np
     import torch
     S = args.shots
@@ -250,31 +251,30 @@ def batched_timing(slt, synth, args, barrier):
     grid = np.array([((i + 0.5) * 300.0 / 8, (j + 0.5) * 150.0 / 8) for j in range(8) for i in range(8)])
     pts = grid[np.arange(S) % 64]
     mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
-    chain = slt.slt_mesh_chain(mesh)
+    t0 = time.perf_counter()
+    best, table = slt.slt_autotune(mesh, list(args.batched_ts), nshots=S, block_threads=(256,),
+                                   shots_per_cta=[g for g in args.shots_per_cta if g <= S], steps=3, split=(9,))
+    tune_s = time.perf_counter() - t0
+    sched = slt.slt_inspect(slt.slt_mesh_chain(mesh), best) if best.tile_size else None
     rk = torch.tensor(cfg["ricker"], device="cuda")
     v = torch.zeros((nc, 2, Np, S), dtype=torch.float64, device="cuda")
     s = torch.zeros((nc, 3, Np, S), dtype=torch.float64, device="cuda")
-    units = 5 * Np * nc * S
-    res = {}
-    for ts in [0] + list(args.batched_ts):
-        sched = None if ts == 0 else slt.slt_inspect(chain, tile_size=ts, split=(9,), executor=0)
-        slt.slt_execute_batched(mesh, sched, pts, v, s, rk, cfg["dt"], W)
+    slt.slt_execute_batched(mesh, sched, pts, v, s, rk, cfg["dt"], W)
+    barrier()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        prof = slt.slt_execute_batched(mesh, sched, pts, v, s, rk[W:], cfg["dt"], K, profile=True)
         barrier()
-        with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-            prof = slt.slt_execute_batched(mesh, sched, pts, v, s, rk[W:], cfg["dt"], K, profile=True)
-            barrier()
-        ms = prof["chain_ms"] / K
-        res["untiled" if ts == 0 else "ts%d" % ts] = {"ms_per_step": ms, "value": units / (ms * 1e-3),
-                                                       "launches": prof["chain_launches"] + prof["layout_launches"],
-                                                       "sm_mhz": clk.summary()["sm_mhz"]}
-        del sched
-    best = max(res, key=lambda k: res[k]["value"])
-    cost = slt.slt_mesh_cost(mesh)
-    fl = cost["flops_per_step"] * S
+    ms = prof["chain_ms"] / K
+    units = 5 * Np * nc * S
+    fl = slt.slt_mesh_cost(mesh)["flops_per_step"] * S
+    pick = ("untiled" if not best.tile_size else
+            "ts%d, %d shots per CTA" % (best.tile_size, best.shots_per_cta or S))
     return {"workload": "708x354 squares on 300x150 (%d cells), P2 FP64, layered, %d shots on the 8x8 grid, "
                         "%d steps, fields [cell][comp][node][shot] (%.1f GB)" % (nc, S, K, 5 * Np * nc * S * 8 / 1e9),
-            "value": res[best]["value"], "unit": "dof-updates/s", "best": best, "ms_per_step": res[best]["ms_per_step"],
-            "fp64_frac": fl / (res[best]["ms_per_step"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "runs": res}
+            "value": units / (ms * 1e-3), "unit": "dof-updates/s", "best": pick, "ms_per_step": ms,
+            "fp64_frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "clocks": clk.summary(),
+            "autotune": {"seconds": tune_s, "rows": ["ts %d, renumber %d, %d threads, %d shots per CTA: %.2f ms" % tuple(r)
+                                                     for r in table]}}
 
 
 def multi_timing(slt, synth, args, barrier):
@@ -381,7 +381,8 @@ def main():
     ap.add_argument("--multi-steps", type=int, default=20)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10)
-    ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64, 128])
+    ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64])
+    ap.add_argument("--shots-per-cta", type=lambda t: [int(x) for x in t.split(",")], default=[16, 64])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

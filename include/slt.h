@@ -100,6 +100,9 @@ typedef struct {
   int32_t block_threads; /* threads per tile CTA: 128, 256 or 384 (0 = 256) */
   int32_t sub_tile_size[16]; /* seed tile size of sub-chain k (0 = tile_size): a fusion scheme
                                 with its own tile size per sub-chain (Section 7.2) */
+  int32_t shots_per_cta;     /* multi-shot runs with the dataflow executor: a tile CTA runs its
+                                items for this many shots (0 = all); the shots go through the
+                                queue in slices of this size, one persistent launch each */
   int32_t seed_loop[16];     /* seed loop of sub-chain k, counted from its first loop (0 = the
                                 first loop, forward tiling only); > 0 selects backward tiling
                                 for the loops before it (Section 5.1.1): MIN projections from
@@ -223,21 +226,25 @@ int slt_group_execute(slt_group group, double* const* v, double* const* sigma, c
 int slt_execute_many(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, double* const* v,
                      double* const* sigma, const double* const* ricker, const double* dt, int64_t nsteps,
                      void* stream);
-/* Autotuner over tile size, tile shape and CTA size (Section 7.3 searches them empirically).
-   Times the untiled chain, then every candidate (tile_sizes[i], renumber, block_threads[b]):
-   renumber 1 (Hilbert tiles) only, or also 0 (chunks of the mesh numbering) when shapes != 0.
-   Each candidate is inspected with `base` for every other option (split points, executor ...),
-   run 2 untimed steps and `steps` timed steps (CUDA events around the executor kernels) with
-   zero fields and no source, nshots = 1: the single-field executor, nshots > 1: the
-   multi-shot executor.  A candidate whose colouring fell back to sequential (its tiles would
-   run one after another) is not timed: its row holds ms = -1.  *best = base with the fastest candidate's tile_size, renumber and
-   block_threads; best->tile_size = 0 when the untiled chain was fastest.  table (host, may be
-   NULL): rows (tile_size, renumber, block_threads, ms per step), the untiled chain first (0, 0,
-   0, ms); 1 + ntile * (shapes ? 2 : 1) * nblock rows.  Allocates the candidate fields
-   (5 Np ncell nshots doubles) for the call; synchronises. */
+/* Autotuner over tile size, tile shape, CTA size and shots per CTA (Section 7.3 searches tile
+   size and shape empirically).  Times the untiled chain, then every candidate (tile_sizes[i],
+   renumber, block_threads[b], shots_per_cta[k]): renumber 1 (Hilbert tiles) only, or also 0
+   (chunks of the mesh numbering) when shapes != 0; the shots-per-CTA candidates apply to
+   nshots > 1 (ngroup = 0 or nshots = 1: one candidate, all shots).  Each candidate is inspected
+   with `base` for every other option (split points, executor ...), run 2 untimed steps and
+   `steps` timed steps (CUDA events around the executor kernels) with zero fields and no source,
+   nshots = 1: the single-field executor, nshots > 1: the multi-shot executor.  A candidate
+   whose colouring fell back to sequential (its tiles would run one after another) is not
+   timed: its row holds ms = -1.  *best = base with the fastest candidate's tile_size,
+   renumber, block_threads and shots_per_cta; best->tile_size = 0 when the untiled chain was
+   fastest.  table (host, may be NULL): rows (tile_size, renumber, block_threads, shots_per_cta,
+   ms per step), the untiled chain first (0, 0, 0, 0, ms); 1 + ntile * (shapes ? 2 : 1) *
+   nblock * max(ngroup, 1) rows (ngroup counted as 1 when nshots = 1).  Allocates the candidate
+   fields (5 Np ncell nshots doubles) for the call; synchronises. */
 int slt_autotune(slt_mesh mesh, const slt_options* base, int32_t nshots, const int32_t* tile_sizes,
-                 int32_t ntile, int32_t shapes, const int32_t* block_threads, int32_t nblock, int32_t steps,
-                 void* stream, slt_options* best, double* table);
+                 int32_t ntile, int32_t shapes, const int32_t* block_threads, int32_t nblock,
+                 const int32_t* shots_per_cta, int32_t ngroup, int32_t steps, void* stream, slt_options* best,
+                 double* table);
 /* Apply one operator once (for tests): op 0 = A (stress -> velocity rate, device
    in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
    out [ncell][3][Np]).  Runs the untiled loops of that operator. */

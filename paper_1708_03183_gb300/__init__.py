@@ -27,7 +27,7 @@ class slt_options(ctypes.Structure):
     _fields_ = [("tile_size", I32), ("colouring", I32), ("renumber", I32), ("max_rounds", I32),
                 ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15), ("executor", I32),
                 ("wait_spins", I32), ("block_threads", I32), ("sub_tile_size", I32 * 16),
-                ("seed_loop", I32 * 16)]
+                ("shots_per_cta", I32), ("seed_loop", I32 * 16)]
 
 
 _SIGS = {
@@ -54,7 +54,7 @@ _SIGS = {
     "slt_execute_host": (ctypes.c_int, [P, P, P, P, P, F64, I64, P]),
     "slt_execute_profiled": (ctypes.c_int, [P, P, P, P, P, F64, I64, P, P]),
     "slt_execute_batched": (ctypes.c_int, [P, P, I32, P, P, P, P, F64, I64, P, P]),
-    "slt_autotune": (ctypes.c_int, [P, P, I32, P, I32, I32, P, I32, I32, P, P, P]),
+    "slt_autotune": (ctypes.c_int, [P, P, I32, P, I32, I32, P, I32, P, I32, I32, P, P, P]),
     "slt_execute_many": (ctypes.c_int, [I32, P, P, P, P, P, P, I64, P]),
     "slt_group_create": (ctypes.c_int, [I32, P, P, P]),
     "slt_group_destroy": (ctypes.c_int, [P]),
@@ -363,18 +363,22 @@ def slt_execute_many(meshes, scheds, vs, sigmas, rickers, dts, nsteps, stream=No
                                 v, s_, r, d, int(nsteps), _stream(stream)))
 
 
-def slt_autotune(mesh, tile_sizes, nshots=1, shapes=False, block_threads=(256,), steps=5, base=None, stream=None,
-                 **kw):
-    """Time the untiled chain and every (tile size, shape, CTA size) candidate on this mesh;
-    returns (best slt_options, table rows (tile_size, renumber, block_threads, ms/step))."""
+def slt_autotune(mesh, tile_sizes, nshots=1, shapes=False, block_threads=(256,), shots_per_cta=(), steps=5,
+                 base=None, stream=None, **kw):
+    """Time the untiled chain and every (tile size, shape, CTA size, shots per CTA) candidate on
+    this mesh; returns (best slt_options, table rows (tile_size, renumber, block_threads,
+    shots_per_cta, ms/step))."""
     base = base if base is not None else slt_options_default(**kw)
     ts, tsp = _host(np.asarray(tile_sizes, dtype=np.int32), np.int32)
     bt, btp = _host(np.asarray(block_threads, dtype=np.int32), np.int32)
-    rows = 1 + len(ts) * (2 if shapes else 1) * len(bt)
-    table = np.zeros((rows, 4), dtype=np.float64)
+    sg, sgp = _host(np.asarray(shots_per_cta if len(shots_per_cta) else [0], dtype=np.int32), np.int32)
+    ng = len(shots_per_cta)
+    rows = 1 + len(ts) * (2 if shapes else 1) * len(bt) * (max(ng, 1) if nshots > 1 else 1)
+    table = np.zeros((rows, 5), dtype=np.float64)
     best = slt_options()
     _check(lib.slt_autotune(mesh.ptr, ctypes.byref(base), int(nshots), tsp, len(ts), int(bool(shapes)), btp, len(bt),
-                            int(steps), _stream(stream), ctypes.byref(best), ctypes.c_void_p(table.ctypes.data)))
+                            sgp if ng else None, ng, int(steps), _stream(stream), ctypes.byref(best),
+                            ctypes.c_void_p(table.ctypes.data)))
     return best, table
 
 

@@ -215,6 +215,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
   REQUIRE(opt->executor == 0 || opt->executor == 1, "executor must be 0 or 1");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
+  REQUIRE(opt->shots_per_cta >= 0, "shots_per_cta must be >= 0");
   REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
               opt->block_threads == 384,
           "block_threads must be 0, 128, 256 or 384");
@@ -244,6 +245,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   s->executor = opt->executor;
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
   if (opt->block_threads) s->block = opt->block_threads;
+  s->shots_per_cta = opt->shots_per_cta;
   inspect_chain(c, *opt, as_stream(stream), s.get());
   *out = s.release();
   API_END
@@ -752,8 +754,8 @@ int slt_execute_many(int32_t n, const slt_mesh* meshes, const slt_schedule* sche
 }
 
 int slt_autotune(slt_mesh m, const slt_options* base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,
-                 int32_t shapes, const int32_t* block_threads, int32_t nblock, int32_t steps, void* stream,
-                 slt_options* best, double* table) {
+                 int32_t shapes, const int32_t* block_threads, int32_t nblock, const int32_t* shots_per_cta,
+                 int32_t ngroup, int32_t steps, void* stream, slt_options* best, double* table) {
   API_BEGIN
   REQUIRE(m && base && best && tile_sizes && block_threads, "null argument");
   REQUIRE(nshots >= 1 && nshots <= 4096, "nshots must be in 1..4096");
@@ -764,8 +766,10 @@ int slt_autotune(slt_mesh m, const slt_options* base, int32_t nshots, const int3
     REQUIRE(block_threads[b] == 128 || block_threads[b] == 256 || block_threads[b] == 384,
             "block_threads must be 128, 256 or 384");
   if (nshots > 1) REQUIRE(base->executor == 0, "the multi-shot executor runs with executor 0");
-  autotune(m, *base, nshots, tile_sizes, ntile, shapes, block_threads, nblock, steps, as_stream(stream), best,
-           table);
+  REQUIRE(ngroup >= 0 && ngroup <= 16 && (ngroup == 0 || shots_per_cta), "0..16 shots-per-CTA candidates");
+  for (int k = 0; k < ngroup; ++k) REQUIRE(shots_per_cta[k] >= 0, "shots per CTA must be >= 0");
+  autotune(m, *base, nshots, tile_sizes, ntile, shapes, block_threads, nblock, shots_per_cta, ngroup, steps,
+           as_stream(stream), best, table);
   API_END
 }
 

@@ -123,10 +123,10 @@ __device__ __forceinline__ void run_tile(const Params& a, int first, int last, i
   for (int J = first; J < last; ++J) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
     const int32_t* items = a.plan_items[J];
-    if constexpr (BATCH) {  // every item for every shot, consecutive threads on consecutive shots
-      const int64_t nwork = (int64_t)(e - b) * a.S;
+    if constexpr (BATCH) {  // every item for each shot of the slice, consecutive threads on consecutive shots
+      const int64_t nwork = (int64_t)(e - b) * a.sg;
       for (int64_t i = threadIdx.x; i < nwork; i += BS)
-        run_loop<P, DF_L2_ONLY, true>(a, J, items[b + i / a.S], st, (int)(i % a.S));
+        run_loop<P, DF_L2_ONLY, true>(a, J, items[b + i / a.sg], st, a.s0 + (int)(i % a.sg));
     } else {
       for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
     }

@@ -103,8 +103,13 @@ struct Timer {
 
 template <int P>
 void run_batched(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s, Timer& tm) {
-  if (sched) {
-    launch_dataflow<P, true>(sched, a, nsteps, s, [&] { tm.begin(s, 3); }, [&] { tm.end(s); });
+  if (sched) {  // the shots in slices of shots_per_cta, one queue pass each
+    const int32_t g = sched->shots_per_cta > 0 ? std::min(sched->shots_per_cta, a.S) : a.S;
+    for (int32_t s0 = 0; s0 < a.S; s0 += g) {
+      a.s0 = s0;
+      a.sg = std::min(g, a.S - s0);
+      launch_dataflow<P, true>(sched, a, nsteps, s, [&] { tm.begin(s, 3); }, [&] { tm.end(s); });
+    }
     return;
   }
   for (int64_t step = 0; step < nsteps; ++step) {
@@ -150,6 +155,8 @@ void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* 
   a.dt = dt;
   a.c24 = dt * dt / 24.0;
   a.S = S;
+  a.s0 = 0;
+  a.sg = S;
   a.fs = fs;
   a.src_wb = d_src_w;
   a.src_b = d_src;

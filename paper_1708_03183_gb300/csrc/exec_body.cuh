@@ -61,6 +61,7 @@ struct Params {
   const int32_t* plan_items[17];
   // multi-shot layout
   int32_t S;                        // shots per cell (1 for one field)
+  int32_t s0, sg;                   // tiled multi-shot runs: shots s0 .. s0 + sg - 1 of the S
   int64_t fs;                       // field row stride: ncp * S
   const int32_t* src_wb;            // [S] source cell of every shot
   const double* src_b;              // [S][Np] source coefficients of every shot

@@ -155,7 +155,8 @@ struct DataflowPlan {
 
 struct slt_schedule_s {
   int32_t executor = 0;              // 0 dataflow, 1 colour phases
-  int32_t block = 256;               // threads per tile CTA (128 or 256)
+  int32_t block = 256;               // threads per tile CTA (128, 256 or 384)
+  int32_t shots_per_cta = 0;         // multi-shot dataflow runs: shots per queue pass (0 = all)
   int64_t wait_spins = 1ll << 24;    // bounded dependency wait of the dataflow executor
   slt::DataflowPlan df;
   std::vector<slt::LoopH> loops;     // copy of the chain's loops
@@ -264,8 +265,8 @@ void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* 
                       double* profile);
 // tune.cpp
 void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,
-              int32_t shapes, const int32_t* blocks, int32_t nblock, int32_t steps, cudaStream_t s,
-              slt_options* best, double* table);
+              int32_t shapes, const int32_t* blocks, int32_t nblock, const int32_t* groups, int32_t ngroup,
+              int32_t steps, cudaStream_t s, slt_options* best, double* table);
 // adjoint.cu
 void upload_adjoint_constants(const RefElem& r);
 void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,

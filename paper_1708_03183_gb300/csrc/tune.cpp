@@ -35,8 +35,8 @@ double time_candidate(slt_mesh m, slt_schedule sched, int32_t nshots, Fields& f,
 }  // namespace
 
 void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t* tile_sizes, int32_t ntile,
-              int32_t shapes, const int32_t* blocks, int32_t nblock, int32_t steps, cudaStream_t s,
-              slt_options* best, double* table) {
+              int32_t shapes, const int32_t* blocks, int32_t nblock, const int32_t* groups, int32_t ngroup,
+              int32_t steps, cudaStream_t s, slt_options* best, double* table) {
   const int64_t per = (int64_t)m->nc * m->Np * nshots;
   Fields f;
   f.v.alloc(2 * per);
@@ -59,16 +59,23 @@ void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t
   best->tile_size = 0;
   double best_ms = time_candidate(m, nullptr, nshots, f, src_w.p, src.p, steps, warm, s);
   int row = 0;
-  auto put = [&](int32_t ts, int32_t rn, int32_t bt, double ms) {
+  auto put = [&](int32_t ts, int32_t rn, int32_t bt, int32_t g, double ms) {
     if (table) {
-      table[4 * row + 0] = ts;
-      table[4 * row + 1] = rn;
-      table[4 * row + 2] = bt;
-      table[4 * row + 3] = ms;
+      table[5 * row + 0] = ts;
+      table[5 * row + 1] = rn;
+      table[5 * row + 2] = bt;
+      table[5 * row + 3] = g;
+      table[5 * row + 4] = ms;
     }
     ++row;
   };
-  put(0, 0, 0, best_ms);
+  put(0, 0, 0, 0, best_ms);
+  // shots per CTA only matter for several shots
+  const int32_t one_group = 0;
+  if (nshots == 1 || ngroup == 0) {
+    groups = &one_group;
+    ngroup = 1;
+  }
   const int nshape = shapes ? 2 : 1;
   for (int i = 0; i < ntile; ++i)
     for (int r = 0; r < nshape; ++r)
@@ -83,15 +90,19 @@ void autotune(slt_mesh m, const slt_options& base, int32_t nshots, const int32_t
         std::unique_ptr<slt_schedule_s, int (*)(slt_schedule)> guard(sched, slt_schedule_destroy);
         bool serial = false;
         for (const SubSched& sub : sched->subs) serial |= sub.fell_back != 0 && sub.m > 1;
-        if (serial && o.colouring == 0) {
-          put(o.tile_size, o.renumber, o.block_threads, -1.0);
-          continue;
-        }
-        double ms = time_candidate(m, sched, nshots, f, src_w.p, src.p, steps, warm, s);
-        put(o.tile_size, o.renumber, o.block_threads, ms);
-        if (ms < best_ms) {
-          best_ms = ms;
-          *best = o;
+        for (int k = 0; k < ngroup; ++k) {
+          o.shots_per_cta = groups[k];
+          if (serial && o.colouring == 0) {
+            put(o.tile_size, o.renumber, o.block_threads, o.shots_per_cta, -1.0);
+            continue;
+          }
+          sched->shots_per_cta = o.shots_per_cta;  // an executor setting: no new inspection
+          double ms = time_candidate(m, sched, nshots, f, src_w.p, src.p, steps, warm, s);
+          put(o.tile_size, o.renumber, o.block_threads, o.shots_per_cta, ms);
+          if (ms < best_ms) {
+            best_ms = ms;
+            *best = o;
+          }
         }
       }
 }

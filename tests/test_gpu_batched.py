@@ -121,3 +121,17 @@ def test_batched_without_sources_and_errors(lib):
     v2 = v.clone()
     lib.slt_execute_batched(mesh, None, None, v, s, None, cfg["dt"], 0)
     assert torch.equal(v, v2)
+
+
+@pytest.mark.parametrize("groups", [1, 2, 3, 7])
+def test_shots_per_cta_slices_give_the_same_bits(lib, groups):
+    # the dataflow executor runs the shots in slices of `groups`: same arithmetic per (cell, shot)
+    cfg = workload("small_p2")
+    mesh = gpu_mesh(lib, cfg)
+    pts = _shots(cfg, 5)
+    v0, s0 = _fields(cfg, 5)
+    whole = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=48, split=(9,))
+    sliced = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=48, split=(9,), shots_per_cta=groups)
+    a = _run_batched(lib, cfg, mesh, whole, pts, v0, s0, 4)
+    b = _run_batched(lib, cfg, mesh, sliced, pts, v0, s0, 4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

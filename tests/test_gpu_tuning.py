@@ -33,18 +33,20 @@ def test_per_subchain_tile_sizes_bit_exact_and_parity(lib, split, sub_ts):
 def test_autotune_table_and_tuned_run(lib, nshots):
     cfg = workload("small_p2")
     mesh = gpu_mesh(lib, cfg)
-    best, table = lib.slt_autotune(mesh, [32, 96], nshots=nshots, shapes=True, block_threads=(128, 256), steps=2,
-                                   split=(9,))
-    assert table.shape == (1 + 2 * 2 * 2, 4)
-    assert tuple(table[0, :3]) == (0, 0, 0)
-    assert {(int(r[0]), int(r[1]), int(r[2])) for r in table[1:]} == {
-        (t, r, b) for t in (32, 96) for r in (0, 1) for b in (128, 256)}
-    assert np.all((table[:, 3] > 0) | (table[:, 3] == -1))
-    ms = np.where(table[:, 3] > 0, table[:, 3], np.inf)
+    groups = (1, 2) if nshots > 1 else ()
+    best, table = lib.slt_autotune(mesh, [32, 96], nshots=nshots, shapes=True, block_threads=(128, 256),
+                                   shots_per_cta=groups, steps=2, split=(9,))
+    ng = max(len(groups), 1)
+    assert table.shape == (1 + 2 * 2 * 2 * ng, 5)
+    assert tuple(table[0, :4]) == (0, 0, 0, 0)
+    assert {(int(r[0]), int(r[1]), int(r[2]), int(r[3])) for r in table[1:]} == {
+        (t, r, b, g) for t in (32, 96) for r in (0, 1) for b in (128, 256) for g in (groups or (0,))}
+    assert np.all((table[:, 4] > 0) | (table[:, 4] == -1))
+    ms = np.where(table[:, 4] > 0, table[:, 4], np.inf)
     k = int(np.argmin(ms))
     assert best.tile_size == int(table[k, 0])
     if best.tile_size:
-        assert (best.renumber, best.block_threads) == (int(table[k, 1]), int(table[k, 2]))
+        assert (best.renumber, best.block_threads, best.shots_per_cta) == tuple(int(x) for x in table[k, 1:4])
         assert best.nsplit == 1 and best.split[0] == 9
     # the winner is an ordinary configuration: parity with the oracle
     sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), best) if best.tile_size else None
