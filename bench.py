@@ -355,7 +355,7 @@ def workload_name(args):
     return ("%s: %dx%d squares on %gx%g, %d triangles, DG P%d FP64, %s material, Ricker f0=%g, "
             "sparse-tiled ts=%d, fusion {velocity, stress}, %s executor" % (
                 args.config, nx, ny, c["Lx"], c["Ly"], 2 * nx * ny, c["p"], c["material"],
-                c["f0"], args.tile_size, ["dataflow", "colour-phase"][getattr(args, "executor", 0)]))
+                c["f0"], args.tile_size, ["dataflow", "colour-phase", "cluster dataflow"][getattr(args, "executor", 0)]))
 
 
 def main():
@@ -366,7 +366,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large")
     ap.add_argument("--tile-size", type=int, default=256)
-    ap.add_argument("--executor", type=int, default=0, help="0 dataflow (persistent), 1 colour phases")
+    ap.add_argument("--executor", type=int, default=0,
+                    help="0 dataflow (persistent), 1 colour phases, 2 dataflow with one CTA cluster per tile")
+    ap.add_argument("--cluster-size", type=int, default=8, help="CTAs per tile cluster (executor 2)")
     ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128, 256 or 384)")
     ap.add_argument("--no-untiled", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -425,7 +427,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sched = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,), executor=args.executor,
-                            block_threads=args.block)
+                            block_threads=args.block, cluster_size=args.cluster_size)
     inspect_s = time.perf_counter() - t0
     subs = [slt.slt_schedule_info(sched, k) for k in range(2)]
 
@@ -458,7 +460,7 @@ def main():
     kern_s = prof["chain_ms"] * 1e-3
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
-    kname = ("k_dataflow<%d,%d>" if args.executor == 0 else "k_tiled<%d,%d>") % (p, args.block)
+    kname = ("k_dataflow<%d,%d>", "k_tiled<%d,%d>", "k_dataflow_cluster<%d,%d>")[args.executor] % (p, args.block)
     traffic = ncu_traffic(kname, args.config, args.steps) if args.scale == 1 and args.block == 256 else None
     tiled_bytes = cost["tiled_bytes_per_step"]
 
@@ -471,7 +473,7 @@ def main():
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "tiles": [s["ntiles"] for s in subs], "colours": [s["ncolours"] for s in subs],
                       "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s,
-                      "executor": ["dataflow", "colour phases"][args.executor], "block_threads": args.block},
+                      "executor": ["dataflow", "colour phases", "dataflow, tile clusters of %d CTAs" % args.cluster_size][args.executor], "block_threads": args.block},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP64_PEAK_TFLOPS,
                         "traffic": traffic, "kernel": kname,

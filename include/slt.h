@@ -95,11 +95,14 @@ typedef struct {
   uint64_t prio_seed;    /* colouring priority seed */
   int32_t nsplit;        /* number of split points (0 = one sub-chain) */
   int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
-  int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases */
+  int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases,
+                            2 = dataflow with one thread-block cluster of 256-thread CTAs per tile
+                            (for large tiles; single-field runs) */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
   int32_t block_threads; /* threads per tile CTA: 128, 256 or 384 (0 = 256) */
   int32_t sub_tile_size[16]; /* seed tile size of sub-chain k (0 = tile_size): a fusion scheme
                                 with its own tile size per sub-chain (Section 7.2) */
+  int32_t cluster_size;      /* executor 2: CTAs per tile cluster, 1..8 (0 = 8) */
   int32_t shots_per_cta;     /* multi-shot runs with the dataflow executor: a tile CTA runs its
                                 items for this many shots (0 = all); the shots go through the
                                 queue in slices of this size, one persistent launch each */

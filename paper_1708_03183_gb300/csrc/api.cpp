@@ -213,7 +213,8 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
   REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
-  REQUIRE(opt->executor == 0 || opt->executor == 1, "executor must be 0 or 1");
+  REQUIRE(opt->executor >= 0 && opt->executor <= 2, "executor must be 0, 1 or 2");
+  REQUIRE(opt->cluster_size >= 0 && opt->cluster_size <= 8, "cluster_size must be in 0..8");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
   REQUIRE(opt->shots_per_cta >= 0, "shots_per_cta must be >= 0");
   REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
@@ -246,6 +247,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
   if (opt->block_threads) s->block = opt->block_threads;
   s->shots_per_cta = opt->shots_per_cta;
+  if (opt->cluster_size) s->cluster = opt->cluster_size;
   inspect_chain(c, *opt, as_stream(stream), s.get());
   *out = s.release();
   API_END

@@ -182,6 +182,38 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
   }
 }
 
+// The same executor with one thread-block cluster per tile (large tiles, few boundary cells):
+// the cluster's CTAs share each loop's items of the tile, separated by a cluster barrier.  The
+// leader CTA's first thread takes nodes from the queue and publishes their successors; the node
+// reaches the other CTAs through `slot[cluster]`, ordered by the barrier.  Every CTA of a cluster
+// passes the same barriers and leaves together, so the barriers always complete.
+template <int P, int BS>
+__global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_cluster(Params a, DF df,
+                                                                                  long long* __restrict__ slot) {
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const unsigned rank = cl.block_rank(), C = cl.num_blocks();
+  const unsigned cid = blockIdx.x / C;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) slot[cid] = df_take(df.q);
+    cl.sync();
+    const long long node = *(volatile long long*)&slot[cid];
+    if (node < 0) return;
+    const long long st = node / df.q.G;
+    const int g = (int)(node % df.q.G);
+    int k = 0;
+    while (g >= df.cum[k + 1]) ++k;
+    const int t = g - df.cum[k];
+    for (int J = df.first[k]; J < df.last[k]; ++J) {
+      const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
+      const int32_t* items = a.plan_items[J];
+      for (int32_t i = b + (int32_t)(rank * BS + threadIdx.x); i < e; i += (int32_t)(C * BS))
+        run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
+      cl.sync();
+    }
+    if (rank == 0 && threadIdx.x == 0) df_publish(df.q, g, st);
+  }
+}
+
 // Error flag of the schedule's last dataflow run (synchronises s): SLT_ERR_TIMEOUT if a wait
 // gave up.
 inline void dataflow_check(::slt_schedule_s* sched, cudaStream_t s) {
@@ -191,17 +223,17 @@ inline void dataflow_check(::slt_schedule_s* sched, cudaStream_t s) {
   if (herr) slt::fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
 }
 
-// Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin` / `rec_end` bracket
-// the three kernels for the caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
-template <int P, bool BATCH, class RB, class RE>
-void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end) {
+// The queue state and sub-chain table of one run of the schedule's plan (plan pointers into `a`),
+// the queue reset and seeded on s.  Returns false when there is nothing to run.
+template <class RB>
+bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaStream_t s, DF& df, RB rec_begin) {
   slt::DataflowPlan& D = sched->df;
-  DF df{};
+  df = DF{};
   DFQ& q = df.q;
   q.G = D.cum.back();
   q.nsteps = nsteps;
   q.total = (long long)nsteps * q.G;
-  if (q.total == 0) return;
+  if (q.total == 0) return false;
   if (q.total >= (1ll << 31)) slt::fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
   for (size_t k = 0; k < D.cum.size(); ++k) df.cum[k] = D.cum[k];
   for (size_t k = 0; k < sched->subs.size(); ++k) {
@@ -232,13 +264,22 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
                                                                                           D.indeg.p);
   k_df_seed<<<(q.G + 255) / 256, 256, 0, s>>>(q, D.indeg0.p);
   SLT_CUDA(cudaGetLastError());
+  return true;
+}
+
+// Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin` / `rec_end` bracket
+// the three kernels for the caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
+template <int P, bool BATCH, class RB, class RE>
+void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end) {
+  DF df;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, rec_begin)) return;
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int bs = sched->block;
   auto launch = [&](auto kernel, int threads) {
     SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
-    const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
+    const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), df.q.total);
     kernel<<<(unsigned)grid, threads, 0, s>>>(a, df);
   };
   if (bs == 128) launch(k_dataflow<P, 128, BATCH>, 128);

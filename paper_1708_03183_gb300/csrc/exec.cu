@@ -20,6 +20,7 @@
 //   E(v)    = (dvx/dx, dvy/dy, dvx/dy + dvy/dx) - sum_f (F_f / 2) Lift_f sym((v - v_nb) (x) n_f)
 //   B v     = C E(v),  C the isotropic Hooke law on (xx, yy, 2xy)
 // with F_f = |face f| / |det J| and n_f the outward unit normal of face f.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -217,6 +218,37 @@ void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) 
   launch_dataflow<P, false>(sched, a, nsteps, s, [&] { g_rec.begin(0, s, 3); }, [&] { g_rec.end(s); });
 }
 
+// executor 2: one cluster of `sched->cluster` 256-thread CTAs per tile, as many clusters as fit
+template <int P>
+void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
+  DF df;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, [&] { g_rec.begin(0, s, 3); })) return;
+  const int C = sched->cluster;
+  auto kernel = k_dataflow_cluster<P, 256>;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  SLT_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel, &cfg));
+  if (nclusters < 1) fail(SLT_ERR_UNSUPPORTED, "no cluster of this size fits on the GPU");
+  nclusters = (int)std::min<long long>(nclusters, df.q.total);
+  if (sched->df_slot.n < (size_t)nclusters) sched->df_slot.alloc(nclusters);
+  cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+  SLT_CUDA(cudaLaunchKernelEx(&cfg, kernel, a, df, sched->df_slot.p));
+  g_rec.end(s);
+  SLT_CUDA(cudaGetLastError());
+  dataflow_check(sched, s);
+}
+
 // The untiled step as one CUDA graph (17 loop kernels and the step-counter increment), captured
 // on the mesh's private stream and launched nsteps times on s: the host issues one launch per
 // step instead of seventeen.  The step index comes from a device counter the graph advances.
@@ -263,6 +295,10 @@ template <int P>
 void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
   if (sched && sched->executor == 0) {
     run_dataflow<P>(sched, a, nsteps, s);
+    return;
+  }
+  if (sched && sched->executor == 2) {
+    run_dataflow_cluster<P>(sched, a, nsteps, s);
     return;
   }
   if (!sched && nsteps >= kGraphMinSteps) {
@@ -368,7 +404,7 @@ void group_build(slt_group grp) {
   for (size_t i = 0; i < grp->meshes.size(); ++i) {
     slt_schedule sc = grp->scheds[i];
     if (sc && sc->executor == 0) by_degree[grp->meshes[i]->p].push_back((int32_t)i);
-    else grp->untiled.push_back((int32_t)i);  // untiled, or the colour-phase executor
+    else grp->untiled.push_back((int32_t)i);  // untiled, or the colour-phase or cluster executor
   }
   for (auto& kv : by_degree) {
     grp->parts.emplace_back();

@@ -4,6 +4,7 @@
 // coalesce over shots and per-cell geometry, neighbours and face masks are warp-uniform; every
 // shot has its own point source.  The loop bodies are those of exec_body.cuh; the arithmetic of
 // each (cell, shot) is exactly that of a single-field run with that shot's source.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

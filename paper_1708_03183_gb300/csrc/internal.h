@@ -154,9 +154,11 @@ struct DataflowPlan {
 }  // namespace slt
 
 struct slt_schedule_s {
-  int32_t executor = 0;              // 0 dataflow, 1 colour phases
+  int32_t executor = 0;              // 0 dataflow, 1 colour phases, 2 dataflow with tile clusters
   int32_t block = 256;               // threads per tile CTA (128, 256 or 384)
   int32_t shots_per_cta = 0;         // multi-shot dataflow runs: shots per queue pass (0 = all)
+  int32_t cluster = 8;               // executor 2: CTAs per tile cluster
+  slt::DevBuf<long long> df_slot;    // executor 2: node handed from each cluster's leader
   int64_t wait_spins = 1ll << 24;    // bounded dependency wait of the dataflow executor
   slt::DataflowPlan df;
   std::vector<slt::LoopH> loops;     // copy of the chain's loops

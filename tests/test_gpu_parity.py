@@ -39,7 +39,7 @@ def test_untiled_chain_matches_oracle(lib, name):
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL, (rel_l2(v, vo), rel_l2(s, so))
 
 
-@pytest.mark.parametrize("executor", [0, 1])
+@pytest.mark.parametrize("executor", [0, 1, 2])
 @pytest.mark.parametrize("name,ts", [("tiny", 64), ("tiny", 7), ("tiny", 1), ("tiny", 10 ** 6),
                                      ("small_p2", 64), ("small_p2", 200), ("small_p3", 48), ("small_p4", 40)])
 def test_tiled_chain_matches_oracle(lib, name, ts, executor):
@@ -52,7 +52,7 @@ def test_tiled_chain_matches_oracle(lib, name, ts, executor):
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL, (rel_l2(v, vo), rel_l2(s, so))
 
 
-@pytest.mark.parametrize("executor", [0, 1])
+@pytest.mark.parametrize("executor", [0, 1, 2])
 @pytest.mark.parametrize("split", [(), (9,), (3, 9, 12), (2, 7, 13), tuple(range(1, 16))])
 def test_fusion_schemes_match_oracle(lib, split, executor):
     cfg = workload("tiny")
@@ -69,19 +69,22 @@ def test_dataflow_equals_colour_phases_bitwise(lib, name, ts):
     cfg = workload(name)
     mesh = gpu_mesh(lib, cfg)
     out = []
-    for ex in (0, 1):
-        sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=(9,), executor=ex)
+    for ex, cl in ((0, 0), (1, 0), (2, 2), (2, 8)):
+        sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=(9,), executor=ex, cluster_size=cl)
         out.append(gpu_run(lib, cfg, sched=sched, mesh=mesh))
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
 
 
-def test_dataflow_wait_limit_reports_timeout_and_context_survives(lib):
+@pytest.mark.parametrize("executor", [0, 2])
+def test_dataflow_wait_limit_reports_timeout_and_context_survives(lib, executor):
     # with a one-poll wait limit the tiles that must wait for a neighbour give up: the kernel
     # sets its error flag and returns, the call reports SLT_ERR_TIMEOUT, and the next call works
     import torch
     cfg = workload("tiny")
     mesh = gpu_mesh(lib, cfg)
-    impatient = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=16, split=(9,), wait_spins=1)
+    impatient = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=16, split=(9,), wait_spins=1,
+                                executor=executor, cluster_size=4)
     v = torch.tensor(cfg["v0"], device="cuda")
     s = torch.tensor(cfg["s0"], device="cuda")
     with pytest.raises(lib.SltError) as e:
