@@ -175,16 +175,20 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
 /* ------------------------------------------------------------------ executor (Section 5.2)
  * nsteps time steps on device fields v, sigma (layout above, updated in place).
  * ricker: device array [nsteps] of the source time function at t_{n+1/2} (NULL: no source).
- * sched = NULL runs the plain untiled chain (one launch per loop, seventeen per step);
- * otherwise the schedule must come from slt_inspect on slt_mesh_chain(mesh) and each tile
- * (one CTA) executes its slice of every loop of its sub-chain in chain order:
+ * sched = NULL runs the plain untiled chain (one launch per loop, seventeen per step; four or
+ * more steps replay a CUDA graph of one step); otherwise the schedule must come from
+ * slt_inspect on slt_mesh_chain(mesh) and each tile executes its slice of every loop of its
+ * sub-chain in chain order:
  *  - executor 1 (colour phases, Algorithm 4 in shared-memory mode): one launch per colour and
- *    sub-chain, all tiles of a colour in parallel;
- *  - executor 0 (dataflow, default): one persistent launch for all nsteps; tiles are taken in
- *    (step, sub-chain, colour) order and each waits only for the tiles it overlaps (lower
- *    colours of its sub-chain, the previous sub-chain's tiles on its cells) - a linear
- *    extension of the same order.  Waits are bounded: SLT_ERR_TIMEOUT if one gives up.  This
- *    mode synchronises the stream before returning.
+ *    sub-chain, all tiles of a colour in parallel, one CTA per tile;
+ *  - executor 0 (dataflow, default): one persistent launch for all nsteps, one CTA per tile;
+ *    each (step, tile) node runs once the tiles it overlaps have finished (lower colours of its
+ *    sub-chain, the previous sub-chain's tiles on its cells): a linear extension of the same
+ *    order.  Waits are bounded: SLT_ERR_TIMEOUT if one gives up;
+ *  - executor 2: as executor 0 with one thread-block cluster of cluster_size CTAs per tile.
+ * The dataflow executors synchronise the stream before returning (they read their error flag);
+ * the untiled and colour-phase executors return after queueing their launches on `stream`.
+ * Results are bit-identical across the three executors for one schedule.
  * Work buffers are owned by the mesh. */
 int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                 double dt, int64_t nsteps, void* stream);
