@@ -51,3 +51,29 @@ def test_dataflow_queue_limit_is_refused(lib):
         lib.slt_execute(mesh, sched, v, s, None, 0.01, (1 << 31) // G + 1)
     assert e.value.code == -6
     lib.slt_execute(mesh, sched, v, s, None, 0.01, 2)   # the context is still usable
+
+
+@pytest.mark.parametrize("p,ts", [(1, 8), (2, 5), (3, 16)])
+def test_mirror_symmetric_source_on_the_gpu(lib, p, ts):
+    # the oracle's mirror pin, on the CUDA path: symmetric to round-off, tiled and untiled
+    import torch
+    import synth
+    from tests.test_oracle_dg import _mirror_mesh, _mirror_pairs, mirror_defect
+    m = _mirror_mesh()
+    nc = m["cell2vert"].shape[0]
+    mat = synth.homogeneous(m, 1.0, 2.0, 1.0)
+    dt = synth.cfl_dt(m, 2.0, p)
+    ricker = synth.ricker_series(5.0, dt, 30)
+    xs = np.array([0.5, 0.70])
+    vo, so = ElasticDG(m, p, *mat).run(np.zeros((nc, 2, (p + 1) * (p + 2) // 2)),
+                                       np.zeros((nc, 3, (p + 1) * (p + 2) // 2)), dt, 30, ricker, xs)
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], p, *mat, xs)
+    pairs = _mirror_pairs(m, p)
+    Np = (p + 1) * (p + 2) // 2
+    for sched in (None, lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=(9,))):
+        v = torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda")
+        s = torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda")
+        lib.slt_execute(mesh, sched, v, s, torch.tensor(ricker, device="cuda"), dt, 30)
+        vg, sg = v.cpu().numpy(), s.cpu().numpy()
+        assert mirror_defect(vg, sg, pairs) < 1e-12
+        assert rel_l2(vg, vo) < TOL and rel_l2(sg, so) < TOL

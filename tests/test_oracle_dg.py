@@ -256,3 +256,71 @@ def test_plane_wave_convergence_periodic(p):
         errs.append(np.sqrt(dg.inner_v(e, e)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[-1] >= p - 0.1, (errs, rates)
+
+
+def _mirror_mesh(nx=5, ny=4):
+    """Unit square of nx x ny squares, each cut into 4 triangles through its centre (all CCW):
+    symmetric under x -> 1 - x; with nx odd, the top and bottom triangles of the middle column
+    are themselves symmetric about x = 1/2."""
+    V = [(i / nx, j / ny) for j in range(ny + 1) for i in range(nx + 1)]
+    cells = []
+    for j in range(ny):
+        for i in range(nx):
+            a, b = j * (nx + 1) + i, j * (nx + 1) + i + 1
+            c, d = b + nx + 1, a + nx + 1
+            o = len(V)
+            V.append(((i + 0.5) / nx, (j + 0.5) / ny))
+            cells += [(a, b, o), (b, c, o), (c, d, o), (d, a, o)]
+    V = np.array(V)
+    c2v = np.array(cells, dtype=np.int32)
+    return {"cell2vert": c2v, "cellxy": V[c2v], "coords": V, "nvert": len(V)}
+
+
+def _mirror_pairs(m, p):
+    """(cell, node) -> (cell', node') with the node at (1 - x, y)."""
+    X = m["cellxy"]
+    nodes = np.array([(i / p, j / p) for j in range(p + 1) for i in range(p + 1 - j)])
+    xy = X[:, None, 0, :] + nodes[None, :, 0:1] * (X[:, None, 1, :] - X[:, None, 0, :]) \
+        + nodes[None, :, 1:2] * (X[:, None, 2, :] - X[:, None, 0, :])
+    key = {}
+    for c in range(xy.shape[0]):
+        cen = tuple(np.round(X[c].mean(0), 9))
+        for n in range(xy.shape[1]):
+            key[(cen, tuple(np.round(xy[c, n], 9)))] = (c, n)
+    pairs = []
+    for c in range(xy.shape[0]):
+        cen = X[c].mean(0)
+        mc = (round(1 - cen[0], 9), round(cen[1], 9))
+        for n in range(xy.shape[1]):
+            q = (round(1 - xy[c, n, 0], 9), round(xy[c, n, 1], 9))
+            pairs.append((c, n) + key[(mc, q)])
+    return np.array(pairs)
+
+
+def mirror_defect(v, s, pairs):
+    """Largest violation of the mirror symmetry (vx, sxy odd; vy, sxx, syy even), relative."""
+    c, n, c2, n2 = pairs.T
+    sign_v = np.array([-1.0, 1.0])[None, :]
+    sign_s = np.array([1.0, 1.0, -1.0])[None, :]
+    dv = v[c, :, n] - sign_v * v[c2, :, n2]
+    ds = s[c, :, n] - sign_s * s[c2, :, n2]
+    return max(np.abs(dv).max() / np.abs(v).max(), np.abs(ds).max() / np.abs(s).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_source_on_the_mirror_axis_gives_a_symmetric_field(p):
+    # a reflection-symmetric mesh, homogeneous material and a point source on the axis inside a
+    # cell that is itself symmetric: the discrete field must be mirror-symmetric (to round-off);
+    # a wrong sign or orientation in any facet term, or a misplaced source, breaks it
+    m = _mirror_mesh()
+    dg = ElasticDG(m, p, *synth.homogeneous(m, 1.0, 2.0, 1.0))
+    dt = synth.cfl_dt(m, 2.0, p)
+    ricker = synth.ricker_series(5.0, dt, 30)
+    v = np.zeros((dg.nc, 2, dg.Np))
+    s = np.zeros((dg.nc, 3, dg.Np))
+    v, s = dg.run(v, s, dt, 30, ricker, np.array([0.5, 0.70]))
+    assert np.abs(v).max() > 0
+    assert mirror_defect(v, s, _mirror_pairs(m, p)) < 1e-12
+    # and the check itself is sharp: a source off the axis breaks the symmetry
+    v2, s2 = dg.run(np.zeros_like(v), np.zeros_like(s), dt, 30, ricker, np.array([0.47, 0.70]))
+    assert mirror_defect(v2, s2, _mirror_pairs(m, p)) > 1e-3
