@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-p4", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--p4-steps", type=int, default=20)
     ap.add_argument("--multi-steps", type=int, default=20)
     ap.add_argument("--shots", type=int, default=64)
@@ -485,6 +486,20 @@ def main():
                    "frac": tiled_bytes * args.steps / kern_s / 1e9 / hbm_peak, "peak_kind": hbm_kind},
            "clocks": clocks,
            "gpu_launches": prof["chain_launches"] + prof["layout_launches"]}
+
+    if not args.no_cluster and args.executor == 0:
+        # the same workload with one thread-block cluster per large tile (fewer boundary cells)
+        csched = slt.slt_inspect(chain, tile_size=2048, split=(9,), executor=2, cluster_size=4)
+        cms, cprof, cclk = timed(csched, k_untiled, args.warmup)
+        ck = cprof["chain_ms"] * 1e-3
+        out["cluster"] = {"executor": "dataflow, one 4-CTA cluster per tile, ts 2048",
+                          "value": whole_job_rate(units_per_step * k_untiled, world, cms * 1e-3),
+                          "ms_per_step": cms / k_untiled, "steps": k_untiled,
+                          "roofline_frac_fp64": flops * k_untiled / ck / 1e12 / FP64_PEAK_TFLOPS,
+                          "traffic": ncu_traffic("k_dataflow_cluster<2,256>", "large_ts2048_c4", k_untiled)
+                          if args.scale == 1 else None,
+                          "clocks": cclk}
+        del csched
 
     if not args.no_untiled:
         K = k_untiled
