@@ -52,6 +52,31 @@ def whole_job_rate(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
+def bind_host_to_gpu(dev):
+    """Run this process on the CPUs of the GPU's NUMA node, so that page-locked host buffers are
+    allocated next to the GPU's host link.  Returns the node, or None when it is unknown (then
+    nothing changes)."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/numa_node" % bus) as f:
+            node = int(f.read())
+        if node < 0:
+            return None
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            cpus = set()
+            for part in f.read().strip().split(","):
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return node
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -514,6 +539,7 @@ def main():
 
     # end to end through the C ABI with pinned host buffers: every step copies the state in,
     # runs one step and copies the state out
+    numa = bind_host_to_gpu(local)
     hv = torch.zeros((nc, 2, Np), dtype=torch.float64).pin_memory()
     hs = torch.zeros((nc, 3, Np), dtype=torch.float64).pin_memory()
     hr = torch.tensor(cfg["ricker"], dtype=torch.float64).pin_memory()
@@ -527,7 +553,7 @@ def main():
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
     out["e2e"] = {"value": whole_job_rate(units_per_step * args.e2e_steps, world, e2e_s), "unit": "dof-updates/s",
                   "h2d_bytes_per_step": 5 * Np * nc * 8 + 8, "d2h_bytes_per_step": 5 * Np * nc * 8,
-                  "steps": args.e2e_steps}
+                  "steps": args.e2e_steps, "host_numa_node": numa}
 
     if not args.no_p4:
         out["p4"] = p4_timing(slt, synth, args, barrier)
