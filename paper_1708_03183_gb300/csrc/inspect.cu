@@ -49,9 +49,6 @@ __global__ void k_div(const int32_t* __restrict__ rank, int64_t n, int32_t ts, i
 __global__ void k_fill(int32_t* __restrict__ a, int64_t n, int32_t v) {
   GRID_STRIDE(e, n) a[e] = v;
 }
-__global__ void k_fill_u(uint32_t* __restrict__ a, int64_t n, uint32_t v) {
-  GRID_STRIDE(e, n) a[e] = v;
-}
 __global__ void k_iota_u(uint32_t* __restrict__ a, int64_t n) {
   GRID_STRIDE(e, n) a[e] = (uint32_t)e;
 }
