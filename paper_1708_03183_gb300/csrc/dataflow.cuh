@@ -117,11 +117,14 @@ __device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
   }
 }
 
-// One tile's slice of the loops [first, last) at step st, loops separated by CTA barriers.
+// One tile's slice of the loops [first, last) at step st, loops separated by CTA barriers.  A loop
+// with no item in this tile writes nothing, so it needs no barrier of its own (the condition is
+// the same for every thread of the CTA); the last loop always ends with one.
 template <int P, int BS, bool BATCH>
 __device__ __forceinline__ void run_tile(const Params& a, int first, int last, int t, long long st) {
   for (int J = first; J < last; ++J) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
+    if (b == e && J + 1 < last) continue;
     const int32_t* items = a.plan_items[J];
     if constexpr (BATCH) {  // every item for each shot of the slice, consecutive threads on consecutive shots
       const int64_t nwork = (int64_t)(e - b) * a.sg;
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_clust
     const int t = g - df.cum[k];
     for (int J = df.first[k]; J < df.last[k]; ++J) {
       const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
+      if (b == e && J + 1 < df.last[k]) continue;  // empty slice: no writes to order (same in every CTA)
       const int32_t* items = a.plan_items[J];
       for (int32_t i = b + (int32_t)(rank * BS + threadIdx.x); i < e; i += (int32_t)(C * BS))
         run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
