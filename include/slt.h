@@ -277,9 +277,12 @@ int slt_record(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const doubl
                int64_t nsteps, double* traces, void* stream);
 /* Misfit J = 1/2 dt sum_n sum_r |trace - data|^2 (data: device [nsteps][nrec][2]) of a run
    from rest, written to *misfit (host), and its gradient grad (device [3][ncell], caller
-   numbering: d/drho, d/dlambda, d/dmu) by the discrete adjoint: the forward run keeps (v, sigma)
-   every checkpoint_every steps (device memory: nsteps / k + k states), each segment is
-   recomputed forward (with sched's executor) and swept backwards in time.  Synchronises.
+   numbering: d/drho, d/dlambda, d/dmu) by the discrete adjoint: the forward run (with sched's
+   executor) keeps (v, sigma) every checkpoint_every = k steps (nsteps / k states); each segment
+   is recomputed forward by the untiled loops, which leave the operator intermediates of every
+   step (A sigma, E(A sigma), ABA sigma, E(v), AB v, E(AB v): 15 Np ncell doubles per step, k
+   steps) for the backward sweep to read; when that memory cannot be allocated, the segment
+   keeps its k states and the backward sweep recomputes them.  Synchronises.
    Uses the mesh's current material and source. */
 int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
                 int64_t nsteps, const double* data, int32_t checkpoint_every, double* grad, double* misfit,

@@ -270,7 +270,17 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
   const int64_t state = 5 * (int64_t)Np * ncp;  // V [2Np] then S [3Np], as in the work buffer
   double* V = m->work.p;
   double* S = m->work.p + 2 * (int64_t)Np * ncp;
-  DevBuf<double> ckpt(std::max<int64_t>(nseg, 1) * state), seg((int64_t)k * state);
+  DevBuf<double> ckpt(std::max<int64_t>(nseg, 1) * state), seg;
+  // the forward intermediates of every step of a segment (15 Np rows each), when memory allows;
+  // otherwise the segment keeps only its states and the reverse sweep recomputes them
+  const int64_t keep_rows = 15 * (int64_t)Np * ncp;
+  DevBuf<double> keep;
+  try {
+    keep.alloc((int64_t)k * keep_rows);
+  } catch (const Error&) {
+    keep.release();
+  }
+  if (!keep.p) seg.alloc((int64_t)k * state);
   DevBuf<double> traces(std::max<int64_t>(N * 2 * rec->n, 1)), Jd(1);
   DevBuf<double> adj(20 * (int64_t)Np * row), g(3 * row);
   double* vt = adj.p;
@@ -305,28 +315,51 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
   for (int64_t j = nseg - 1; j >= 0; --j) {
     const int64_t n0 = j * k, n1 = std::min<int64_t>(N, n0 + k);
     SLT_CUDA(cudaMemcpyAsync(V, ckpt.p + j * state, state * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int64_t n = n0; n < n1; ++n) {  // recompute: sigma^n before the step, v^{n+1/2} after it
-      double* slot = seg.p + (n - n0) * state;
+    for (int64_t n = n0; n < n1; ++n) {  // recompute the segment
+      if (keep.p) {  // the step's intermediates stay in its slot
+        exec_step_keep(m, ricker, dt, n, keep.p + (n - n0) * keep_rows, s);
+        continue;
+      }
+      double* slot = seg.p + (n - n0) * state;  // sigma^n before the step, v^{n+1/2} after it
       SLT_CUDA(cudaMemcpyAsync(slot + 2 * (int64_t)Np * ncp, S, 3 * (int64_t)Np * ncp * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
       exec_steps_work(m, sched, ricker, dt, n, 1, s);
       SLT_CUDA(cudaMemcpyAsync(slot, V, 2 * (int64_t)Np * ncp * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     for (int64_t n = n1 - 1; n >= n0; --n) {
-      const double* v = seg.p + (n - n0) * state;
-      const double* sig = v + 2 * (int64_t)Np * ncp;
+      const int64_t r = (int64_t)Np * ncp;
+      const double* kept = keep.p ? keep.p + (n - n0) * keep_rows : nullptr;
+      // forward intermediates of step n: kept, or recomputed from the segment's states
+      const double *Asig, *EAsig, *ABAsig, *Ev, *ABv, *EABv;
+      if (kept) {
+        Asig = kept;
+        EAsig = kept + 2 * r;
+        ABAsig = kept + 5 * r;
+        Ev = kept + 7 * r;
+        ABv = kept + 10 * r;
+        EABv = kept + 12 * r;
+      } else {
+        const double* v = seg.p + (n - n0) * state;
+        const double* sig = v + 2 * r;
+        op_E(m, v, T3a, s);        // Ev
+        hooke(T3a, T3b);           // Bv
+        op_A(m, T3b, T2a, s);      // ABv
+        op_E(m, T2a, T3b, s);      // E(ABv)
+        op_A(m, sig, T2c, s);      // A sigma (kept in T2c until the velocity update)
+        Ev = T3a;
+        ABv = T2a;
+        EABv = T3b;
+        Asig = T2c;
+        EAsig = ABAsig = nullptr;  // computed below, after T2a/T3a are free
+      }
       // stress update (adjoint st of sigma^{n+1})
-      op_E(m, v, T3a, s);        // Ev
-      hooke(T3a, T3b);           // Bv
-      op_A(m, T3b, T2a, s);      // ABv
-      op_E(m, T2a, T3b, s);      // E(ABv)
       op_A(m, st, T2b, s);       // A st
       op_E(m, T2b, T3c, s);      // E(A st)
       switch (P) {
-        case 1: k_grad_s<1><<<gr, 128, 0, s>>>(st, T3a, T3b, T3c, T2b, T2a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 2: k_grad_s<2><<<gr, 128, 0, s>>>(st, T3a, T3b, T3c, T2b, T2a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 3: k_grad_s<3><<<gr, 128, 0, s>>>(st, T3a, T3b, T3c, T2b, T2a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 4: k_grad_s<4><<<gr, 128, 0, s>>>(st, T3a, T3b, T3c, T2b, T2a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 1: k_grad_s<1><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 2: k_grad_s<2><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 3: k_grad_s<3><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 4: k_grad_s<4><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
       }
       hooke(T3c, T3a);           // BA st
       op_A(m, T3a, T2a, s);      // ABA st
@@ -335,18 +368,23 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
       k_inject<<<1, 128, 0, s>>>(vt, ncp, Np, rec->n, rec->w.p, rec->q.p, traces.p + n * 2 * rec->n,
                                  data + n * 2 * rec->n, m->mat.p, dt);
       // velocity update (adjoint vt of v^{n+1/2})
-      op_A(m, sig, T2a, s);      // A sigma
-      op_E(m, T2a, T3a, s);      // E(A sigma)
-      hooke(T3a, T3b);           // BA sigma
-      op_A(m, T3b, T2b, s);      // ABA sigma
+      if (!kept) {
+        SLT_CUDA(cudaMemcpyAsync(T2a, Asig, 2 * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        Asig = T2a;
+        op_E(m, Asig, T3a, s);   // E(A sigma)
+        hooke(T3a, T3b);         // BA sigma
+        op_A(m, T3b, T2b, s);    // ABA sigma
+        EAsig = T3a;
+        ABAsig = T2b;
+      }
       op_E(m, vt, T3b, s);       // E vt
       hooke(T3b, T3c);           // B vt
       op_A(m, T3c, T2c, s);      // AB vt
       switch (P) {
-        case 1: k_grad_v<1><<<gr, 128, 0, s>>>(vt, T2a, T2b, T2c, T3b, T3a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 2: k_grad_v<2><<<gr, 128, 0, s>>>(vt, T2a, T2b, T2c, T3b, T3a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 3: k_grad_v<3><<<gr, 128, 0, s>>>(vt, T2a, T2b, T2c, T3b, T3a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 4: k_grad_v<4><<<gr, 128, 0, s>>>(vt, T2a, T2b, T2c, T3b, T3a, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 1: k_grad_v<1><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 2: k_grad_v<2><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 3: k_grad_v<3><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 4: k_grad_v<4><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
       }
       op_E(m, T2c, T3a, s);      // E(AB vt)
       hooke(T3a, T3b);           // BAB vt

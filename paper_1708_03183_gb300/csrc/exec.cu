@@ -341,6 +341,46 @@ void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, doubl
   }
 }
 
+// One untiled step on the mesh's work fields that leaves its operator intermediates in `keep`
+// (rows of ncp, work order): A sigma [2Np], E(A sigma) [3Np], ABA sigma [2Np], E(v) [3Np],
+// AB v [2Np], E(AB v) [3Np] - the loops write them there instead of the scratch buffers (same
+// loop bodies, so the same numbers).  The adjoint's reverse sweep reads them back.
+void exec_step_keep(slt_mesh m, const double* ricker, double dt, int64_t step, double* keep, cudaStream_t s) {
+  Params a = make_params(m);
+  a.dt = dt;
+  a.c24 = dt * dt / 24.0;
+  a.ricker = ricker ? ricker + step : nullptr;
+  a.step = 0;
+  const int64_t r = m->Np * m->ncp;
+  double* kA = keep;             // A sigma
+  double* kEA = kA + 2 * r;      // E(A sigma)
+  double* kABA = kEA + 3 * r;    // ABA sigma
+  double* kEv = kABA + 2 * r;    // E(v)
+  double* kABv = kEv + 3 * r;    // AB v
+  double* kEABv = kABv + 2 * r;  // E(AB v)
+  Params a1 = a, a2 = a, a3 = a, a4 = a;
+  a1.buf[B_U1] = kA;     // loops 0-8: U1 = A sigma, E = E(A sigma), U2 = ABA sigma
+  a1.buf[B_E] = kEA;
+  a1.buf[B_U2] = kABA;
+  a2.buf[B_E] = kEv;     // loops 9-11: E = E(v), U1 = volume part of AB v
+  a2.buf[B_U1] = kABv;
+  a3.buf[B_U1] = kABv;   // loops 12-13: U1 = AB v
+  a4.buf[B_U1] = kABv;   // loops 14-16: E = E(AB v)
+  a4.buf[B_E] = kEABv;
+  auto run = [&](const Params& q, int first, int last) {
+    switch (m->p) {
+      case 1: launch_untiled_range<1>(q, first, last, s); break;
+      case 2: launch_untiled_range<2>(q, first, last, s); break;
+      case 3: launch_untiled_range<3>(q, first, last, s); break;
+      case 4: launch_untiled_range<4>(q, first, last, s); break;
+    }
+  };
+  run(a1, 0, 9);
+  run(a2, 9, 12);
+  run(a3, 12, 14);
+  run(a4, 14, 17);
+}
+
 // Operators on work-layout buffers (untiled loops with redirected operands), for the adjoint.
 void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s) {
   Params a = make_params(m);

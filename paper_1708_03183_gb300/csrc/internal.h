@@ -258,6 +258,7 @@ void exec_apply(slt_mesh m, int op, const double* in, double* out, cudaStream_t 
 void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, double dt, int64_t step0,
                      int64_t nsteps, cudaStream_t s);
 // A: stress-like [3Np][ncp] -> velocity rate [2Np][ncp]; E: velocity-like -> strain [3Np][ncp]
+void exec_step_keep(slt_mesh m, const double* ricker, double dt, int64_t step, double* keep, cudaStream_t s);
 void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s);
 void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s);
 // exec_batched.cu
