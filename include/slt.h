@@ -281,8 +281,9 @@ int slt_record(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const doubl
    executor) keeps (v, sigma) every checkpoint_every = k steps (nsteps / k states); each segment
    is recomputed forward by the untiled loops, which leave the operator intermediates of every
    step (A sigma, E(A sigma), ABA sigma, E(v), AB v, E(AB v): 15 Np ncell doubles per step, k
-   steps) for the backward sweep to read; when that memory cannot be allocated, the segment
-   keeps its k states and the backward sweep recomputes them.  Synchronises.
+   steps) for the backward sweep to read; with checkpoint_every = -k, or when that memory cannot
+   be allocated, the segment keeps only its k states (5 Np ncell doubles each) and the backward
+   sweep recomputes the intermediates (about 1.3x the time).  Synchronises.
    Uses the mesh's current material and source. */
 int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
                 int64_t nsteps, const double* data, int32_t checkpoint_every, double* grad, double* misfit,

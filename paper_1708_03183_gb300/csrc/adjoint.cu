@@ -263,7 +263,8 @@ void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
 }
 
 void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t N,
-                 const double* data, int32_t k, double* grad_out, double* J_host, cudaStream_t s) {
+                 const double* data, int32_t k_arg, double* grad_out, double* J_host, cudaStream_t s) {
+  const int32_t k = k_arg < 0 ? -k_arg : k_arg;  // k_arg < 0: segments keep states only
   const int Np = m->Np, P = m->p;
   const int64_t nc = m->nc, ncp = m->ncp, row = ncp;
   const int64_t nseg = (N + k - 1) / k;
@@ -275,10 +276,12 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
   // otherwise the segment keeps only its states and the reverse sweep recomputes them
   const int64_t keep_rows = 15 * (int64_t)Np * ncp;
   DevBuf<double> keep;
-  try {
-    keep.alloc((int64_t)k * keep_rows);
-  } catch (const Error&) {
-    keep.release();
+  if (k_arg > 0) {
+    try {
+      keep.alloc((int64_t)k * keep_rows);
+    } catch (const Error&) {
+      keep.release();
+    }
   }
   if (!keep.p) seg.alloc((int64_t)k * state);
   DevBuf<double> traces(std::max<int64_t>(N * 2 * rec->n, 1)), Jd(1);

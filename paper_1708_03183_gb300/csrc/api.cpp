@@ -675,7 +675,7 @@ int slt_adjoint(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
   REQUIRE(m && rec && data && grad && misfit, "null argument");
   REQUIRE(rec->mesh == m, "the receivers belong to another mesh");
   REQUIRE(nsteps >= 1 && std::isfinite(dt), "nsteps >= 1 and finite dt required");
-  REQUIRE(checkpoint_every >= 1, "checkpoint_every must be >= 1");
+  REQUIRE(checkpoint_every != 0 && checkpoint_every != INT32_MIN, "checkpoint_every must be nonzero");
   if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
   adjoint_run(m, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, as_stream(stream));
   API_END

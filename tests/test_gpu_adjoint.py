@@ -45,7 +45,8 @@ def test_record_matches_oracle(lib, p):
     assert rel_l2(tr.cpu().numpy(), want) < 1e-11
 
 
-@pytest.mark.parametrize("p,tiled,k", [(1, False, 7), (2, False, 30), (2, True, 7), (3, True, 11)])
+@pytest.mark.parametrize("p,tiled,k", [(1, False, 7), (2, False, 30), (2, True, 7), (3, True, 11),
+                                       (1, False, -7), (2, True, -7), (3, False, -30)])
 def test_adjoint_matches_oracle(lib, p, tiled, k):
     import torch
     m, p, model, dt, nsteps, ricker, xs, rec, data = _problem(p=p)
