@@ -208,9 +208,12 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
    Fields are device arrays with the shots innermost: v [ncell][2][Np][nshots],
    sigma [ncell][3][Np][nshots], updated in place.  Each (cell, shot) computes exactly what a
    single-field run of that shot computes.  sched = NULL: untiled chain (17 launches per step,
-   one thread per cell and shot); otherwise the dataflow executor (the schedule's executor must
-   be 0), each tile's items expanded over the shots.  profile (NULL = none) as in
-   slt_execute_profiled.  Synchronises.  Work memory: 15 Np ncell nshots doubles. */
+   one thread per cell and shot); otherwise the dataflow executor, each tile's items expanded
+   over the shots, in slices of the schedule's shots_per_cta (one persistent launch per slice).
+   profile (NULL = none) as in slt_execute_profiled.  Synchronises.  Work memory: 15 Np ncell
+   nshots doubles, kept by the mesh.  SLT_ERR_ARG for nshots outside 1..4096, a non-finite dt or
+   a source outside the mesh; SLT_ERR_UNSUPPORTED when the schedule's executor is not 0;
+   SLT_ERR_STATE for a schedule of another mesh. */
 int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const double* src_xy, double* v,
                         double* sigma, const double* ricker, double dt, int64_t nsteps, void* stream,
                         double* profile);
@@ -225,7 +228,10 @@ int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const
    (per-mesh dependency counters, no barrier across meshes), the degrees one after the other;
    untiled meshes run side by side on private streams forked from `stream`.  Synchronises;
    SLT_ERR_TIMEOUT if a wait gave up.  The meshes and schedules must outlive the group.
-   slt_execute_many = create, execute once, destroy. */
+   Errors: SLT_ERR_ARG for n outside 1..256, a null or repeated mesh, a null field or a
+   non-finite dt; SLT_ERR_STATE for a schedule of another mesh; SLT_ERR_UNSUPPORTED when tiled
+   meshes of one degree use different CTA sizes.  slt_execute_many = create, execute once,
+   destroy. */
 int slt_group_create(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, slt_group* out);
 int slt_group_destroy(slt_group group);
 int slt_group_execute(slt_group group, double* const* v, double* const* sigma, const double* const* ricker,
@@ -247,7 +253,9 @@ int slt_execute_many(int32_t n, const slt_mesh* meshes, const slt_schedule* sche
    fastest.  table (host, may be NULL): rows (tile_size, renumber, block_threads, shots_per_cta,
    ms per step), the untiled chain first (0, 0, 0, 0, ms); 1 + ntile * (shapes ? 2 : 1) *
    nblock * max(ngroup, 1) rows (ngroup counted as 1 when nshots = 1).  Allocates the candidate
-   fields (5 Np ncell nshots doubles) for the call; synchronises. */
+   fields (5 Np ncell nshots doubles) for the call; synchronises.  SLT_ERR_ARG for nshots outside
+   1..4096, 0..64 tile sizes, 1..4 CTA sizes (each 128, 256 or 384), 0..16 shot counts, steps
+   outside 1..1000, or nshots > 1 with an executor other than 0. */
 int slt_autotune(slt_mesh mesh, const slt_options* base, int32_t nshots, const int32_t* tile_sizes,
                  int32_t ntile, int32_t shapes, const int32_t* block_threads, int32_t nblock,
                  const int32_t* shots_per_cta, int32_t ngroup, int32_t steps, void* stream, slt_options* best,
