@@ -175,8 +175,8 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
 /* ------------------------------------------------------------------ executor (Section 5.2)
  * nsteps time steps on device fields v, sigma (layout above, updated in place).
  * ricker: device array [nsteps] of the source time function at t_{n+1/2} (NULL: no source).
- * sched = NULL runs the plain untiled chain (one launch per loop, seventeen per step; four or
- * more steps replay a CUDA graph of one step); otherwise the schedule must come from
+ * sched = NULL runs the plain untiled chain (ten launches per step, one per run of consecutive
+ * loops that need no value from another cell; four or more steps replay a CUDA graph of one step); otherwise the schedule must come from
  * slt_inspect on slt_mesh_chain(mesh) and each tile executes its slice of every loop of its
  * sub-chain in chain order:
  *  - executor 1 (colour phases, Algorithm 4 in shared-memory mode): one launch per colour and
@@ -207,7 +207,7 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
    own point sources src_xy [nshots][2] (host; NULL = no source), sharing the Ricker series.
    Fields are device arrays with the shots innermost: v [ncell][2][Np][nshots],
    sigma [ncell][3][Np][nshots], updated in place.  Each (cell, shot) computes exactly what a
-   single-field run of that shot computes.  sched = NULL: untiled chain (17 launches per step,
+   single-field run of that shot computes.  sched = NULL: untiled chain (10 launches per step,
    one thread per cell and shot); otherwise the dataflow executor, each tile's items expanded
    over the shots, in slices of the schedule's shots_per_cta (one persistent launch per slice).
    profile (NULL = none) as in slt_execute_profiled.  Synchronises.  Work memory: 15 Np ncell

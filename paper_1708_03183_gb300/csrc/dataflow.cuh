@@ -117,21 +117,22 @@ __device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
   }
 }
 
-// One tile's slice of the loops [first, last) at step st, loops separated by CTA barriers.  A loop
-// with no item in this tile writes nothing, so it needs no barrier of its own (the condition is
-// the same for every thread of the CTA); the last loop always ends with one.
+// One tile's slice of the segments of [first, last) at step st, segments separated by CTA
+// barriers.  A segment with no item in this tile writes nothing, so it needs no barrier of its own
+// (the condition is the same for every thread of the CTA); the last segment always ends with one.
 template <int P, int BS, bool BATCH>
 __device__ __forceinline__ void run_tile(const Params& a, int first, int last, int t, long long st) {
-  for (int J = first; J < last; ++J) {
+  for (int J = first; J < last; J = seg_end(J, last)) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
-    if (b == e && J + 1 < last) continue;
+    if (b == e && seg_end(J, last) < last) continue;
     const int32_t* items = a.plan_items[J];
+    const int H = phase_of(J);
     if constexpr (BATCH) {  // every item for each shot of the slice, consecutive threads on consecutive shots
       const int64_t nwork = (int64_t)(e - b) * a.sg;
       for (int64_t i = threadIdx.x; i < nwork; i += BS)
-        run_loop<P, DF_L2_ONLY, true>(a, J, items[b + i / a.sg], st, a.s0 + (int)(i % a.sg));
+        run_seg<P, DF_L2_ONLY, true>(a, H, items[b + i / a.sg], st, a.s0 + (int)(i % a.sg));
     } else {
-      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
+      for (int32_t i = b + threadIdx.x; i < e; i += BS) run_seg<P, DF_L2_ONLY, false>(a, H, items[i], st);
     }
     __syncthreads();
   }
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
 }
 
 // The same executor with one thread-block cluster per tile (large tiles, few boundary cells):
-// the cluster's CTAs share each loop's items of the tile, separated by a cluster barrier.  The
+// the cluster's CTAs share each segment's items of the tile, separated by a cluster barrier.  The
 // leader CTA's first thread takes nodes from the queue and publishes their successors; the node
 // reaches the other CTAs through `slot[cluster]`, ordered by the barrier.  Every CTA of a cluster
 // passes the same barriers and leaves together, so the barriers always complete.
@@ -206,12 +207,13 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_clust
     int k = 0;
     while (g >= df.cum[k + 1]) ++k;
     const int t = g - df.cum[k];
-    for (int J = df.first[k]; J < df.last[k]; ++J) {
+    for (int J = df.first[k]; J < df.last[k]; J = seg_end(J, df.last[k])) {
       const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
-      if (b == e && J + 1 < df.last[k]) continue;  // empty slice: no writes to order (same in every CTA)
+      if (b == e && seg_end(J, df.last[k]) < df.last[k]) continue;  // empty slice: no writes to order
       const int32_t* items = a.plan_items[J];
+      const int H = phase_of(J);
       for (int32_t i = b + (int32_t)(rank * BS + threadIdx.x); i < e; i += (int32_t)(C * BS))
-        run_loop<P, DF_L2_ONLY, false>(a, J, items[i], st);
+        run_seg<P, DF_L2_ONLY, false>(a, H, items[i], st);
       cl.sync();
     }
     if (rank == 0 && threadIdx.x == 0) df_publish(df.q, g, st);

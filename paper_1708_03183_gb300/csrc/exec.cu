@@ -38,24 +38,12 @@ namespace {
 
 #include "exec_body.cuh"
 
-// Untiled chain: loop J over every cell of the mesh (facet loops pull all interior or all
-// exterior faces of the cell).
-template <int P, int J>
-__global__ void __launch_bounds__(128) k_loop(Params a) {
+// Untiled chain: phase H (one or more consecutive loops, see run_phase) over every cell.
+template <int P, int H>
+__global__ void __launch_bounds__(128) k_phase(Params a) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (w >= a.nc) return;
-  int32_t item = (int32_t)w;
-  if (is_int_loop(J) || is_ext_loop(J)) {
-    int mask = 0;
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      bool interior = a.nbr[f * a.ncp + w] >= 0;
-      if (is_int_loop(J) ? interior : !interior) mask |= 1 << f;
-    }
-    if (!mask) return;
-    item = (int32_t)((w << 3) | mask);
-  }
-  run_loop<P, false, false>(a, J, item, (J == 16 && a.step_dev) ? (int64_t)*a.step_dev : a.step);
+  run_phase<P, H, false>(a, w, 0, (H == 9 && a.step_dev) ? (int64_t)*a.step_dev : a.step);
 }
 
 // advances the device step counter at the end of a graph-captured step
@@ -63,44 +51,45 @@ __global__ void k_step_inc(long long* step) { *step += 1; }
 
 #include "dataflow.cuh"
 
-// Tiled chain: one CTA per tile of one colour; the tile runs its slice of every loop of the
-// sub-chain [first, last) in order, loops separated by a CTA barrier.
+// Tiled chain: one CTA per tile of one colour; the tile runs its slice of every segment of the
+// sub-chain [first, last) in order, segments separated by a CTA barrier.
 template <int P, int BS>
 __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_tiled(Params a, int first, int last,
                                                                        const int32_t* __restrict__ tiles) {
   const int t = tiles[blockIdx.x];
-  for (int J = first; J < last; ++J) {
+  for (int J = first; J < last; J = seg_end(J, last)) {
     const int32_t b = a.plan_ptr[J][t], e = a.plan_ptr[J][t + 1];
     const int32_t* items = a.plan_items[J];
-    for (int32_t i = b + threadIdx.x; i < e; i += BS) run_loop<P, false, false>(a, J, items[i], a.step);
+    const int H = phase_of(J);
+    for (int32_t i = b + threadIdx.x; i < e; i += BS) run_seg<P, false, false>(a, H, items[i], a.step);
     __syncthreads();
   }
 }
 
-template <int P, int J>
-void launch_loop(const Params& a, cudaStream_t s);
+template <int P, int H>
+void launch_phase(const Params& a, cudaStream_t s);
 
+// The untiled loops [first, last) of the chain, as the fused phases that cover them exactly
+// (every caller's range starts and ends on a phase boundary).
 template <int P>
 void launch_untiled_range(const Params& a, int first, int last, cudaStream_t s) {
-  for (int J = first; J < last; ++J) {
-    switch (J) {
-      case 0: launch_loop<P, 0>(a, s); break;
-      case 1: launch_loop<P, 1>(a, s); break;
-      case 2: launch_loop<P, 2>(a, s); break;
-      case 3: launch_loop<P, 3>(a, s); break;
-      case 4: launch_loop<P, 4>(a, s); break;
-      case 5: launch_loop<P, 5>(a, s); break;
-      case 6: launch_loop<P, 6>(a, s); break;
-      case 7: launch_loop<P, 7>(a, s); break;
-      case 8: launch_loop<P, 8>(a, s); break;
-      case 9: launch_loop<P, 9>(a, s); break;
-      case 10: launch_loop<P, 10>(a, s); break;
-      case 11: launch_loop<P, 11>(a, s); break;
-      case 12: launch_loop<P, 12>(a, s); break;
-      case 13: launch_loop<P, 13>(a, s); break;
-      case 14: launch_loop<P, 14>(a, s); break;
-      case 15: launch_loop<P, 15>(a, s); break;
-      case 16: launch_loop<P, 16>(a, s); break;
+  for (int h = 0; h < kPhases; ++h) {
+    if (phase_first(h) < first || phase_first(h + 1) > last) {
+      if (phase_first(h) < last && phase_first(h + 1) > first)
+        fail(SLT_ERR_UNSUPPORTED, "loop range does not align with the untiled phases");
+      continue;
+    }
+    switch (h) {
+      case 0: launch_phase<P, 0>(a, s); break;
+      case 1: launch_phase<P, 1>(a, s); break;
+      case 2: launch_phase<P, 2>(a, s); break;
+      case 3: launch_phase<P, 3>(a, s); break;
+      case 4: launch_phase<P, 4>(a, s); break;
+      case 5: launch_phase<P, 5>(a, s); break;
+      case 6: launch_phase<P, 6>(a, s); break;
+      case 7: launch_phase<P, 7>(a, s); break;
+      case 8: launch_phase<P, 8>(a, s); break;
+      case 9: launch_phase<P, 9>(a, s); break;
     }
   }
   SLT_CUDA(cudaGetLastError());
@@ -187,12 +176,12 @@ Params make_params(slt_mesh m) {
   return a;
 }
 
-template <int P, int J>
-void launch_loop(const Params& a, cudaStream_t s) {
+template <int P, int H>
+void launch_phase(const Params& a, cudaStream_t s) {
   int threads = 128;
   int64_t blocks = (a.nc + threads - 1) / threads;
   g_rec.begin(0, s);
-  k_loop<P, J><<<(unsigned)blocks, threads, 0, s>>>(a);
+  k_phase<P, H><<<(unsigned)blocks, threads, 0, s>>>(a);
   g_rec.end(s);
 }
 
@@ -249,9 +238,9 @@ void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStre
   dataflow_check(sched, s);
 }
 
-// The untiled step as one CUDA graph (17 loop kernels and the step-counter increment), captured
+// The untiled step as one CUDA graph (the 10 phase kernels and the step-counter increment), captured
 // on the mesh's private stream and launched nsteps times on s: the host issues one launch per
-// step instead of seventeen.  The step index comes from a device counter the graph advances.
+// step instead of ten.  The step index comes from a device counter the graph advances.
 template <int P>
 void run_untiled_graph(slt_mesh m, Params a, int64_t nsteps, cudaStream_t s) {
   if (!m->step_dev.p) m->step_dev.alloc(1);
@@ -280,7 +269,7 @@ void run_untiled_graph(slt_mesh m, Params a, int64_t nsteps, cudaStream_t s) {
   SLT_CUDA(e);
   cudaError_t err = cudaSuccess;
   for (int64_t step = 0; step < nsteps && err == cudaSuccess; ++step) {
-    g_rec.begin(0, s, 18);
+    g_rec.begin(0, s, kPhases + 1);
     err = cudaGraphLaunch(exec, s);
     g_rec.end(s);
   }

@@ -22,46 +22,27 @@ namespace {
 #include "exec_body.cuh"
 #include "dataflow.cuh"
 
-template <int P, int J>
-__global__ void __launch_bounds__(128) k_loop_b(Params a) {
+// Untiled chain, phase H (see run_phase) over every (cell, shot).
+template <int P, int H>
+__global__ void __launch_bounds__(128) k_phase_b(Params a) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // over nc * S
   if (t >= a.nc * a.S) return;
-  const int64_t c = t / a.S;
-  const int s = (int)(t % a.S);
-  int32_t item = (int32_t)c;
-  if (is_facet_loop(J)) {
-    int mask = 0;
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      bool interior = a.nbr[f * a.ncp + c] >= 0;
-      if (is_int_loop(J) ? interior : !interior) mask |= 1 << f;
-    }
-    if (!mask) return;
-    item = (int32_t)((c << 3) | mask);
-  }
-  run_loop<P, false, true>(a, J, item, a.step, s);
+  run_phase<P, H, true>(a, t / a.S, (int)(t % a.S), a.step);
 }
 
 template <int P>
 void launch_untiled_b(const Params& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)((a.nc * a.S + 127) / 128);
-  k_loop_b<P, 0><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 1><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 2><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 3><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 4><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 5><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 6><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 7><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 8><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 9><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 10><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 11><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 12><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 13><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 14><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 15><<<blocks, 128, 0, s>>>(a);
-  k_loop_b<P, 16><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 0><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 1><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 2><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 3><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 4><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 5><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 6><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 7><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 8><<<blocks, 128, 0, s>>>(a);
+  k_phase_b<P, 9><<<blocks, 128, 0, s>>>(a);
   SLT_CUDA(cudaGetLastError());
 }
 
@@ -115,7 +96,7 @@ void run_batched(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaS
   }
   for (int64_t step = 0; step < nsteps; ++step) {
     a.step = step;
-    tm.begin(s, 17);
+    tm.begin(s, kPhases);
     launch_untiled_b<P>(a, s);
     tm.end(s);
   }

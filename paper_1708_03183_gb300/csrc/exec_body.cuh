@@ -33,7 +33,7 @@ __device__ __forceinline__ int fnode(int f, int k) {
   return f == 0 ? nidx(P, k, 0) : (f == 1 ? nidx(P, P - k, k) : nidx(P, 0, P - k));
 }
 
-// Field loads: plain (L1-cached) in the per-loop and colour-phase kernels; L2-only (ld.global.cg)
+// Field loads: plain (L1-cached) in the untiled and colour-phase kernels; L2-only (ld.global.cg)
 // in the persistent dataflow kernel, where other SMs write the fields during the launch.
 template <bool CG>
 __device__ __forceinline__ double ld(const double* p) {
@@ -57,8 +57,8 @@ struct Params {
   int64_t step;
   const long long* step_dev;        // if set, the step index is read here (graph-captured steps)
   double dt, c24;
-  const int32_t* plan_ptr[17];
-  const int32_t* plan_items[17];
+  const int32_t* plan_ptr[17];      // tiled: per segment (indexed by its first loop), tile offsets
+  const int32_t* plan_items[17];    // and items (work id << 4) | (vol << 3) | face mask
   // multi-shot layout
   int32_t S;                        // shots per cell (1 for one field)
   int32_t s0, sg;                   // tiled multi-shot runs: shots s0 .. s0 + sg - 1 of the S
@@ -84,10 +84,15 @@ __device__ __forceinline__ int64_t ncol(const Params& a, int64_t wn, int s) {  /
   else return wn;
 }
 
+// The bodies are built from parts that accumulate in registers: a phase chains the parts of
+// consecutive loops of one cell (volume, then interior faces, then free-surface faces) before a
+// single store, in the order the loops would apply them one by one.
+
+// volume part of A: u[comp * Np + i] = (div S)_i, the metric terms (rx .. sy) already over rho;
+// x row from (sxx, sxy), y row from (sxy, syy)
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const double* S, double* U, double rx,
+__device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const double* S, double* u, double rx,
                                         double ry, double sx, double sy) {
-  // U = div(S) scaled (rx.. already divided by rho): x row uses (sxx, sxy), y row (sxy, syy)
   constexpr int Np = np_of(P);
   const RefC& R = c_ref[P];
   const int64_t fs = fstride<BATCH>(a), w = q.f;
@@ -109,20 +114,88 @@ __device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const dou
         if ((dr_nz(P, i) >> j) & 1u) acc = fma(R.Dr[i * MAXNP + j], A[j], acc);
         if ((ds_nz(P, i) >> j) & 1u) acc = fma(R.Ds[i * MAXNP + j], B[j], acc);
       }
-      U[(int64_t)(comp * Np + i) * fs + w] = acc;
+      u[comp * Np + i] = acc;
     }
   }
 }
 
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void volB(const Params& a, const Pos& q, const double* S, double* U) {
+__device__ __forceinline__ void volB_part(const Params& a, const Pos& q, const double* S, double* u) {
   const int64_t n = a.ncp, c = q.c;
   double ir = a.mat[c];
-  vol_div<P, CG, BATCH>(a, q, S, U, a.geo[c] * ir, a.geo[n + c] * ir, a.geo[2 * n + c] * ir, a.geo[3 * n + c] * ir);
+  vol_div<P, CG, BATCH>(a, q, S, u, a.geo[c] * ir, a.geo[n + c] * ir, a.geo[2 * n + c] * ir, a.geo[3 * n + c] * ir);
 }
 
+// interior faces of A (faces in mask): u += -(F/2 rho) Lift ((S - S_nb) n)
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void volD(const Params& a, const Pos& q, const double* V, double* E) {
+__device__ __forceinline__ void intB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
+  constexpr int Np = np_of(P), Nfp = P + 1;
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const double ir = a.mat[c];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const int32_t nb = a.nbr[f * n + c];
+    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
+    const int fn = (nb >> 1) & 3, flip = nb & 1;
+    const double sc = -0.5 * a.fgeo[(3 * f + 2) * n + c] * ir;
+    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
+    double gx[Nfp], gy[Nfp];
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int i0 = fnode<P>(f, k);
+      const int i1 = fnode<P>(fn, flip ? P - k : k);
+      double dxx = ld<CG>(&S[(int64_t)i0 * fs + w]) - ld<CG>(&S[(int64_t)i1 * fs + wn]);
+      double dyy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(Np + i1) * fs + wn]);
+      double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * fs + wn]);
+      gx[k] = fma(dxy, ny, dxx * nx);
+      gy[k] = fma(dyy, ny, dxy * nx);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i)
+#pragma unroll
+      for (int k = 0; k < Nfp; ++k) {
+        u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
+        u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
+      }
+  }
+}
+
+// free-surface faces of A (faces in mask): u += -(F/rho) Lift (S n)
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void extB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
+  constexpr int Np = np_of(P), Nfp = P + 1;
+  const RefC& R = c_ref[P];
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const double ir = a.mat[c];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const double sc = -a.fgeo[(3 * f + 2) * n + c] * ir;
+    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
+    double gx[Nfp], gy[Nfp];
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int i0 = fnode<P>(f, k);
+      double sxx = ld<CG>(&S[(int64_t)i0 * fs + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]),
+             sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]);
+      gx[k] = fma(sxy, ny, sxx * nx);
+      gy[k] = fma(syy, ny, sxy * nx);
+    }
+#pragma unroll
+    for (int i = 0; i < Np; ++i)
+#pragma unroll
+      for (int k = 0; k < Nfp; ++k) {
+        u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
+        u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
+      }
+  }
+}
+
+// volume part of E: e = (dvx/dx, dvy/dy, dvx/dy + dvy/dx) at the nodes, e[comp * Np + i]
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void volD_part(const Params& a, const Pos& q, const double* V, double* e) {
   constexpr int Np = np_of(P);
   const RefC& R = c_ref[P];
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
@@ -147,129 +220,18 @@ __device__ __forceinline__ void volD(const Params& a, const Pos& q, const double
         dsy = fma(R.Ds[i * MAXNP + j], vy[j], dsy);
       }
     }
-    E[(int64_t)i * fs + w] = fma(sx, dsx, rx * drx);
-    E[(int64_t)(Np + i) * fs + w] = fma(sy, dsy, ry * dry);
-    E[(int64_t)(2 * Np + i) * fs + w] = fma(sx, dsy, fma(rx, dry, fma(sy, dsx, ry * drx)));
+    e[i] = fma(sx, dsx, rx * drx);
+    e[Np + i] = fma(sy, dsy, ry * dry);
+    e[2 * Np + i] = fma(sx, dsy, fma(rx, dry, fma(sy, dsx, ry * drx)));
   }
 }
 
-// S1 = C E at the nodes, then U = div(S1)/rho
+// interior faces of E (faces in mask): e += -(F/2) Lift sym((V - V_nb) (x) n)
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void hookeB(const Params& a, const Pos& q, const double* E, double* S1, double* U) {
-  constexpr int Np = np_of(P);
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
-  double l2m = fma(2.0, mu, lam);
-#pragma unroll
-  for (int j = 0; j < Np; ++j) {
-    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
-           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
-    S1[(int64_t)j * fs + w] = fma(lam, eyy, l2m * exx);
-    S1[(int64_t)(Np + j) * fs + w] = fma(lam, exx, l2m * eyy);
-    S1[(int64_t)(2 * Np + j) * fs + w] = mu * g;
-  }
-  volB<P, CG, BATCH>(a, q, S1, U);
-}
-
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void intB(const Params& a, const Pos& q, int mask, const double* S, double* U) {
+__device__ __forceinline__ void intD_part(const Params& a, const Pos& q, int mask, const double* V, double* e) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  const double ir = a.mat[c];
-  double ax[Np], ay[Np];  // the increments accumulate onto the current values of U
-#pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    ax[i] = ld<CG>(&U[(int64_t)i * fs + w]);
-    ay[i] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]);
-  }
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    if (!((mask >> f) & 1)) continue;
-    const int32_t nb = a.nbr[f * n + c];
-    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
-    const int fn = (nb >> 1) & 3, flip = nb & 1;
-    const double sc = -0.5 * a.fgeo[(3 * f + 2) * n + c] * ir;
-    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
-    double gx[Nfp], gy[Nfp];
-#pragma unroll
-    for (int k = 0; k < Nfp; ++k) {
-      const int i0 = fnode<P>(f, k);
-      const int i1 = fnode<P>(fn, flip ? P - k : k);
-      double dxx = ld<CG>(&S[(int64_t)i0 * fs + w]) - ld<CG>(&S[(int64_t)i1 * fs + wn]);
-      double dyy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(Np + i1) * fs + wn]);
-      double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * fs + wn]);
-      gx[k] = fma(dxy, ny, dxx * nx);
-      gy[k] = fma(dyy, ny, dxy * nx);
-    }
-#pragma unroll
-    for (int i = 0; i < Np; ++i)
-#pragma unroll
-      for (int k = 0; k < Nfp; ++k) {
-        ax[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], ax[i]);
-        ay[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], ay[i]);
-      }
-  }
-#pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * fs + w] = ax[i];
-    U[(int64_t)(Np + i) * fs + w] = ay[i];
-  }
-}
-
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void extB(const Params& a, const Pos& q, int mask, const double* S, double* U) {
-  constexpr int Np = np_of(P), Nfp = P + 1;
-  const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  const double ir = a.mat[c];
-  double ax[Np], ay[Np];  // the increments accumulate onto the current values of U
-#pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    ax[i] = ld<CG>(&U[(int64_t)i * fs + w]);
-    ay[i] = ld<CG>(&U[(int64_t)(Np + i) * fs + w]);
-  }
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    if (!((mask >> f) & 1)) continue;
-    const double sc = -a.fgeo[(3 * f + 2) * n + c] * ir;
-    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
-    double gx[Nfp], gy[Nfp];
-#pragma unroll
-    for (int k = 0; k < Nfp; ++k) {
-      const int i0 = fnode<P>(f, k);
-      double sxx = ld<CG>(&S[(int64_t)i0 * fs + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]),
-             sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]);
-      gx[k] = fma(sxy, ny, sxx * nx);
-      gy[k] = fma(syy, ny, sxy * nx);
-    }
-#pragma unroll
-    for (int i = 0; i < Np; ++i)
-#pragma unroll
-      for (int k = 0; k < Nfp; ++k) {
-        ax[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], ax[i]);
-        ay[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], ay[i]);
-      }
-  }
-#pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    U[(int64_t)i * fs + w] = ax[i];
-    U[(int64_t)(Np + i) * fs + w] = ay[i];
-  }
-}
-
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void intD(const Params& a, const Pos& q, int mask, const double* V, double* E) {
-  constexpr int Np = np_of(P), Nfp = P + 1;
-  const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  double exx[Np], eyy[Np], eg[Np];  // the increments accumulate onto the current values of E
-#pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    exx[i] = ld<CG>(&E[(int64_t)i * fs + w]);
-    eyy[i] = ld<CG>(&E[(int64_t)(Np + i) * fs + w]);
-    eg[i] = ld<CG>(&E[(int64_t)(2 * Np + i) * fs + w]);
-  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!((mask >> f) & 1)) continue;
@@ -294,17 +256,72 @@ __device__ __forceinline__ void intD(const Params& a, const Pos& q, int mask, co
         lx = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dx[k], lx);
         ly = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dy[k], ly);
       }
-      exx[i] = fma(cx, lx, exx[i]);
-      eyy[i] = fma(cy, ly, eyy[i]);
-      eg[i] = fma(cy, lx, fma(cx, ly, eg[i]));
+      e[i] = fma(cx, lx, e[i]);
+      e[Np + i] = fma(cy, ly, e[Np + i]);
+      e[2 * Np + i] = fma(cy, lx, fma(cx, ly, e[2 * Np + i]));
     }
   }
+}
+
+template <int R, bool CG, bool BATCH>
+__device__ __forceinline__ void load_rows(const Params& a, const Pos& q, const double* X, double* x) {
+  const int64_t fs = fstride<BATCH>(a), w = q.f;
 #pragma unroll
-  for (int i = 0; i < Np; ++i) {
-    E[(int64_t)i * fs + w] = exx[i];
-    E[(int64_t)(Np + i) * fs + w] = eyy[i];
-    E[(int64_t)(2 * Np + i) * fs + w] = eg[i];
+  for (int r = 0; r < R; ++r) x[r] = ld<CG>(&X[(int64_t)r * fs + w]);
+}
+template <int R, bool BATCH>
+__device__ __forceinline__ void store_rows(const Params& a, const Pos& q, double* X, const double* x) {
+  const int64_t fs = fstride<BATCH>(a), w = q.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) X[(int64_t)r * fs + w] = x[r];
+}
+
+// ---- bodies of the phases: a phase is a run of consecutive loops of the chain that write one
+// cell's output and read nothing another thread writes during the run.  One work item covers a
+// cell's share of every loop of the run: `vol` = the cell loop of the run, imask / emask = the
+// interior / free-surface faces of its facet loops.  Without `vol` the faces accumulate onto the
+// stored output (the cell loop ran in another tile).
+
+// volume part of A (U = div(S)/rho) when vol, else U as stored; then the faces of imask, emask
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void segA(const Params& a, const Pos& q, bool vol, int imask, int emask,
+                                     const double* S, double* U) {
+  double u[2 * np_of(P)];
+  if (vol) volB_part<P, CG, BATCH>(a, q, S, u);
+  else load_rows<2 * np_of(P), CG, BATCH>(a, q, U, u);
+  intB_part<P, CG, BATCH>(a, q, imask, S, u);
+  extB_part<P, CG, BATCH>(a, q, emask, S, u);
+  store_rows<2 * np_of(P), BATCH>(a, q, U, u);
+}
+// volume part of E(V) when vol, else E as stored; then the interior faces of imask
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void segE(const Params& a, const Pos& q, bool vol, int imask, const double* V,
+                                     double* E) {
+  double e[3 * np_of(P)];
+  if (vol) volD_part<P, CG, BATCH>(a, q, V, e);
+  else load_rows<3 * np_of(P), CG, BATCH>(a, q, E, e);
+  intD_part<P, CG, BATCH>(a, q, imask, V, e);
+  store_rows<3 * np_of(P), BATCH>(a, q, E, e);
+}
+
+// S1 = C E at the nodes, then U = div(S1)/rho
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void hookeB(const Params& a, const Pos& q, const double* E, double* S1, double* U) {
+  constexpr int Np = np_of(P);
+  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
+  double l2m = fma(2.0, mu, lam);
+#pragma unroll
+  for (int j = 0; j < Np; ++j) {
+    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
+           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
+    S1[(int64_t)j * fs + w] = fma(lam, eyy, l2m * exx);
+    S1[(int64_t)(Np + j) * fs + w] = fma(lam, exx, l2m * eyy);
+    S1[(int64_t)(2 * Np + j) * fs + w] = mu * g;
   }
+  double u[2 * np_of(P)];
+  volB_part<P, CG, BATCH>(a, q, S1, u);
+  store_rows<2 * np_of(P), BATCH>(a, q, U, u);
 }
 
 template <int P, bool CG, bool BATCH>
@@ -359,39 +376,65 @@ __device__ __forceinline__ void updS(const Params& a, const Pos& q, int64_t step
   }
 }
 
-__host__ __device__ constexpr bool is_int_loop(int J) { return J == 1 || J == 4 || J == 6 || J == 10 || J == 12 || J == 15; }
-__host__ __device__ constexpr bool is_ext_loop(int J) { return J == 2 || J == 7 || J == 13; }
-__host__ __device__ constexpr bool is_facet_loop(int J) { return is_int_loop(J) || is_ext_loop(J); }
-
-// one iteration of loop J for shot s; item = cell work id (cell loops) or (work id << 3) | face
-// mask (facet loops)
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void run_loop(const Params& a, int J, int32_t item, int64_t step, int s = 0) {
+// phase H at one (cell, shot)
+template <int P, int H, bool CG, bool BATCH>
+__device__ __forceinline__ void phase_body(const Params& a, const Pos& q, bool vol, int imask, int emask,
+                                           int64_t step) {
   double* const* b = a.buf;
+  if constexpr (H == 0) segA<P, CG, BATCH>(a, q, vol, imask, emask, b[B_S], b[B_U1]);
+  else if constexpr (H == 1) segE<P, CG, BATCH>(a, q, vol, imask, b[B_U1], b[B_E]);
+  else if constexpr (H == 2) hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U2]);
+  else if constexpr (H == 3) segA<P, CG, BATCH>(a, q, false, imask, emask, b[B_S1], b[B_U2]);
+  else if constexpr (H == 4) updV<P, CG, BATCH>(a, q);
+  else if constexpr (H == 5) segE<P, CG, BATCH>(a, q, vol, imask, b[B_V], b[B_E]);
+  else if constexpr (H == 6) hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U1]);
+  else if constexpr (H == 7) segA<P, CG, BATCH>(a, q, false, imask, emask, b[B_S1], b[B_U1]);
+  else if constexpr (H == 8) segE<P, CG, BATCH>(a, q, vol, imask, b[B_U1], b[B_E]);
+  else updS<P, CG, BATCH>(a, q, step);
+}
+
+// the faces of `mask` that have a neighbour (interior) and those that do not (free surface)
+__device__ __forceinline__ void split_mask(const Params& a, int64_t c, int mask, int& imask, int& emask) {
+  imask = 0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+    if (((mask >> f) & 1) && a.nbr[f * a.ncp + c] >= 0) imask |= 1 << f;
+  emask = mask & ~imask;
+}
+
+// Untiled: phase H over every face of cell w, shot s
+template <int P, int H, bool BATCH>
+__device__ __forceinline__ void run_phase(const Params& a, int64_t w, int s, int64_t step) {
   Pos q;
-  q.c = is_facet_loop(J) ? (int64_t)(item >> 3) : (int64_t)item;
+  q.c = w;
+  q.s = s;
+  q.f = BATCH ? w * a.S + s : w;
+  int imask, emask;
+  split_mask(a, w, 7, imask, emask);
+  phase_body<P, H, false, BATCH>(a, q, true, imask, emask, step);
+}
+
+// Tiled: one item of the segment of phase H, item = (work id << 4) | (vol << 3) | face mask
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void run_seg(const Params& a, int H, int32_t item, int64_t step, int s = 0) {
+  Pos q;
+  q.c = (int64_t)(item >> 4);
   q.s = s;
   q.f = BATCH ? q.c * a.S + s : q.c;
-  const int mask = item & 7;
-  switch (J) {
-    case 0: volB<P, CG, BATCH>(a, q, b[B_S], b[B_U1]); break;
-    case 1: intB<P, CG, BATCH>(a, q, mask, b[B_S], b[B_U1]); break;
-    case 2: extB<P, CG, BATCH>(a, q, mask, b[B_S], b[B_U1]); break;
-    case 3: volD<P, CG, BATCH>(a, q, b[B_U1], b[B_E]); break;
-    case 4: intD<P, CG, BATCH>(a, q, mask, b[B_U1], b[B_E]); break;
-    case 5: hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U2]); break;
-    case 6: intB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U2]); break;
-    case 7: extB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U2]); break;
-    case 8: updV<P, CG, BATCH>(a, q); break;
-    case 9: volD<P, CG, BATCH>(a, q, b[B_V], b[B_E]); break;
-    case 10: intD<P, CG, BATCH>(a, q, mask, b[B_V], b[B_E]); break;
-    case 11: hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U1]); break;
-    case 12: intB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U1]); break;
-    case 13: extB<P, CG, BATCH>(a, q, mask, b[B_S1], b[B_U1]); break;
-    case 14: volD<P, CG, BATCH>(a, q, b[B_U1], b[B_E]); break;
-    case 15: intD<P, CG, BATCH>(a, q, mask, b[B_U1], b[B_E]); break;
-    case 16: updS<P, CG, BATCH>(a, q, step); break;
-    default: break;
+  const bool vol = (item >> 3) & 1;
+  int imask, emask;
+  split_mask(a, q.c, item & 7, imask, emask);
+  switch (H) {
+    case 0: phase_body<P, 0, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 1: phase_body<P, 1, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 2: phase_body<P, 2, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 3: phase_body<P, 3, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 4: phase_body<P, 4, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 5: phase_body<P, 5, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 6: phase_body<P, 6, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 7: phase_body<P, 7, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 8: phase_body<P, 8, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    default: phase_body<P, 9, CG, BATCH>(a, q, vol, imask, emask, step); break;
   }
 }
 

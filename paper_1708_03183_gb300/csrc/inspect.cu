@@ -237,35 +237,45 @@ __global__ void k_lm_local(const uint32_t* __restrict__ tile, const uint32_t* __
 }
 
 // executor plan of a facet loop: entries (tile, work id, face bit), sorted, OR-reduced per cell
-__global__ void k_plan_facet_keys(const int32_t* __restrict__ map, const int8_t* __restrict__ face, int64_t nslot,
-                                  const int32_t* __restrict__ iperm, uint32_t* __restrict__ wid, uint32_t* __restrict__ slot) {
-  GRID_STRIDE(s, nslot) {
-    wid[s] = (uint32_t)iperm[map[s]];
-    slot[s] = (uint32_t)s;
+// segment plan entries: one per (iteration, cell it writes) of a cell loop (vol bit) ...
+__global__ void k_seg_cells(const int32_t* __restrict__ sig, const int32_t* __restrict__ iperm, int64_t n,
+                            uint32_t* __restrict__ tile, uint32_t* __restrict__ wid, uint32_t* __restrict__ bits) {
+  GRID_STRIDE(p, n) {
+    tile[p] = (uint32_t)sig[p];
+    wid[p] = (uint32_t)iperm[p];
+    bits[p] = 8u;
   }
 }
-__global__ void k_plan_facet_flags(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid, int64_t n,
+// ... and of a facet loop: slot p = facet * a + side, the face bit of that side's cell
+__global__ void k_seg_facets(const int32_t* __restrict__ map, const int8_t* __restrict__ face, int64_t ns, int a,
+                             const int32_t* __restrict__ sig, const int32_t* __restrict__ iperm,
+                             uint32_t* __restrict__ tile, uint32_t* __restrict__ wid, uint32_t* __restrict__ bits) {
+  GRID_STRIDE(p, ns) {
+    tile[p] = (uint32_t)sig[p / a];
+    wid[p] = (uint32_t)iperm[map[p]];
+    bits[p] = 1u << face[p];
+  }
+}
+// first entry of each run of equal (tile, work id) in sorted order
+__global__ void k_run_heads(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid, int64_t n,
                                    int32_t* __restrict__ flag) {
   GRID_STRIDE(p, n) flag[p] = (p == 0 || tile[p] != tile[p - 1] || wid[p] != wid[p - 1]);
 }
-__global__ void k_plan_facet_emit(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid,
-                                  const uint32_t* __restrict__ slot, const int8_t* __restrict__ face,
-                                  const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
-                                  int32_t* __restrict__ items, uint32_t* __restrict__ utile) {
+// one item per run: the work id and the union of the run's bits
+__global__ void k_seg_emit(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ wid,
+                           const uint32_t* __restrict__ bits, const int32_t* __restrict__ flag,
+                           const int32_t* __restrict__ pos, int64_t n, int32_t* __restrict__ items,
+                           uint32_t* __restrict__ utile) {
   GRID_STRIDE(p, n) if (flag[p]) {
-    int mask = 0;
-    for (int64_t q = p; q < n && tile[q] == tile[p] && wid[q] == wid[p]; ++q) mask |= 1 << face[slot[q]];
-    items[pos[p]] = (int32_t)((wid[p] << 3) | (uint32_t)mask);
+    uint32_t b = 0;
+    for (int64_t q = p; q < n && tile[q] == tile[p] && wid[q] == wid[p]; ++q) b |= bits[q];
+    items[pos[p]] = (int32_t)((wid[p] << 4) | b);
     utile[pos[p]] = tile[p];
   }
 }
-// facet pull items: full masks (7) first, then by decreasing mask
-__global__ void k_mask_key(const int32_t* __restrict__ items, int64_t n, uint32_t* __restrict__ key) {
-  GRID_STRIDE(p, n) key[p] = 7u - (uint32_t)(items[p] & 7);
-}
-__global__ void k_gather_iperm(const int32_t* __restrict__ iperm, const uint32_t* __restrict__ e, int64_t n,
-                               int32_t* __restrict__ out) {
-  GRID_STRIDE(p, n) out[p] = iperm[e[p]];
+// sort key of an item inside its tile: full flags (vol and three faces) first
+__global__ void k_flag_key(const int32_t* __restrict__ items, int64_t n, uint32_t* __restrict__ key) {
+  GRID_STRIDE(p, n) key[p] = 15u - (uint32_t)(items[p] & 15);
 }
 
 struct InverseMap {
@@ -506,65 +516,72 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
   d_f2f.upload(mesh->f2f.data(), mesh->nfi * 2, s);
   d_e2f.upload(mesh->e2f.data(), mesh->nfe, s);
   const int nl = sub.last - sub.first;
+  sub.plan_ptr.clear();
+  sub.plan_items.clear();
   sub.plan_ptr.resize(nl);
   sub.plan_items.resize(nl);
+  if (mesh->nc >= (int64_t(1) << 27)) fail(SLT_ERR_UNSUPPORTED, "the tiled executors take below 2^27 cells");
   const int tbits = bits_for(std::max(m - 1, 1)), wbits = bits_for(std::max<int64_t>(mesh->nc - 1, 1));
-  for (int jj = 0; jj < nl; ++jj) {
-    const LoopH& L = sched->loops[sub.first + jj];
-    const int32_t* sig = sub.sigma[jj].p;
-    sub.plan_ptr[jj].alloc(m + 1);
-    if (L.set == 0) {  // cell loop: work ids sorted by (tile, work id)
-      int64_t n = mesh->nc;
-      DevBuf<uint32_t> tile(n), wid(n), order;
-      DevBuf<uint32_t> e(n);
-      k_iota_u<<<grid_for(n), 256, 0, s>>>(e.p, n);
-      k_gather_div<<<grid_for(n), 256, 0, s>>>(sig, e.p, n, 1, tile.p);
-      k_gather_div<<<grid_for(n), 256, 0, s>>>(d_iperm.p, e.p, n, 1, wid.p);
-      sort_by_two(tile, tbits, wid, wbits, n, order, s);
-      sub.plan_items[jj].alloc(n);
-      k_gather_iperm<<<grid_for(n), 256, 0, s>>>(d_iperm.p, order.p, n, sub.plan_items[jj].p);
-      lower_bound_offsets(tile.p, n, m, sub.plan_ptr[jj].p, s);
-    } else {  // facet loop: (work id, face mask) per touched cell, sorted by (tile, work id)
-      const bool interior = L.set == 1;
-      const int a = interior ? 2 : 1;
-      const int64_t nf = interior ? mesh->nfi : mesh->nfe, ns = nf * a;
-      if (ns == 0) {
-        k_fill<<<grid_for(m + 1), 256, 0, s>>>(sub.plan_ptr[jj].p, m + 1, 0);
-        sub.plan_items[jj].alloc(1);
-        continue;
-      }
-      const int32_t* map = interior ? d_f2c.p : d_e2c.p;
-      const int8_t* face = interior ? d_f2f.p : d_e2f.p;
-      DevBuf<uint32_t> wid(ns), slot(ns), tile(ns), order;
-      k_plan_facet_keys<<<grid_for(ns), 256, 0, s>>>(map, face, ns, d_iperm.p, wid.p, slot.p);
-      k_gather_div<<<grid_for(ns), 256, 0, s>>>(sig, slot.p, ns, a, tile.p);
-      sort_by_two(tile, tbits, wid, wbits, ns, order, s);
-      DevBuf<uint32_t> swid(ns);
-      k_gather_div<<<grid_for(ns), 256, 0, s>>>((const int32_t*)wid.p, order.p, ns, 1, swid.p);
-      DevBuf<int32_t> flag(ns), pos(ns + 1);
-      k_plan_facet_flags<<<grid_for(ns), 256, 0, s>>>(tile.p, swid.p, ns, flag.p);
-      exclusive_scan_i32(flag.p, pos.p, ns, s);
-      int32_t nu = 0;
-      SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + ns, 4, cudaMemcpyDeviceToHost, s));
-      SLT_CUDA(cudaStreamSynchronize(s));
-      sub.plan_items[jj].alloc(std::max(nu, 1));
-      DevBuf<uint32_t> utile(std::max(nu, 1));
-      k_plan_facet_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, swid.p, order.p, face, flag.p, pos.p, ns,
-                                                     sub.plan_items[jj].p, utile.p);
-      // inside each tile, items with the same face mask side by side (stable, so work-id order
-      // within a mask): a warp then runs only the faces its lanes have
-      {
-        DevBuf<uint32_t> mk(nu), ord;
-        k_mask_key<<<grid_for(nu), 256, 0, s>>>(sub.plan_items[jj].p, nu, mk.p);
-        DevBuf<uint32_t> ut(nu);
-        SLT_CUDA(cudaMemcpyAsync(ut.p, utile.p, (size_t)nu * 4, cudaMemcpyDeviceToDevice, s));
-        sort_by_two(ut, tbits, mk, 3, nu, ord, s);
-        DevBuf<int32_t> sorted(std::max(nu, 1));
-        k_gather_div<<<grid_for(nu), 256, 0, s>>>(sub.plan_items[jj].p, ord.p, nu, 1, (uint32_t*)sorted.p);
-        std::swap(sub.plan_items[jj], sorted);
-      }
-      lower_bound_offsets(utile.p, nu, m, sub.plan_ptr[jj].p, s);
+  // one plan per segment (the part of a phase inside the sub-chain), stored at its first loop:
+  // per tile, one item per cell the segment's loops touch, (work id << 4) | (vol << 3) | faces
+  for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+    const int J1 = seg_end(J0, sub.last);
+    int64_t n = 0;
+    for (int J = J0; J < J1; ++J) {
+      const int set = sched->loops[J].set;
+      n += set == 0 ? mesh->nc : set == 1 ? 2 * mesh->nfi : mesh->nfe;
     }
+    const int jj = J0 - sub.first;
+    sub.plan_ptr[jj].alloc(m + 1);
+    if (n == 0) {
+      k_fill<<<grid_for(m + 1), 256, 0, s>>>(sub.plan_ptr[jj].p, m + 1, 0);
+      sub.plan_items[jj].alloc(1);
+      continue;
+    }
+    // entries (tile, work id, bits) of every iteration of the segment's loops and cell it writes
+    DevBuf<uint32_t> tile(n), wid(n), bits(n), order;
+    int64_t o = 0;
+    for (int J = J0; J < J1; ++J) {
+      const int set = sched->loops[J].set;
+      const int32_t* sig = sub.sigma[J - sub.first].p;
+      if (set == 0) {
+        k_seg_cells<<<grid_for(mesh->nc), 256, 0, s>>>(sig, d_iperm.p, mesh->nc, tile.p + o, wid.p + o, bits.p + o);
+        o += mesh->nc;
+      } else {
+        const bool interior = set == 1;
+        const int a = interior ? 2 : 1;
+        const int64_t ns = (interior ? mesh->nfi : mesh->nfe) * a;
+        if (ns == 0) continue;
+        k_seg_facets<<<grid_for(ns), 256, 0, s>>>(interior ? d_f2c.p : d_e2c.p, interior ? d_f2f.p : d_e2f.p, ns, a,
+                                                  sig, d_iperm.p, tile.p + o, wid.p + o, bits.p + o);
+        o += ns;
+      }
+    }
+    SLT_CUDA(cudaGetLastError());
+    sort_by_two(tile, tbits, wid, wbits, n, order, s);  // tile sorted in place, order the permutation
+    DevBuf<uint32_t> swid(n), sbits(n);
+    k_gather_div<<<grid_for(n), 256, 0, s>>>((const int32_t*)wid.p, order.p, n, 1, swid.p);
+    k_gather_div<<<grid_for(n), 256, 0, s>>>((const int32_t*)bits.p, order.p, n, 1, sbits.p);
+    DevBuf<int32_t> flag(n), pos(n + 1);
+    k_run_heads<<<grid_for(n), 256, 0, s>>>(tile.p, swid.p, n, flag.p);
+    exclusive_scan_i32(flag.p, pos.p, n, s);
+    int32_t nu = 0;
+    SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + n, 4, cudaMemcpyDeviceToHost, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    DevBuf<int32_t> items(std::max(nu, 1));
+    DevBuf<uint32_t> utile(std::max(nu, 1));
+    k_seg_emit<<<grid_for(n), 256, 0, s>>>(tile.p, swid.p, sbits.p, flag.p, pos.p, n, items.p, utile.p);
+    // inside each tile, items with the same flags side by side (stable, so work-id order within
+    // equal flags), full ones first: a warp then runs only the parts its lanes have
+    {
+      DevBuf<uint32_t> mk(std::max(nu, 1)), ut(std::max(nu, 1)), ord;
+      k_flag_key<<<grid_for(nu), 256, 0, s>>>(items.p, nu, mk.p);
+      SLT_CUDA(cudaMemcpyAsync(ut.p, utile.p, (size_t)nu * 4, cudaMemcpyDeviceToDevice, s));
+      sort_by_two(ut, tbits, mk, 4, nu, ord, s);
+      sub.plan_items[jj].alloc(std::max(nu, 1));
+      k_gather_div<<<grid_for(nu), 256, 0, s>>>(items.p, ord.p, nu, 1, (uint32_t*)sub.plan_items[jj].p);
+    }
+    lower_bound_offsets(utile.p, nu, m, sub.plan_ptr[jj].p, s);
     SLT_CUDA(cudaGetLastError());
     SLT_CUDA(cudaStreamSynchronize(s));
   }
@@ -723,7 +740,7 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
 }
 
 // Dependencies between tiles for the dataflow executor, from the cells each tile touches in
-// each sub-chain (its plan items): inside a sub-chain, a tile waits for the lower-colour tiles
+// each sub-chain (its plan items; both cells of an interior facet are items of the facet's tile): inside a sub-chain, a tile waits for the lower-colour tiles
 // that touch one of its cells; across sub-chains, for the tiles of the previous sub-chain (in
 // chain order, wrapping to the previous step) that touched the same cell.  Every access to a
 // cell is thereby ordered as in the untiled chain.
@@ -742,13 +759,13 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
     SubSched& sub = sched->subs[k];
     std::vector<int32_t> col = sub.colour.download(s, sub.m);
     for (int32_t i = 0; i < sub.m; ++i) colour[D.cum[k] + i] = col[i];
-    for (int jj = 0; jj < sub.last - sub.first; ++jj) {
-      const bool cell_loop = sched->loops[sub.first + jj].set == 0;
+    for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+      const int jj = J0 - sub.first;
       std::vector<int32_t> ptr = sub.plan_ptr[jj].download(s, sub.m + 1);
       std::vector<int32_t> items = sub.plan_items[jj].download(s, std::max(ptr[sub.m], 1));
       for (int32_t t = 0; t < sub.m; ++t)
         for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
-          const int64_t w = cell_loop ? items[i] : (items[i] >> 3);
+          const int64_t w = items[i] >> 4;
           int32_t* T = &touch[k][w * CAP];
           uint8_t& n = ntouch[k][w];
           bool have = false;

@@ -96,6 +96,35 @@ enum LoopKind : int32_t {
 };
 // which field buffers each loop of the seventeen uses is fixed by its position (exec.cu)
 
+#ifdef __CUDACC__
+#define SLT_HD __host__ __device__
+#else
+#define SLT_HD
+#endif
+
+// The chain in ten phases.  phase_first(h) is the first chain loop of phase h (phase_first(10) = 17):
+//   0: loops 0-2   A(S) -> U1          5: loops 9-10   E(V) -> E
+//   1: loops 3-4   E(U1) -> E          6: loop 11      Hooke E -> S1, div -> U1
+//   2: loop 5      Hooke E -> S1,      7: loops 12-13  faces of A(S1) += U1
+//                  div -> U2           8: loops 14-15  E(U1) -> E
+//   3: loops 6-7   faces of A(S1) += U2  9: loop 16    stress update
+//   4: loop 8      velocity update
+SLT_HD constexpr int phase_first(int h) {
+  return h == 0 ? 0 : h == 1 ? 3 : h == 2 ? 5 : h == 3 ? 6 : h == 4 ? 8 : h == 5 ? 9 : h == 6 ? 11 : h == 7 ? 12
+       : h == 8 ? 14 : h == 9 ? 16 : 17;
+}
+constexpr int kPhases = 10;
+SLT_HD constexpr int phase_of(int J) {
+  return J < 3 ? 0 : J < 5 ? 1 : J < 6 ? 2 : J < 8 ? 3 : J < 9 ? 4 : J < 11 ? 5 : J < 12 ? 6 : J < 14 ? 7
+       : J < 16 ? 8 : 9;
+}
+// A segment is the part of a phase inside one sub-chain [first, last): the tiled executors run a
+// tile's segments in order with one barrier after each.  The segment starting at loop J ends here.
+SLT_HD constexpr int seg_end(int J, int last) {
+  return phase_first(phase_of(J) + 1) < last ? phase_first(phase_of(J) + 1) : last;
+}
+
+
 // ---------------------------------------------------------------- primitives (sort.cu)
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key; tmp buffers of
 // size n.  keys/vals are replaced by the sorted sequence.
@@ -135,7 +164,7 @@ struct SubSched {
   // executor plan (elastic chains only)
   std::vector<int32_t> colour_ptr;                     // host, ncolours + 1
   DevBuf<int32_t> tiles_by_colour;
-  std::vector<DevBuf<int32_t>> plan_ptr, plan_items;   // per loop of the sub-chain
+  std::vector<DevBuf<int32_t>> plan_ptr, plan_items;   // per segment, at its first loop (others empty)
 };
 
 }  // namespace slt

@@ -76,6 +76,20 @@ def test_dataflow_equals_colour_phases_bitwise(lib, name, ts):
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
 
 
+@pytest.mark.parametrize("name", ["tiny", "small_p2", "small_p3", "small_p4"])
+def test_untiled_phases_equal_tiled_loops_bitwise(lib, name):
+    # the untiled chain fuses runs of loops into one pass per cell (ten launches); a schedule of
+    # one tile runs the loops one by one over every cell: the sums are taken in the same order, so
+    # the bits agree (smaller tiles may add one cell's faces in another order: rounding differs)
+    cfg = workload(name)
+    mesh = gpu_mesh(lib, cfg)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=10 ** 6, split=(9,))
+    for n in (2, 8):  # one launch per phase; a replayed graph of one step
+        vt, st = gpu_run(lib, cfg, nsteps=n, sched=sched, mesh=mesh)
+        vu, su = gpu_run(lib, cfg, nsteps=n, sched=None, mesh=mesh)
+        assert np.array_equal(vt, vu) and np.array_equal(st, su), (name, n)
+
+
 @pytest.mark.parametrize("executor", [0, 2])
 def test_dataflow_wait_limit_reports_timeout_and_context_survives(lib, executor):
     # with a one-poll wait limit the tiles that must wait for a neighbour give up: the kernel
