@@ -224,7 +224,7 @@ def adjoint_timing(slt, synth, args, barrier):
     squares (200k cells, P2, layered +-5 % per cell), one shot of the top row of the 8x8 source
     grid, 50 receivers along the top edge, checkpoints every 50 steps, `--adjoint-steps` steps.
     Both record the receivers after every step, so their forward steps run as the untiled
-    chain (ten fused phases per step): the persistent tiled executor needs many steps per launch."""
+    chain (six fused phases per step): the persistent tiled executor needs many steps per launch."""
     import numpy as np
     import torch
     n = args.adjoint_steps

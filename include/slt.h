@@ -175,10 +175,11 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
 /* ------------------------------------------------------------------ executor (Section 5.2)
  * nsteps time steps on device fields v, sigma (layout above, updated in place).
  * ricker: device array [nsteps] of the source time function at t_{n+1/2} (NULL: no source).
- * sched = NULL runs the plain untiled chain (ten launches per step, one per run of consecutive
- * loops that need no value from another cell; four or more steps replay a CUDA graph of one step); otherwise the schedule must come from
- * slt_inspect on slt_mesh_chain(mesh) and each tile executes its slice of every loop of its
- * sub-chain in chain order:
+ * sched = NULL runs the plain untiled chain: six launches per step, one per run of consecutive
+ * loops in which no cell reads a value another cell writes during the run; four or more steps
+ * replay a CUDA graph of one step.  Otherwise the schedule must come from slt_inspect on
+ * slt_mesh_chain(mesh) and each tile executes its slice of every loop of its sub-chain in chain
+ * order:
  *  - executor 1 (colour phases, Algorithm 4 in shared-memory mode): one launch per colour and
  *    sub-chain, all tiles of a colour in parallel, one CTA per tile;
  *  - executor 0 (dataflow, default): one persistent launch for all nsteps, one CTA per tile;
@@ -207,7 +208,7 @@ int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* 
    own point sources src_xy [nshots][2] (host; NULL = no source), sharing the Ricker series.
    Fields are device arrays with the shots innermost: v [ncell][2][Np][nshots],
    sigma [ncell][3][Np][nshots], updated in place.  Each (cell, shot) computes exactly what a
-   single-field run of that shot computes.  sched = NULL: untiled chain (10 launches per step,
+   single-field run of that shot computes.  sched = NULL: untiled chain (6 launches per step,
    one thread per cell and shot); otherwise the dataflow executor, each tile's items expanded
    over the shots, in slices of the schedule's shots_per_cta (one persistent launch per slice).
    profile (NULL = none) as in slt_execute_profiled.  Synchronises.  Work memory: 15 Np ncell

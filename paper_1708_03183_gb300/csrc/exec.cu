@@ -38,12 +38,14 @@ namespace {
 
 #include "exec_body.cuh"
 
-// Untiled chain: phase H (one or more consecutive loops, see run_phase) over every cell.
-template <int P, int H>
+// Untiled chain: the PARTS of phase H (consecutive loops, see phase_first) over every cell, one
+// thread per cell.  (A grid-stride form would let the compiler hoist the reference-matrix entries
+// out of its loop into registers, more than doubling the register count.)
+template <int P, int H, int PARTS>
 __global__ void __launch_bounds__(128) k_phase(Params a) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (w >= a.nc) return;
-  run_phase<P, H, false>(a, w, 0, (H == 9 && a.step_dev) ? (int64_t)*a.step_dev : a.step);
+  run_phase<P, H, PARTS, false>(a, w, 0, (H == 5 && a.step_dev) ? (int64_t)*a.step_dev : a.step);
 }
 
 // advances the device step counter at the end of a graph-captured step
@@ -66,30 +68,37 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_tiled(Params a
   }
 }
 
-template <int P, int H>
+template <int P, int H, int PARTS>
 void launch_phase(const Params& a, cudaStream_t s);
 
-// The untiled loops [first, last) of the chain, as the fused phases that cover them exactly
-// (every caller's range starts and ends on a phase boundary).
+// parts (kPartA, kPartF, kPartB) of phase h among the loops [lo, hi)
+inline int phase_parts(int h, int lo, int hi) {
+  int parts = 0;
+  for (int J = std::max(lo, phase_first(h)); J < std::min(hi, phase_first(h + 1)); ++J)
+    parts |= !is_cell_loop(J) ? kPartF : J == phase_first(h) ? kPartA : kPartB;
+  return parts;
+}
+
+// The untiled loops [first, last) of the chain as phases: whole phases, and the operator E alone
+// (loops 3-4 of phase 1); other partial phases are not built.
 template <int P>
 void launch_untiled_range(const Params& a, int first, int last, cudaStream_t s) {
   for (int h = 0; h < kPhases; ++h) {
-    if (phase_first(h) < first || phase_first(h + 1) > last) {
-      if (phase_first(h) < last && phase_first(h + 1) > first)
-        fail(SLT_ERR_UNSUPPORTED, "loop range does not align with the untiled phases");
-      continue;
-    }
-    switch (h) {
-      case 0: launch_phase<P, 0>(a, s); break;
-      case 1: launch_phase<P, 1>(a, s); break;
-      case 2: launch_phase<P, 2>(a, s); break;
-      case 3: launch_phase<P, 3>(a, s); break;
-      case 4: launch_phase<P, 4>(a, s); break;
-      case 5: launch_phase<P, 5>(a, s); break;
-      case 6: launch_phase<P, 6>(a, s); break;
-      case 7: launch_phase<P, 7>(a, s); break;
-      case 8: launch_phase<P, 8>(a, s); break;
-      case 9: launch_phase<P, 9>(a, s); break;
+    const int parts = phase_parts(h, first, last);
+    if (!parts) continue;
+    if (parts == phase_parts(h, 0, 17)) {
+      switch (h) {
+        case 0: launch_phase<P, 0, kAllParts>(a, s); break;
+        case 1: launch_phase<P, 1, kAllParts>(a, s); break;
+        case 2: launch_phase<P, 2, kAllParts>(a, s); break;
+        case 3: launch_phase<P, 3, kAllParts>(a, s); break;
+        case 4: launch_phase<P, 4, kAllParts>(a, s); break;
+        case 5: launch_phase<P, 5, kAllParts>(a, s); break;
+      }
+    } else if (h == 1 && parts == (kPartA | kPartF)) {
+      launch_phase<P, 1, kPartA | kPartF>(a, s);
+    } else {
+      fail(SLT_ERR_UNSUPPORTED, "loop range does not align with the untiled phases");
     }
   }
   SLT_CUDA(cudaGetLastError());
@@ -176,12 +185,12 @@ Params make_params(slt_mesh m) {
   return a;
 }
 
-template <int P, int H>
+template <int P, int H, int PARTS>
 void launch_phase(const Params& a, cudaStream_t s) {
-  int threads = 128;
-  int64_t blocks = (a.nc + threads - 1) / threads;
+  constexpr int threads = 128;
+  const int64_t blocks = (a.nc + threads - 1) / threads;
   g_rec.begin(0, s);
-  k_phase<P, H><<<(unsigned)blocks, threads, 0, s>>>(a);
+  k_phase<P, H, PARTS><<<(unsigned)blocks, threads, 0, s>>>(a);
   g_rec.end(s);
 }
 
@@ -238,9 +247,9 @@ void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStre
   dataflow_check(sched, s);
 }
 
-// The untiled step as one CUDA graph (the 10 phase kernels and the step-counter increment), captured
+// The untiled step as one CUDA graph (the 6 phase kernels and the step-counter increment), captured
 // on the mesh's private stream and launched nsteps times on s: the host issues one launch per
-// step instead of ten.  The step index comes from a device counter the graph advances.
+// step instead of six.  The step index comes from a device counter the graph advances.
 template <int P>
 void run_untiled_graph(slt_mesh m, Params a, int64_t nsteps, cudaStream_t s) {
   if (!m->step_dev.p) m->step_dev.alloc(1);

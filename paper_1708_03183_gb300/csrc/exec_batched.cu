@@ -22,12 +22,12 @@ namespace {
 #include "exec_body.cuh"
 #include "dataflow.cuh"
 
-// Untiled chain, phase H (see run_phase) over every (cell, shot).
+// Untiled chain, phase H (see phase_first) over every (cell, shot).
 template <int P, int H>
 __global__ void __launch_bounds__(128) k_phase_b(Params a) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // over nc * S
   if (t >= a.nc * a.S) return;
-  run_phase<P, H, true>(a, t / a.S, (int)(t % a.S), a.step);
+  run_phase<P, H, kAllParts, true>(a, t / a.S, (int)(t % a.S), a.step);
 }
 
 template <int P>
@@ -39,10 +39,6 @@ void launch_untiled_b(const Params& a, cudaStream_t s) {
   k_phase_b<P, 3><<<blocks, 128, 0, s>>>(a);
   k_phase_b<P, 4><<<blocks, 128, 0, s>>>(a);
   k_phase_b<P, 5><<<blocks, 128, 0, s>>>(a);
-  k_phase_b<P, 6><<<blocks, 128, 0, s>>>(a);
-  k_phase_b<P, 7><<<blocks, 128, 0, s>>>(a);
-  k_phase_b<P, 8><<<blocks, 128, 0, s>>>(a);
-  k_phase_b<P, 9><<<blocks, 128, 0, s>>>(a);
   SLT_CUDA(cudaGetLastError());
 }
 

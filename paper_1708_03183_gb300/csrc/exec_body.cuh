@@ -58,7 +58,7 @@ struct Params {
   const long long* step_dev;        // if set, the step index is read here (graph-captured steps)
   double dt, c24;
   const int32_t* plan_ptr[17];      // tiled: per segment (indexed by its first loop), tile offsets
-  const int32_t* plan_items[17];    // and items (work id << 4) | (vol << 3) | face mask
+  const int32_t* plan_items[17];    // and items (see run_seg)
   // multi-shot layout
   int32_t S;                        // shots per cell (1 for one field)
   int32_t s0, sg;                   // tiled multi-shot runs: shots s0 .. s0 + sg - 1 of the S
@@ -276,77 +276,92 @@ __device__ __forceinline__ void store_rows(const Params& a, const Pos& q, double
   for (int r = 0; r < R; ++r) X[(int64_t)r * fs + w] = x[r];
 }
 
-// ---- bodies of the phases: a phase is a run of consecutive loops of the chain that write one
-// cell's output and read nothing another thread writes during the run.  One work item covers a
-// cell's share of every loop of the run: `vol` = the cell loop of the run, imask / emask = the
-// interior / free-surface faces of its facet loops.  Without `vol` the faces accumulate onto the
-// stored output (the cell loop ran in another tile).
+// ---- bodies of the phases.  A phase is a run of consecutive loops of the chain that write only
+// the cell's own outputs and read nothing another thread writes during the run (no neighbour
+// value produced inside the run), so one thread can take a cell through all of them.  A work
+// item covers a cell's share of each loop of the run: pa = the run's first loop, a cell loop
+// (volume part); imask / emask = the interior / free-surface faces of its facet loops; pb = a
+// later cell loop of the run (Hooke's law or an update).  Missing parts were done in another
+// tile: the item starts from the stored output.
 
-// volume part of A (U = div(S)/rho) when vol, else U as stored; then the faces of imask, emask
+// A(S) -> U: volume part when pa, else U as stored; then the faces of imask, emask
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void segA(const Params& a, const Pos& q, bool vol, int imask, int emask,
+__device__ __forceinline__ void segA(const Params& a, const Pos& q, bool pa, int imask, int emask,
                                      const double* S, double* U) {
   double u[2 * np_of(P)];
-  if (vol) volB_part<P, CG, BATCH>(a, q, S, u);
+  if (pa) volB_part<P, CG, BATCH>(a, q, S, u);
   else load_rows<2 * np_of(P), CG, BATCH>(a, q, U, u);
   intB_part<P, CG, BATCH>(a, q, imask, S, u);
   extB_part<P, CG, BATCH>(a, q, emask, S, u);
   store_rows<2 * np_of(P), BATCH>(a, q, U, u);
 }
-// volume part of E(V) when vol, else E as stored; then the interior faces of imask
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void segE(const Params& a, const Pos& q, bool vol, int imask, const double* V,
-                                     double* E) {
-  double e[3 * np_of(P)];
-  if (vol) volD_part<P, CG, BATCH>(a, q, V, e);
-  else load_rows<3 * np_of(P), CG, BATCH>(a, q, E, e);
-  intD_part<P, CG, BATCH>(a, q, imask, V, e);
-  store_rows<3 * np_of(P), BATCH>(a, q, E, e);
-}
 
-// S1 = C E at the nodes, then U = div(S1)/rho
+// E(V) -> E (volume part when pa, else E as stored; the faces of imask), then, when pb, Hooke's
+// law S1 = C E and the volume part of A(S1) -> U
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void hookeB(const Params& a, const Pos& q, const double* E, double* S1, double* U) {
+__device__ __forceinline__ void segEB(const Params& a, const Pos& q, bool pa, bool pb, int imask, const double* V,
+                                      double* E, double* S1, double* U) {
   constexpr int Np = np_of(P);
+  double e[3 * Np];
+  if (pa) volD_part<P, CG, BATCH>(a, q, V, e);
+  else load_rows<3 * Np, CG, BATCH>(a, q, E, e);
+  intD_part<P, CG, BATCH>(a, q, imask, V, e);
+  if (pa || imask) store_rows<3 * Np, BATCH>(a, q, E, e);
+  if (!pb) return;
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
-  double l2m = fma(2.0, mu, lam);
+  const double lam = a.mat[n + c], mu = a.mat[2 * n + c];
+  const double l2m = fma(2.0, mu, lam);
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
-    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
-           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
-    S1[(int64_t)j * fs + w] = fma(lam, eyy, l2m * exx);
-    S1[(int64_t)(Np + j) * fs + w] = fma(lam, exx, l2m * eyy);
-    S1[(int64_t)(2 * Np + j) * fs + w] = mu * g;
+    S1[(int64_t)j * fs + w] = fma(lam, e[Np + j], l2m * e[j]);
+    S1[(int64_t)(Np + j) * fs + w] = fma(lam, e[j], l2m * e[Np + j]);
+    S1[(int64_t)(2 * Np + j) * fs + w] = mu * e[2 * Np + j];
   }
-  double u[2 * np_of(P)];
+  double u[2 * Np];
   volB_part<P, CG, BATCH>(a, q, S1, u);
-  store_rows<2 * np_of(P), BATCH>(a, q, U, u);
+  store_rows<2 * Np, BATCH>(a, q, U, u);
 }
 
+// faces of A(S1) onto U2 (imask, emask), then, when pb, the velocity update
+// V += dt (U1 + dt^2/24 U2)
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void updV(const Params& a, const Pos& q) {
+__device__ __forceinline__ void segAV(const Params& a, const Pos& q, bool pb, int imask, int emask) {
   constexpr int Np = np_of(P);
+  double* const* b = a.buf;
+  double u[2 * Np];
+  load_rows<2 * Np, CG, BATCH>(a, q, b[B_U2], u);
+  if (imask | emask) {
+    intB_part<P, CG, BATCH>(a, q, imask, b[B_S1], u);
+    extB_part<P, CG, BATCH>(a, q, emask, b[B_S1], u);
+    store_rows<2 * Np, BATCH>(a, q, b[B_U2], u);
+  }
+  if (!pb) return;
   const int64_t fs = fstride<BATCH>(a), w = q.f;
-  double* V = a.buf[B_V];
-  const double* U1 = a.buf[B_U1];
-  const double* U2 = a.buf[B_U2];
+  double* V = b[B_V];
+  const double* U1 = b[B_U1];
 #pragma unroll
   for (int r = 0; r < 2 * Np; ++r) {
     int64_t o = (int64_t)r * fs + w;
-    V[o] = fma(a.dt, fma(a.c24, ld<CG>(&U2[o]), ld<CG>(&U1[o])), ld<CG>(&V[o]));
+    V[o] = fma(a.dt, fma(a.c24, u[r], ld<CG>(&U1[o])), ld<CG>(&V[o]));
   }
 }
 
+// E(U1) -> E as segEB, then, when pb, the stress update S += dt (S1 + dt^2/24 C E) + source
 template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void updS(const Params& a, const Pos& q, int64_t step) {
+__device__ __forceinline__ void segES(const Params& a, const Pos& q, bool pa, bool pb, int imask, int64_t step) {
   constexpr int Np = np_of(P);
+  double* const* b = a.buf;
+  double e[3 * Np];
+  if (pa) volD_part<P, CG, BATCH>(a, q, b[B_U1], e);
+  else load_rows<3 * Np, CG, BATCH>(a, q, b[B_E], e);
+  intD_part<P, CG, BATCH>(a, q, imask, b[B_U1], e);
+  if (pa || imask) store_rows<3 * Np, BATCH>(a, q, b[B_E], e);
+  if (!pb) return;
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  double* S = a.buf[B_S];
-  const double* S1 = a.buf[B_S1];
-  const double* E = a.buf[B_E];
-  double lam = a.mat[n + c], mu = a.mat[2 * n + c];
-  double l2m = fma(2.0, mu, lam);
+  double* S = b[B_S];
+  const double* S1 = b[B_S1];
+  const double lam = a.mat[n + c], mu = a.mat[2 * n + c];
+  const double l2m = fma(2.0, mu, lam);
   int32_t sw;
   const double* sv;
   if constexpr (BATCH) {
@@ -360,8 +375,7 @@ __device__ __forceinline__ void updS(const Params& a, const Pos& q, int64_t step
   const double gs = src ? a.dt * a.ricker[step] : 0.0;
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
-    double exx = ld<CG>(&E[(int64_t)j * fs + w]), eyy = ld<CG>(&E[(int64_t)(Np + j) * fs + w]),
-           g = ld<CG>(&E[(int64_t)(2 * Np + j) * fs + w]);
+    const double exx = e[j], eyy = e[Np + j], g = e[2 * Np + j];
     double cxx = fma(lam, eyy, l2m * exx), cyy = fma(lam, exx, l2m * eyy), cxy = mu * g;
     int64_t oxx = (int64_t)j * fs + w, oyy = (int64_t)(Np + j) * fs + w, oxy = (int64_t)(2 * Np + j) * fs + w;
     double nxx = fma(a.dt, fma(a.c24, cxx, ld<CG>(&S1[oxx])), ld<CG>(&S[oxx]));
@@ -376,21 +390,17 @@ __device__ __forceinline__ void updS(const Params& a, const Pos& q, int64_t step
   }
 }
 
-// phase H at one (cell, shot)
+// phase H at one (cell, shot); the phases and their loops are listed with phase_first
 template <int P, int H, bool CG, bool BATCH>
-__device__ __forceinline__ void phase_body(const Params& a, const Pos& q, bool vol, int imask, int emask,
+__device__ __forceinline__ void phase_body(const Params& a, const Pos& q, bool pa, bool pb, int imask, int emask,
                                            int64_t step) {
   double* const* b = a.buf;
-  if constexpr (H == 0) segA<P, CG, BATCH>(a, q, vol, imask, emask, b[B_S], b[B_U1]);
-  else if constexpr (H == 1) segE<P, CG, BATCH>(a, q, vol, imask, b[B_U1], b[B_E]);
-  else if constexpr (H == 2) hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U2]);
-  else if constexpr (H == 3) segA<P, CG, BATCH>(a, q, false, imask, emask, b[B_S1], b[B_U2]);
-  else if constexpr (H == 4) updV<P, CG, BATCH>(a, q);
-  else if constexpr (H == 5) segE<P, CG, BATCH>(a, q, vol, imask, b[B_V], b[B_E]);
-  else if constexpr (H == 6) hookeB<P, CG, BATCH>(a, q, b[B_E], b[B_S1], b[B_U1]);
-  else if constexpr (H == 7) segA<P, CG, BATCH>(a, q, false, imask, emask, b[B_S1], b[B_U1]);
-  else if constexpr (H == 8) segE<P, CG, BATCH>(a, q, vol, imask, b[B_U1], b[B_E]);
-  else updS<P, CG, BATCH>(a, q, step);
+  if constexpr (H == 0) segA<P, CG, BATCH>(a, q, pa, imask, emask, b[B_S], b[B_U1]);
+  else if constexpr (H == 1) segEB<P, CG, BATCH>(a, q, pa, pb, imask, b[B_U1], b[B_E], b[B_S1], b[B_U2]);
+  else if constexpr (H == 2) segAV<P, CG, BATCH>(a, q, pb, imask, emask);
+  else if constexpr (H == 3) segEB<P, CG, BATCH>(a, q, pa, pb, imask, b[B_V], b[B_E], b[B_S1], b[B_U1]);
+  else if constexpr (H == 4) segA<P, CG, BATCH>(a, q, false, imask, emask, b[B_S1], b[B_U1]);
+  else segES<P, CG, BATCH>(a, q, pa, pb, imask, step);
 }
 
 // the faces of `mask` that have a neighbour (interior) and those that do not (free surface)
@@ -402,39 +412,39 @@ __device__ __forceinline__ void split_mask(const Params& a, int64_t c, int mask,
   emask = mask & ~imask;
 }
 
-// Untiled: phase H over every face of cell w, shot s
-template <int P, int H, bool BATCH>
+// parts of a phase (untiled launches): the first cell loop, the facet loops, the later cell loop
+constexpr int kPartA = 1, kPartF = 2, kPartB = 4, kAllParts = 7;
+
+// Untiled: the PARTS of phase H at cell w, shot s (every face of the cell)
+template <int P, int H, int PARTS, bool BATCH>
 __device__ __forceinline__ void run_phase(const Params& a, int64_t w, int s, int64_t step) {
   Pos q;
   q.c = w;
   q.s = s;
   q.f = BATCH ? w * a.S + s : w;
-  int imask, emask;
-  split_mask(a, w, 7, imask, emask);
-  phase_body<P, H, false, BATCH>(a, q, true, imask, emask, step);
+  int imask = 0, emask = 0;
+  if (PARTS & kPartF) split_mask(a, w, 7, imask, emask);
+  phase_body<P, H, false, BATCH>(a, q, (PARTS & kPartA) != 0, (PARTS & kPartB) != 0, imask, emask, step);
 }
 
-// Tiled: one item of the segment of phase H, item = (work id << 4) | (vol << 3) | face mask
+// Tiled: one item of a segment of phase H,
+// item = (work id << 5) | (later cell loop << 4) | (first cell loop << 3) | face mask
 template <int P, bool CG, bool BATCH>
 __device__ __forceinline__ void run_seg(const Params& a, int H, int32_t item, int64_t step, int s = 0) {
   Pos q;
-  q.c = (int64_t)(item >> 4);
+  q.c = (int64_t)(item >> 5);
   q.s = s;
   q.f = BATCH ? q.c * a.S + s : q.c;
-  const bool vol = (item >> 3) & 1;
+  const bool pa = (item >> 3) & 1, pb = (item >> 4) & 1;
   int imask, emask;
   split_mask(a, q.c, item & 7, imask, emask);
   switch (H) {
-    case 0: phase_body<P, 0, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 1: phase_body<P, 1, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 2: phase_body<P, 2, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 3: phase_body<P, 3, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 4: phase_body<P, 4, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 5: phase_body<P, 5, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 6: phase_body<P, 6, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 7: phase_body<P, 7, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    case 8: phase_body<P, 8, CG, BATCH>(a, q, vol, imask, emask, step); break;
-    default: phase_body<P, 9, CG, BATCH>(a, q, vol, imask, emask, step); break;
+    case 0: phase_body<P, 0, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
+    case 1: phase_body<P, 1, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
+    case 2: phase_body<P, 2, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
+    case 3: phase_body<P, 3, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
+    case 4: phase_body<P, 4, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
+    default: phase_body<P, 5, CG, BATCH>(a, q, pa, pb, imask, emask, step); break;
   }
 }
 

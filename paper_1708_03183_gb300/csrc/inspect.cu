@@ -237,13 +237,14 @@ __global__ void k_lm_local(const uint32_t* __restrict__ tile, const uint32_t* __
 }
 
 // executor plan of a facet loop: entries (tile, work id, face bit), sorted, OR-reduced per cell
-// segment plan entries: one per (iteration, cell it writes) of a cell loop (vol bit) ...
+// segment plan entries: one per (iteration, cell it writes) of a cell loop (its part bit) ...
 __global__ void k_seg_cells(const int32_t* __restrict__ sig, const int32_t* __restrict__ iperm, int64_t n,
-                            uint32_t* __restrict__ tile, uint32_t* __restrict__ wid, uint32_t* __restrict__ bits) {
+                            uint32_t bit, uint32_t* __restrict__ tile, uint32_t* __restrict__ wid,
+                            uint32_t* __restrict__ bits) {
   GRID_STRIDE(p, n) {
     tile[p] = (uint32_t)sig[p];
     wid[p] = (uint32_t)iperm[p];
-    bits[p] = 8u;
+    bits[p] = bit;
   }
 }
 // ... and of a facet loop: slot p = facet * a + side, the face bit of that side's cell
@@ -269,13 +270,13 @@ __global__ void k_seg_emit(const uint32_t* __restrict__ tile, const uint32_t* __
   GRID_STRIDE(p, n) if (flag[p]) {
     uint32_t b = 0;
     for (int64_t q = p; q < n && tile[q] == tile[p] && wid[q] == wid[p]; ++q) b |= bits[q];
-    items[pos[p]] = (int32_t)((wid[p] << 4) | b);
+    items[pos[p]] = (int32_t)((wid[p] << 5) | b);
     utile[pos[p]] = tile[p];
   }
 }
-// sort key of an item inside its tile: full flags (vol and three faces) first
+// sort key of an item inside its tile: full flags (both cell loops and three faces) first
 __global__ void k_flag_key(const int32_t* __restrict__ items, int64_t n, uint32_t* __restrict__ key) {
-  GRID_STRIDE(p, n) key[p] = 15u - (uint32_t)(items[p] & 15);
+  GRID_STRIDE(p, n) key[p] = 31u - (uint32_t)(items[p] & 31);
 }
 
 struct InverseMap {
@@ -520,10 +521,11 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
   sub.plan_items.clear();
   sub.plan_ptr.resize(nl);
   sub.plan_items.resize(nl);
-  if (mesh->nc >= (int64_t(1) << 27)) fail(SLT_ERR_UNSUPPORTED, "the tiled executors take below 2^27 cells");
+  if (mesh->nc >= (int64_t(1) << 26)) fail(SLT_ERR_UNSUPPORTED, "the tiled executors take below 2^26 cells");
   const int tbits = bits_for(std::max(m - 1, 1)), wbits = bits_for(std::max<int64_t>(mesh->nc - 1, 1));
   // one plan per segment (the part of a phase inside the sub-chain), stored at its first loop:
-  // per tile, one item per cell the segment's loops touch, (work id << 4) | (vol << 3) | faces
+  // per tile, one item per cell the segment's loops touch,
+  // (work id << 5) | (later cell loop << 4) | (first cell loop << 3) | faces
   for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
     const int J1 = seg_end(J0, sub.last);
     int64_t n = 0;
@@ -545,7 +547,9 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
       const int set = sched->loops[J].set;
       const int32_t* sig = sub.sigma[J - sub.first].p;
       if (set == 0) {
-        k_seg_cells<<<grid_for(mesh->nc), 256, 0, s>>>(sig, d_iperm.p, mesh->nc, tile.p + o, wid.p + o, bits.p + o);
+        const uint32_t bit = J == phase_first(phase_of(J)) ? 8u : 16u;
+        k_seg_cells<<<grid_for(mesh->nc), 256, 0, s>>>(sig, d_iperm.p, mesh->nc, bit, tile.p + o, wid.p + o,
+                                                         bits.p + o);
         o += mesh->nc;
       } else {
         const bool interior = set == 1;
@@ -577,7 +581,7 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
       DevBuf<uint32_t> mk(std::max(nu, 1)), ut(std::max(nu, 1)), ord;
       k_flag_key<<<grid_for(nu), 256, 0, s>>>(items.p, nu, mk.p);
       SLT_CUDA(cudaMemcpyAsync(ut.p, utile.p, (size_t)nu * 4, cudaMemcpyDeviceToDevice, s));
-      sort_by_two(ut, tbits, mk, 4, nu, ord, s);
+      sort_by_two(ut, tbits, mk, 5, nu, ord, s);
       sub.plan_items[jj].alloc(std::max(nu, 1));
       k_gather_div<<<grid_for(nu), 256, 0, s>>>(items.p, ord.p, nu, 1, (uint32_t*)sub.plan_items[jj].p);
     }
@@ -765,7 +769,7 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
       std::vector<int32_t> items = sub.plan_items[jj].download(s, std::max(ptr[sub.m], 1));
       for (int32_t t = 0; t < sub.m; ++t)
         for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
-          const int64_t w = items[i] >> 4;
+          const int64_t w = items[i] >> 5;
           int32_t* T = &touch[k][w * CAP];
           uint8_t& n = ntouch[k][w];
           bool have = false;

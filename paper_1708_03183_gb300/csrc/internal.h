@@ -102,28 +102,32 @@ enum LoopKind : int32_t {
 #define SLT_HD
 #endif
 
-// The chain in ten phases.  phase_first(h) is the first chain loop of phase h (phase_first(10) = 17):
-//   0: loops 0-2   A(S) -> U1          5: loops 9-10   E(V) -> E
-//   1: loops 3-4   E(U1) -> E          6: loop 11      Hooke E -> S1, div -> U1
-//   2: loop 5      Hooke E -> S1,      7: loops 12-13  faces of A(S1) += U1
-//                  div -> U2           8: loops 14-15  E(U1) -> E
-//   3: loops 6-7   faces of A(S1) += U2  9: loop 16    stress update
-//   4: loop 8      velocity update
+// The chain in six phases: runs of consecutive loops in which no thread reads a value another
+// thread writes during the run.  phase_first(h) is the first loop of phase h (phase_first(6) = 17):
+//   0: loops 0-2    A(S) -> U1 (volume, interior faces, free surface)
+//   1: loops 3-5    E(U1) -> E, then S1 = C E and the volume part of A(S1) -> U2
+//   2: loops 6-8    faces of A(S1) onto U2, then V += dt (U1 + dt^2/24 U2)
+//   3: loops 9-11   E(V) -> E, then S1 = C E and the volume part of A(S1) -> U1
+//   4: loops 12-13  faces of A(S1) onto U1
+//   5: loops 14-16  E(U1) -> E, then S += dt (S1 + dt^2/24 C E) + source
+// The neighbour values read inside a phase (S in 0, U1 in 1 and 5, S1 in 2 and 4, V in 3) are all
+// written by an earlier phase.
 SLT_HD constexpr int phase_first(int h) {
-  return h == 0 ? 0 : h == 1 ? 3 : h == 2 ? 5 : h == 3 ? 6 : h == 4 ? 8 : h == 5 ? 9 : h == 6 ? 11 : h == 7 ? 12
-       : h == 8 ? 14 : h == 9 ? 16 : 17;
+  return h == 0 ? 0 : h == 1 ? 3 : h == 2 ? 6 : h == 3 ? 9 : h == 4 ? 12 : h == 5 ? 14 : 17;
 }
-constexpr int kPhases = 10;
+constexpr int kPhases = 6;
 SLT_HD constexpr int phase_of(int J) {
-  return J < 3 ? 0 : J < 5 ? 1 : J < 6 ? 2 : J < 8 ? 3 : J < 9 ? 4 : J < 11 ? 5 : J < 12 ? 6 : J < 14 ? 7
-       : J < 16 ? 8 : 9;
+  return J < 3 ? 0 : J < 6 ? 1 : J < 9 ? 2 : J < 12 ? 3 : J < 14 ? 4 : 5;
+}
+// loops over cells (the others run over interior or free-surface facets)
+SLT_HD constexpr bool is_cell_loop(int J) {
+  return J == 0 || J == 3 || J == 5 || J == 8 || J == 9 || J == 11 || J == 14 || J == 16;
 }
 // A segment is the part of a phase inside one sub-chain [first, last): the tiled executors run a
 // tile's segments in order with one barrier after each.  The segment starting at loop J ends here.
 SLT_HD constexpr int seg_end(int J, int last) {
   return phase_first(phase_of(J) + 1) < last ? phase_first(phase_of(J) + 1) : last;
 }
-
 
 // ---------------------------------------------------------------- primitives (sort.cu)
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key; tmp buffers of
