@@ -511,6 +511,16 @@ def main():
                    "frac": tiled_bytes * args.steps / kern_s / 1e9 / hbm_peak, "peak_kind": hbm_kind},
            "clocks": clocks,
            "gpu_launches": prof["chain_launches"] + prof["layout_launches"]}
+    if args.executor != 1:
+        # the dependency graph the dataflow executor ran: time per step cannot fall below the
+        # longest chain (in node times), and reaches the work bound only when the nodes of a step
+        # are many more per tile in flight than that chain is long
+        dinfo = slt.slt_schedule_dataflow_info(sched)
+        out["dataflow"] = {"nodes_per_step": dinfo["nodes_per_step"], "deps_per_step": dinfo["deps_per_step"],
+                           "critical_path_nodes_per_step": dinfo["critical_path_nodes"],
+                           "critical_path_work_weighted": dinfo["critical_path_items"],
+                           "tiles_in_flight": dinfo["tiles_in_flight"],
+                           "node_rounds_per_step": dinfo["nodes_per_step"] / max(dinfo["tiles_in_flight"], 1)}
 
     if not args.no_cluster and args.executor == 0:
         # the same workload with one thread-block cluster per large tile (fewer boundary cells)

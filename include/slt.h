@@ -122,6 +122,15 @@ int slt_schedule_destroy(slt_schedule sched);
    conflict pairs in the last conflicting round, iterations with no projected element (sent to
    tile 0), first loop, number of loops. */
 int slt_schedule_info(slt_schedule sched, int32_t subchain, int64_t info[8]);
+/* The dependency graph of the dataflow executor (schedules inspected on slt_mesh_chain; a node
+   is one (time step, tile) pair): info[0] = nodes per time step (tiles of all sub-chains),
+   [1] dependency edges per step, [2] the longest dependency chain per step in the steady state,
+   in nodes, [3] the same with every node weighted by its work items and divided by the mean items
+   per node, [4] work items per step, [5] tiles in flight in the last dataflow run of the schedule
+   (CTAs, or clusters for executor 2; 0 before the first run).  Time per step cannot fall below
+   [3] node times however many tiles are in flight; it reaches the work bound only when
+   [0] / [5] is well above [3].  SLT_ERR_ARG for a schedule without an executor plan. */
+int slt_schedule_dataflow_info(slt_schedule sched, double info[6]);
 /* Copy one integer array of the schedule to host memory.  Call with host_out = NULL to get
    the length in *n.  kind:
      0 rank of every seed element            (loop, desc ignored)

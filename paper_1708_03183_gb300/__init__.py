@@ -44,6 +44,7 @@ _SIGS = {
     "slt_inspect": (ctypes.c_int, [P, P, P, P]),
     "slt_schedule_destroy": (ctypes.c_int, [P]),
     "slt_schedule_info": (ctypes.c_int, [P, I32, P]),
+    "slt_schedule_dataflow_info": (ctypes.c_int, [P, P]),
     "slt_schedule_export": (ctypes.c_int, [P, I32, I32, I32, P, P]),
     "slt_mesh_create": (ctypes.c_int, [P, P, I64, I32, P, P, P, P, P, P]),
     "slt_mesh_destroy": (ctypes.c_int, [P]),
@@ -215,6 +216,14 @@ def slt_schedule_info(sched, sub):
     _check(lib.slt_schedule_info(sched.ptr, sub, ctypes.c_void_p(info.ctypes.data)))
     keys = ["ntiles", "ncolours", "restarts", "fell_back", "conflicts", "unprojected", "first", "nloops"]
     return dict(zip(keys, (int(x) for x in info)))
+
+
+def slt_schedule_dataflow_info(sched):
+    info = np.zeros(6, dtype=np.float64)
+    _check(lib.slt_schedule_dataflow_info(sched.ptr, ctypes.c_void_p(info.ctypes.data)))
+    keys = ["nodes_per_step", "deps_per_step", "critical_path_nodes", "critical_path_items", "items_per_step",
+            "tiles_in_flight"]
+    return dict(zip(keys, (float(x) for x in info)))
 
 
 EXPORT_KINDS = {"rank": 0, "colour": 1, "sigma": 2, "list_ptr": 3, "list": 4, "fp_ptr": 5, "fp": 6, "lmap": 7}

@@ -275,6 +275,20 @@ int slt_schedule_info(slt_schedule s, int32_t sub, int64_t info[8]) {
   API_END
 }
 
+int slt_schedule_dataflow_info(slt_schedule s, double info[6]) {
+  API_BEGIN
+  REQUIRE(s && info, "null argument");
+  const DataflowPlan& D = s->df;
+  REQUIRE(!D.cum.empty(), "the schedule has no executor plan (not inspected on a mesh chain)");
+  info[0] = D.cum.back();
+  info[1] = (double)D.ndeps;
+  info[2] = D.cp_nodes;
+  info[3] = D.cp_items;
+  info[4] = D.items_per_step;
+  info[5] = (double)D.last_grid;
+  API_END
+}
+
 int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc, int32_t* host_out, int64_t* n) {
   API_BEGIN
   REQUIRE(s && n, "null argument");

@@ -286,6 +286,7 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
   auto launch = [&](auto kernel, int threads) {
     SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
     const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), df.q.total);
+    sched->df.last_grid = grid;
     kernel<<<(unsigned)grid, threads, 0, s>>>(a, df);
   };
   if (bs == 128) launch(k_dataflow<P, 128, BATCH>, 128);

@@ -239,6 +239,7 @@ void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStre
   SLT_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel, &cfg));
   if (nclusters < 1) fail(SLT_ERR_UNSUPPORTED, "no cluster of this size fits on the GPU");
   nclusters = (int)std::min<long long>(nclusters, df.q.total);
+  sched->df.last_grid = nclusters;
   if (sched->df_slot.n < (size_t)nclusters) sched->df_slot.alloc(nclusters);
   cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
   SLT_CUDA(cudaLaunchKernelEx(&cfg, kernel, a, df, sched->df_slot.p));

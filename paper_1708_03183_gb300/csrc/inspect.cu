@@ -743,6 +743,43 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
   if (c->mesh) build_dataflow(out, c->mesh, s);
 }
 
+// Longest dependency chain per time step of the (step, tile) graph in the steady state: the
+// chain lengths L over 12 steps, every node after its dependencies (within a step in order of
+// sub-chain, then colour; wrapped dependencies from the step before), L(node) = weight +
+// max L(dependency); the growth of max L over the last 5 steps divided by 5.  With unit weights
+// it counts nodes; with plan-item weights it is divided by the mean items per node.
+void critical_path(DataflowPlan& D, const std::vector<std::vector<int32_t>>& deps,
+                   const std::vector<int32_t>& colour, const std::vector<double>& items_of) {
+  const int32_t G = D.cum.back();
+  D.items_per_step = 0;
+  for (double x : items_of) D.items_per_step += x;
+  if (G == 0) return;
+  std::vector<int32_t> order(G);
+  std::vector<int> sub_of(G);
+  for (size_t k = 0; k + 1 < D.cum.size(); ++k)
+    for (int32_t g = D.cum[k]; g < D.cum[k + 1]; ++g) sub_of[g] = (int)k;
+  for (int32_t g = 0; g < G; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return sub_of[x] != sub_of[y] ? sub_of[x] < sub_of[y] : colour[x] < colour[y];
+  });
+  constexpr int kSteps = 12, kTail = 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<double> prev(G, 0.0), cur(G, 0.0), top(kSteps, 0.0);
+    for (int st = 0; st < kSteps; ++st) {
+      for (int32_t g : order) {
+        double m = 0;
+        for (int32_t e : deps[g]) m = std::max(m, (e & 1) ? prev[e >> 1] : cur[e >> 1]);
+        cur[g] = (pass ? items_of[g] : 1.0) + m;
+        top[st] = std::max(top[st], cur[g]);
+      }
+      std::swap(prev, cur);
+    }
+    const double per_step = (top[kSteps - 1] - top[kSteps - 1 - kTail]) / kTail;
+    if (pass == 0) D.cp_nodes = per_step;
+    else D.cp_items = D.items_per_step > 0 ? per_step / (D.items_per_step / G) : 0;
+  }
+}
+
 // Dependencies between tiles for the dataflow executor, from the cells each tile touches in
 // each sub-chain (its plan items; both cells of an interior facet are items of the facet's tile): inside a sub-chain, a tile waits for the lower-colour tiles
 // that touch one of its cells; across sub-chains, for the tiles of the previous sub-chain (in
@@ -759,6 +796,7 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
   std::vector<int32_t> colour(G);
   std::vector<std::vector<int32_t>> touch(K, std::vector<int32_t>(nc * CAP));
   std::vector<std::vector<uint8_t>> ntouch(K, std::vector<uint8_t>(nc, 0));
+  std::vector<double> items_of(G, 0.0);  // plan items of each node
   for (int k = 0; k < K; ++k) {
     SubSched& sub = sched->subs[k];
     std::vector<int32_t> col = sub.colour.download(s, sub.m);
@@ -767,7 +805,8 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
       const int jj = J0 - sub.first;
       std::vector<int32_t> ptr = sub.plan_ptr[jj].download(s, sub.m + 1);
       std::vector<int32_t> items = sub.plan_items[jj].download(s, std::max(ptr[sub.m], 1));
-      for (int32_t t = 0; t < sub.m; ++t)
+      for (int32_t t = 0; t < sub.m; ++t) {
+        items_of[D.cum[k] + t] += ptr[t + 1] - ptr[t];
         for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
           const int64_t w = items[i] >> 5;
           int32_t* T = &touch[k][w * CAP];
@@ -778,6 +817,7 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
           if (n == CAP) fail(SLT_ERR_UNSUPPORTED, "a cell is touched by more than 16 tiles of one sub-chain");
           T[n++] = t;
         }
+      }
     }
   }
   std::vector<std::vector<int32_t>> deps(G);
@@ -817,6 +857,7 @@ void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
     }
     D.ndeps += (int64_t)deps[g].size();
   }
+  critical_path(D, deps, colour, items_of);
   std::vector<int32_t> ptr(G + 1, 0), flat;
   for (int32_t g = 0; g < G; ++g) {
     ptr[g + 1] = ptr[g] + (int32_t)succ[g].size();

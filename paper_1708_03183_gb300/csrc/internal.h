@@ -183,6 +183,10 @@ struct DataflowPlan {
   DevBuf<unsigned long long> head;   // head, tail
   DevBuf<int32_t> err;
   int64_t ndeps = 0;
+  // longest dependency chain per time step in the steady state, in nodes (each node counted once)
+  // and in plan items (each node weighted by its items); items of all nodes of one step
+  double cp_nodes = 0, cp_items = 0, items_per_step = 0;
+  int64_t last_grid = 0;             // tiles in flight (CTAs or clusters) of the last launch
 };
 }  // namespace slt
 

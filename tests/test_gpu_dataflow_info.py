@@ -1,0 +1,90 @@
+"""The dependency-graph figures of the dataflow executor (GPU inspector), recounted here from the
+schedule's exported colours and tiling functions with the executor's ordering rule: inside a
+sub-chain a tile follows the lower-colour tiles that touch one of its cells; across sub-chains it
+follows the tiles of the previous sub-chain (the last one of the previous step for the first) that
+touched the same cell."""
+import numpy as np
+import pytest
+
+from oracle import inspector as OI
+from tests.helpers import workload, gpu_mesh, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _recount(lib, sched, cfg, bounds):
+    _, _, inter, exter = OI.elastic_chain(cfg["mesh"])
+    nc = cfg["mesh"]["cell2vert"].shape[0]
+    K = len(bounds)
+    cols, touch = [], []
+    for k, (lo, hi) in enumerate(bounds):
+        cols.append(lib.slt_schedule_export(sched, "colour", k))
+        pairs = set()
+        for J in range(lo, hi):
+            sig = lib.slt_schedule_export(sched, "sigma", J)
+            kind = OI.ELASTIC_LOOPS[J][0]
+            if kind == "cells":
+                pairs |= set(zip(range(nc), sig.tolist()))
+            elif kind == "ifacets":
+                pairs |= set(zip(inter[:, 0].tolist(), sig.tolist())) | set(zip(inter[:, 2].tolist(), sig.tolist()))
+            else:
+                pairs |= set(zip(exter[:, 0].tolist(), sig.tolist()))
+        per_cell = [[] for _ in range(nc)]
+        for c, t in pairs:
+            per_cell[c].append(t)
+        touch.append(per_cell)
+    base = np.cumsum([0] + [len(c) for c in cols])
+    deps = set()  # (node, dependency, from the previous step)
+    for c in range(nc):
+        for k in range(K):
+            prev, wrap = (k - 1, 0) if k else (K - 1, 1)
+            for b in touch[k][c]:
+                for a in touch[k][c]:
+                    if cols[k][a] < cols[k][b]:
+                        deps.add((base[k] + b, base[k] + a, 0))
+                for a in touch[prev][c]:
+                    deps.add((base[k] + b, base[prev] + a, wrap))
+    G = int(base[-1])
+    by_node = [[] for _ in range(G)]
+    for g, e, w in deps:
+        by_node[g].append((e, w))
+    order = sorted(range(G), key=lambda g: (np.searchsorted(base, g, side="right"), cols_of(cols, base, g)))
+    prev_l, top = [0.0] * G, []
+    for _ in range(12):
+        cur = [0.0] * G
+        for g in order:
+            cur[g] = 1.0 + max([prev_l[e] if w else cur[e] for e, w in by_node[g]], default=0.0)
+        top.append(max(cur))
+        prev_l = cur
+    return G, len(deps), (top[11] - top[6]) / 5
+
+
+def cols_of(cols, base, g):
+    k = int(np.searchsorted(base, g, side="right")) - 1
+    return int(cols[k][g - base[k]])
+
+
+@pytest.mark.parametrize("name,ts,split", [("small_p2", 32, (9,)), ("tiny", 24, (3, 9, 12)), ("small_p3", 40, ())])
+def test_dataflow_graph_figures_match_a_recount(lib, name, ts, split):
+    cfg = workload(name)
+    mesh = gpu_mesh(lib, cfg)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=split)
+    bounds = list(zip((0,) + tuple(split), tuple(split) + (17,)))
+    G, ndeps, cp = _recount(lib, sched, cfg, bounds)
+    info = lib.slt_schedule_dataflow_info(sched)
+    assert info["nodes_per_step"] == G
+    assert info["deps_per_step"] == ndeps
+    assert info["critical_path_nodes"] == pytest.approx(cp, rel=0, abs=1e-12)
+    assert len(bounds) <= info["critical_path_nodes"] <= G
+    assert info["tiles_in_flight"] == 0
+    gpu_run(lib, cfg, nsteps=2, sched=sched, mesh=mesh)
+    assert 0 < lib.slt_schedule_dataflow_info(sched)["tiles_in_flight"] <= 2 * G
+
+
+def test_one_tile_per_subchain_is_a_chain_of_sub_chains(lib):
+    cfg = workload("small_p2")
+    mesh = gpu_mesh(lib, cfg)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=10 ** 6, split=(9,))
+    info = lib.slt_schedule_dataflow_info(sched)
+    assert info["nodes_per_step"] == 2 and info["critical_path_nodes"] == 2
+    assert info["critical_path_items"] == pytest.approx(2.0)
