@@ -193,6 +193,50 @@ print(json.dumps({"t": t, "nc": nc, "Np": Np}))
     return 5 * d["Np"] * d["nc"] * nsteps / d["t"], d
 
 
+def inspector_timing(slt, synth, args, scale=4):
+    """The GPU inspector against the oracle inspector (sequential C on one host core) on the same
+    mesh: the bench workload's generator reduced by `scale` in each direction, the bench's tile
+    size, fusion {velocity, stress}, Hilbert renumbering.  Best of 3 on each side (seconds)."""
+    import torch
+    c = synth.CONFIGS[args.config]
+    nx, ny = c["nx"] // scale, c["ny"] // scale
+    cfg = synth.build_config(args.config, nx=nx, ny=ny, nsteps=1)
+    m = cfg["mesh"]
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
+    chain = slt.slt_mesh_chain(mesh)
+    gpu = float("inf")
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc = slt.slt_inspect(chain, tile_size=args.tile_size, split=(9,))
+        torch.cuda.synchronize()
+        gpu = min(gpu, time.perf_counter() - t0)
+        del sc
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import synth
+from oracle import inspector as OI
+cfg = synth.build_config(%r, nx=%d, ny=%d, nsteps=1)
+ch, xy, _, _ = OI.elastic_chain(cfg["mesh"])
+OI.build()
+best = float("inf")
+for _ in range(3):
+    t = time.perf_counter()
+    for lo, hi in ((0, 9), (9, 17)):
+        OI.inspect(ch.sub(lo, hi), %d, renumber=True, xy=xy)
+    best = min(best, time.perf_counter() - t)
+print(json.dumps({"t": best}))
+""" % (ROOT, args.config, nx, ny, args.tile_size)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    orc = json.loads(out.stdout.strip().splitlines()[-1])["t"]
+    return {"sample": "%dx%d squares (%d cells), ts %d, fusion {velocity, stress}, Hilbert renumbering; best of 3"
+                      % (nx, ny, m["cell2vert"].shape[0], args.tile_size),
+            "gpu_s": gpu, "oracle_s": orc, "oracle_cores": 1, "oracle_over_gpu": orc / gpu}
+
+
 def run_reference(args, rank):
     """--impl reference: the oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -582,6 +626,8 @@ def main():
         out["cpu_baseline"] = {"value": rate, "unit": "dof-updates/s", "cores": 1, "kind": "oracle",
                                "sample": "10 time steps of the same generator's mesh reduced 4x per direction "
                                          "(%d cells, P%d), single BLAS thread, %.1f s" % (d["nc"], p, d["t"])}
+        out["inspector"] = inspector_timing(slt, synth, args)
+        out["inspector"]["gpu_s_bench_mesh"] = inspect_s
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -102,10 +102,13 @@ __device__ __forceinline__ long long df_take(const DFQ& q) {
   return node;
 }
 
-// Thread 0, after the CTA finished node (st, g): release its successors.
+// The first warp, after the CTA (or cluster) finished node (st, g) and passed a barrier: release
+// its successors, one lane per successor (about ten per node), so that the decrements travel to L2
+// side by side instead of one after another.  Each lane's fence and acq_rel decrement order the
+// whole tile's writes, which the barrier made visible to it, before the successor can be taken.
 __device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
   __threadfence();
-  for (int i = q.succ_ptr[g]; i < q.succ_ptr[g + 1]; ++i) {
+  for (int i = q.succ_ptr[g] + (int)(threadIdx.x & 31); i < q.succ_ptr[g + 1]; i += 32) {
     const int e = q.succ[i];
     const long long s2 = st + (e & 1);
     if (s2 >= q.nsteps) continue;
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Param
     int k = 0;
     while (g >= df.cum[k + 1]) ++k;
     run_tile<P, BS, BATCH>(a, df.first[k], df.last[k], g - df.cum[k], st);
-    if (threadIdx.x == 0) df_publish(df.q, g, st);
+    if (threadIdx.x < 32) df_publish(df.q, g, st);
   }
 }
 
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
     for (int i = threadIdx.x; i < (int)(sizeof(Params) / 4); i += BS) dst[i] = src[i];
     __syncthreads();
     run_tile<P, BS, false>(sp, df.first[k], df.last[k], g - df.cum[k], st);
-    if (threadIdx.x == 0) df_publish(df.q, g, st);
+    if (threadIdx.x < 32) df_publish(df.q, g, st);
   }
 }
 
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_clust
         run_seg<P, DF_L2_ONLY, false>(a, H, items[i], st);
       cl.sync();
     }
-    if (rank == 0 && threadIdx.x == 0) df_publish(df.q, g, st);
+    if (rank == 0 && threadIdx.x < 32) df_publish(df.q, g, st);
   }
 }
 
