@@ -4,8 +4,8 @@
 #pragma once
 
 // Resident tiles per SM: at p <= 2, 768 threads (three 256-thread tiles, 80 registers; the
-// heaviest loop bodies spill a little, which measured faster than two tiles at 128 registers);
-// at p >= 3 the loop bodies need their registers and one tile is the minimum.
+// heaviest phase bodies spill a little, which measured faster than two tiles at 128 registers);
+// at p >= 3 the phase bodies need their registers and one tile is the minimum.
 template <int P, int BS>
 constexpr int tile_min_blocks() {
   return P <= 2 ? 768 / BS : 1;

@@ -1,6 +1,6 @@
 // Executor of the DG elastic loop chain (Section 5.2, Algorithm 4, shared-memory mode).
 //
-// One thread per cell for every loop.  Facet loops are executed as pulls: the thread of cell c
+// One thread per cell for every phase.  Facet loops are executed as pulls: the thread of cell c
 // applies the contributions of the facets of c that belong to the loop's iteration set (a
 // 3-bit face mask per cell), so two threads never increment the same cell and no atomics
 // are needed.  The reference matrices live in constant memory and every lane of a warp reads
@@ -12,7 +12,8 @@
 //             5 hookeB E->S1 and volB S1->U2, 6 intB S1,U2+, 7 extB S1,U2+, 8 updV V+=dt(U1+c U2)
 //   stress:   9 volD V->E, 10 intD V,E+, 11 hookeB E->S1 and volB S1->U1, 12 intB S1,U1+,
 //             13 extB S1,U1+, 14 volD U1->E, 15 intD U1,E+, 16 updS S+=dt(S1+c C E)+source
-// with c = dt^2/24: the fourth-order staggered Taylor leapfrog.
+// with c = dt^2/24: the fourth-order staggered Taylor leapfrog.  The executors run it as the six
+// phases of internal.h (loops 0-2, 3-5, 6-8, 9-11, 12-13, 14-16), one thread per cell and phase.
 //
 // Operators in nodal strong form (the mass matrix cancels in the volume terms):
 //   A sigma = (1/rho) div(sigma) - sum_f (F_f / 2 rho) Lift_f ((sigma - sigma_nb) n_f)
@@ -342,8 +343,8 @@ void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, doubl
 
 // One untiled step on the mesh's work fields that leaves its operator intermediates in `keep`
 // (rows of ncp, work order): A sigma [2Np], E(A sigma) [3Np], ABA sigma [2Np], E(v) [3Np],
-// AB v [2Np], E(AB v) [3Np] - the loops write them there instead of the scratch buffers (same
-// loop bodies, so the same numbers).  The adjoint's reverse sweep reads them back.
+// AB v [2Np], E(AB v) [3Np] - the phases write them there instead of the scratch buffers (same
+// phase bodies, so the same numbers).  The adjoint's reverse sweep reads them back.
 void exec_step_keep(slt_mesh m, const double* ricker, double dt, int64_t step, double* keep, cudaStream_t s) {
   Params a = make_params(m);
   a.dt = dt;

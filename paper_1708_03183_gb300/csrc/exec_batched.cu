@@ -2,7 +2,7 @@
 // with the shots innermost ([cell][comp][node][shot] for the caller, rows of ncp * S doubles in
 // the work layout).  Consecutive threads take consecutive shots of one cell, so field loads
 // coalesce over shots and per-cell geometry, neighbours and face masks are warp-uniform; every
-// shot has its own point source.  The loop bodies are those of exec_body.cuh; the arithmetic of
+// shot has its own point source.  The phase bodies are those of exec_body.cuh; the arithmetic of
 // each (cell, shot) is exactly that of a single-field run with that shot's source.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
