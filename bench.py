@@ -449,7 +449,7 @@ def main():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-p4", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
-    ap.add_argument("--p4-steps", type=int, default=20)
+    ap.add_argument("--p4-steps", type=int, default=100)
     ap.add_argument("--multi-steps", type=int, default=20)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10)
