@@ -626,6 +626,11 @@ def main():
         out["cpu_baseline"] = {"value": rate, "unit": "dof-updates/s", "cores": 1, "kind": "oracle",
                                "sample": "10 time steps of the same generator's mesh reduced 4x per direction "
                                          "(%d cells, P%d), single BLAS thread, %.1f s" % (d["nc"], p, d["t"])}
+        others = {}
+        for name, steps, scale in (("tiny", 20, 1), ("p4", 3, 4)):
+            r, dd = oracle_sample_rate(name, steps, scale)
+            others[name] = {"value": r, "sample": "%d steps, %d cells, P%d" % (steps, dd["nc"], synth.CONFIGS[name]["p"])}
+        out["cpu_baseline"]["other_configs"] = others
         out["inspector"] = inspector_timing(slt, synth, args)
         out["inspector"]["gpu_s_bench_mesh"] = inspect_s
     if rank == 0:
