@@ -123,7 +123,9 @@ int slt_schedule_destroy(slt_schedule sched);
    tile 0), first loop, number of loops. */
 int slt_schedule_info(slt_schedule sched, int32_t subchain, int64_t info[8]);
 /* The dependency graph of the dataflow executor (schedules inspected on slt_mesh_chain; a node
-   is one (time step, tile) pair): info[0] = nodes per time step (tiles of all sub-chains),
+   is one (time step, tile) pair; its edges are the part of Algorithm 4's order that matters, tiles
+   of lower colour before higher colour within a sub-chain and sub-chains in chain order, kept only
+   between tiles that touch a common cell): info[0] = nodes per time step (tiles of all sub-chains),
    [1] dependency edges per step, [2] the longest dependency chain per step in the steady state,
    in nodes, [3] the same with every node weighted by its work items and divided by the mean items
    per node, [4] work items per step, [5] tiles in flight in the last dataflow run of the schedule
