@@ -1,6 +1,7 @@
 """Parity at the full sizes of the benchmarked workloads, in the launch configurations bench.py
-times: the large P2 mesh (1.0M cells; the whole schedule bit for bit against the oracle inspector
-and two tiled steps against the oracle's chain), the P4 mesh, sampled shots of the 64-shot
+times: the large P2 mesh (1.0M cells; the whole schedule bit for bit against the oracle inspector,
+two tiled steps against the oracle's chain, and the discrete energy over a 100-step launch), the P4
+mesh, sampled shots of the 64-shot
 batched run, sampled members of the 16-mesh group, and the adjoint workload's gradient against
 central differences of its misfit.  Minutes of oracle time: marked slow."""
 import numpy as np
@@ -52,6 +53,33 @@ def test_fullsize_tiled_steps_match_oracle(lib, large):
     dg = ElasticDG(cfg["mesh"], 2, cfg["rho"], cfg["lam"], cfg["mu"])
     vo, so = dg.run(v0, s0, cfg["dt"], 2, cfg["ricker"], cfg["src"])
     assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
+
+
+def test_fullsize_energy_invariant_over_a_long_tiled_launch(lib, large):
+    # source off, seeded random start: the leapfrog's discrete energy
+    # E^n = 1/2 <v^{n+1/2}, M_rho v^{n-1/2}> + 1/2 <sigma^n, M_S sigma^n> is invariant (the operator
+    # pair is skew-adjoint), so after one persistent 100-step launch, the bench's launch form, it
+    # equals its starting value up to rounding; the inner products are the oracle's
+    import torch
+    cfg, mesh, sched = large
+    nc = cfg["mesh"]["cell2vert"].shape[0]
+    rng = np.random.default_rng(23)
+    v0 = 1e-3 * rng.standard_normal((nc, 2, 6))
+    s0 = 1e-3 * rng.standard_normal((nc, 3, 6))
+    dg = ElasticDG(cfg["mesh"], 2, cfg["rho"], cfg["lam"], cfg["mu"])
+
+    def energy(v, s):  # v = v^{n-1/2}, s = sigma^n; one more step gives v^{n+1/2}
+        vt, st = torch.tensor(v, device="cuda"), torch.tensor(s, device="cuda")
+        lib.slt_execute(mesh, sched, vt, st, None, cfg["dt"], 1)
+        return 0.5 * dg.inner_v(vt.cpu().numpy(), v) + 0.5 * dg.inner_s(s, s)
+
+    e0 = energy(v0, s0)
+    v, s = torch.tensor(v0, device="cuda"), torch.tensor(s0, device="cuda")
+    lib.slt_execute(mesh, sched, v, s, None, cfg["dt"], 100)
+    v1, s1 = v.cpu().numpy(), s.cpu().numpy()
+    e100 = energy(v1, s1)
+    assert np.isfinite(e100) and abs(e100 - e0) <= 1e-10 * abs(e0), (e0, e100)
+    assert rel_l2(v1, v0) > 1e-2  # the fields did move
 
 
 def test_fullsize_p4_tiled_steps_match_oracle(lib):
