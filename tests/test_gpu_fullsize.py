@@ -55,6 +55,38 @@ def test_fullsize_tiled_steps_match_oracle(lib, large):
     assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
 
 
+@pytest.fixture(scope="module")
+def large_oracle4(large):
+    # four oracle steps at full size from seeded random fields, with the source
+    cfg = large[0]
+    nc = cfg["mesh"]["cell2vert"].shape[0]
+    rng = np.random.default_rng(29)
+    v0 = 1e-3 * rng.standard_normal((nc, 2, 6))
+    s0 = 1e-3 * rng.standard_normal((nc, 3, 6))
+    dg = ElasticDG(cfg["mesh"], 2, cfg["rho"], cfg["lam"], cfg["mu"])
+    vo, so = dg.run(v0.copy(), s0.copy(), cfg["dt"], 4, cfg["ricker"], cfg["src"])
+    return v0, s0, vo, so
+
+
+@pytest.mark.parametrize("form", ["untiled_graph", "tiled_ts256", "cluster_ts2048_c4"])
+def test_fullsize_four_steps_in_each_timed_launch_form(lib, large, large_oracle4, form):
+    # the other launch forms bench.py times at full size: the untiled chain replayed as a CUDA graph
+    # (four or more steps), the default dataflow executor, and the cluster executor of its
+    # `cluster` key (ts 2048, 4-CTA clusters), each four steps in one call against the oracle
+    import torch
+    cfg, mesh, sched = large
+    v0, s0, vo, so = large_oracle4
+    if form == "untiled_graph":
+        sc = None
+    elif form == "tiled_ts256":
+        sc = sched
+    else:
+        sc = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=2048, split=(9,), executor=2, cluster_size=4)
+    v, s = torch.tensor(v0, device="cuda"), torch.tensor(s0, device="cuda")
+    lib.slt_execute(mesh, sc, v, s, torch.tensor(cfg["ricker"], device="cuda"), cfg["dt"], 4)
+    assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
+
+
 def test_fullsize_energy_invariant_over_a_long_tiled_launch(lib, large):
     # source off, seeded random start: the leapfrog's discrete energy
     # E^n = 1/2 <v^{n+1/2}, M_rho v^{n-1/2}> + 1/2 <sigma^n, M_S sigma^n> is invariant (the operator
