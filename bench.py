@@ -450,7 +450,7 @@ def main():
     ap.add_argument("--no-p4", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--p4-steps", type=int, default=100)
-    ap.add_argument("--multi-steps", type=int, default=20)
+    ap.add_argument("--multi-steps", type=int, default=40)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64])

@@ -5,10 +5,11 @@
 
 // Resident tiles per SM: at p <= 2, 768 threads (three 256-thread tiles, 80 registers; the
 // heaviest phase bodies spill a little, which measured faster than two tiles at 128 registers);
-// at p >= 3 the phase bodies need their registers and one tile is the minimum.
+// at p = 3 two 256-thread tiles (128 registers, about 90 bytes of spills; the tiles in flight
+// double); at p = 4 the phase bodies need their registers and one tile is the minimum.
 template <int P, int BS>
 constexpr int tile_min_blocks() {
-  return P <= 2 ? 768 / BS : 1;
+  return P <= 2 ? 768 / BS : (P == 3 && BS == 256) ? 2 : 1;
 }
 
 // Field loads of the dataflow kernel go to L2 only (ld.global.cg).  Cacheable loads after the
