@@ -1,5 +1,6 @@
-// Loop bodies of the DG elastic chain, shared by the single-field executor (exec.cu) and the
-// multi-shot executor (exec_batched.cu).  Included inside an anonymous namespace of each
+// Phase bodies of the DG elastic chain (the parts of each loop, chained per cell into the six
+// phases listed in internal.h), shared by the single-field executors (exec.cu, dataflow.cuh) and
+// the multi-shot executor (exec_batched.cu).  Included inside an anonymous namespace of each
 // translation unit, which therefore holds its own copy of the reference matrices.
 //
 // One thread computes one (cell, shot) work item.  Per-cell data (geometry, material,
