@@ -171,3 +171,109 @@ def test_dropping_either_kind_of_wait_breaks_the_result(drop):
         out = _replay_fields((inter, exter), nc, _iterations(subs, _random_order(subs, deps, 3, rng)))
         differs |= any(not np.array_equal(a, b) for a, b in zip(ref, out))
     assert differs
+
+
+def _segment_items(ch, inter, exter, sub, t, a, b):
+    """The items of tile t's segment [a, b): per cell, its share of each loop of the segment in loop
+    order, as (loop, iteration, side) with side = the cell's place in the facet (0 for cell loops)."""
+    items = {}
+    ptrs = sub["s"]["lists"]
+    for j in range(a, b):
+        ptr, its = ptrs[j - sub["lo"]]
+        kind = I.ELASTIC_LOOPS[j][0]
+        for e in its[ptr[t]:ptr[t + 1]]:
+            e = int(e)
+            if kind == "cells":
+                items.setdefault(e, []).append((j, e, 0))
+            elif kind == "ifacets":
+                items.setdefault(int(inter[e, 0]), []).append((j, e, 0))
+                items.setdefault(int(inter[e, 2]), []).append((j, e, 1))
+            else:
+                items.setdefault(int(exter[e, 0]), []).append((j, e, 0))
+    return items
+
+
+def _replay_pull(mesh_facets, nc, ops):
+    """The integer model with each facet iteration split into its two per-cell halves (the pull
+    form): each half hashes the same reads and updates only its own cell."""
+    inter, exter = mesh_facets
+    data = {f: (np.arange(nc, dtype=np.int64) * 1000003 + 17 * (i + 1)) % M61
+            for i, f in enumerate(("S", "U1", "E", "S1", "U2", "V"))}
+    for (j, e, side) in ops:
+        reads, writes, inc = FIELDS[j]
+        reads, writes = reads.split(), writes.split()
+        kind = I.ELASTIC_LOOPS[j][0]
+        cells = [int(inter[e, 0]), int(inter[e, 2])] if kind == "ifacets" else (
+            [int(exter[e, 0])] if kind == "efacets" else [e])
+        h = (j + 1) * 0x9E3779B1 + e
+        for f in reads:
+            for c in cells:
+                h = (h * 31 + int(data[f][c])) % M61
+        c = cells[side]
+        for w, f in enumerate(writes):
+            v = (h * (side + 1) * (w + 3)) % M61
+            data[f][c] = (int(data[f][c]) + v) % M61 if inc else v
+    return [data[f] for f in sorted(data)]
+
+
+@pytest.mark.parametrize("split,ts", [((9,), 8), ((3, 9, 12), 6), ((1, 5, 9, 13), 8)])
+def test_segments_run_cell_by_cell_replay_the_chain(split, ts):
+    # the tiled executors run each tile as segments (the part of each phase in the sub-chain): one
+    # thread per touched cell takes it through the segment's loops, the cells of a segment in any
+    # order.  With the phase table of the executors, any such run of any allowed tile order replays
+    # the chain exactly.
+    from tests.test_phases import phase_starts
+    m = synth.make_mesh(7, 6, seed=11)
+    ch, _, inter, exter = I.elastic_chain(m)
+    nc = m["cell2vert"].shape[0]
+    bounds = list(zip((0,) + split, split + (17,)))
+    subs = _schedule(ch, bounds, ts)
+    deps = _dependencies(subs)
+    starts = phase_starts()
+    nsteps = 2
+    ref = _replay_fields((inter, exter), nc, _untiled(ch, nsteps))
+    rng = np.random.default_rng(ts + 7 * len(split))
+    for _ in range(6):
+        ops = []
+        for (_st, k, t) in _random_order(subs, deps, nsteps, rng):
+            sub = subs[k]
+            lo, hi = bounds[k]
+            cuts = sorted({lo, hi} | {x for x in starts if lo < x < hi})
+            for a, b in zip(cuts, cuts[1:]):
+                items = list(_segment_items(ch, inter, exter, sub, t, a, b).values())
+                rng.shuffle(items)
+                for it in items:
+                    ops += it
+        out = _replay_pull((inter, exter), nc, ops)
+        for x, y in zip(ref, out):
+            assert np.array_equal(x, y)
+
+
+def test_a_phase_that_reads_a_neighbour_value_it_writes_breaks_the_replay():
+    # sharpness: cutting the chain into segments that run loop 5 (which writes S1) together with
+    # loop 6 (which reads S1 across faces) makes some cell order differ from the chain
+    m = synth.make_mesh(7, 6, seed=11)
+    ch, _, inter, exter = I.elastic_chain(m)
+    nc = m["cell2vert"].shape[0]
+    bounds = [(0, 9), (9, 17)]
+    subs = _schedule(ch, bounds, 8)
+    ref = _replay_fields((inter, exter), nc, _untiled(ch, 1))
+    rng = np.random.default_rng(3)
+    bad = [0, 3, 9, 12, 14, 17]        # phase 1 widened to loops 3-8
+    differs = False
+    for _ in range(6):
+        ops = []
+        for k, sub in enumerate(subs):
+            lo, hi = bounds[k]
+            col = sub["s"]["colour"]
+            cuts = sorted({lo, hi} | {x for x in bad if lo < x < hi})
+            for c in range(sub["s"]["ncolours"]):
+                for t in [t for t in range(sub["s"]["ntiles"]) if col[t] == c]:
+                    for a, b in zip(cuts, cuts[1:]):
+                        items = list(_segment_items(ch, inter, exter, sub, t, a, b).values())
+                        rng.shuffle(items)
+                        for it in items:
+                            ops += it
+        out = _replay_pull((inter, exter), nc, ops)
+        differs |= any(not np.array_equal(x, y) for x, y in zip(ref, out))
+    assert differs
