@@ -116,6 +116,16 @@ typedef struct {
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
    no split, dataflow executor, no per-sub-chain tile sizes. */
 int slt_options_default(slt_options* opt);
+/* Inspect `chain` with the options `opt` (start from slt_options_default) on `stream` (a
+   cudaStream_t; NULL = the default stream) and return a new schedule in *out, owned by the caller
+   (slt_schedule_destroy).  The schedule copies what it needs from the chain.  Synchronises
+   `stream`.  For chains made by slt_mesh_chain it also builds the executor plans (per-tile
+   segment items) and the dataflow graph.  Errors: SLT_ERR_ARG for a null argument, a chain without
+   loops, or invalid options (tile_size < 1, split points not strictly increasing inside
+   (0, nloops), seed_loop outside its sub-chain, renumber = 1 without points on a seed set,
+   executor, cluster_size, block_threads or wait_spins out of range); SLT_ERR_UNSUPPORTED for 2^26
+   cells or more on a mesh chain, or a cell touched by more than 16 tiles of one sub-chain
+   (executor plans); SLT_ERR_OOM / SLT_ERR_CUDA from the device.  *out is NULL on error. */
 int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
 int slt_schedule_destroy(slt_schedule sched);
 /* Per sub-chain statistics: info[0..7] = ntiles, ncolours, restarts, fell_back_to_sequential,
