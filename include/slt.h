@@ -67,6 +67,8 @@ int slt_loop(slt_chain chain, int32_t set_id, int32_t ndesc, const int32_t* map_
 /* Attach a 2-D point (host, [size][2] doubles) to every element of a set; the Hilbert
    renumbering of the seed partition uses the points of the seed set. */
 int slt_set_points(slt_chain chain, int32_t set_id, const double* host_xy);
+/* Counts of the chain's sets, maps and loops (host; a NULL output is skipped); SLT_ERR_ARG for a
+   null chain. */
 int slt_chain_info(slt_chain chain, int32_t* nsets, int32_t* nmaps, int32_t* nloops);
 
 /* ------------------------------------------------------------------ inspector (Section 5.1)
@@ -284,7 +286,9 @@ int slt_autotune(slt_mesh mesh, const slt_options* base, int32_t nshots, const i
                  double* table);
 /* Apply one operator once (for tests): op 0 = A (stress -> velocity rate, device
    in [ncell][3][Np], out [ncell][2][Np]); op 1 = B (velocity -> stress rate, in [ncell][2][Np],
-   out [ncell][3][Np]).  Runs the untiled loops of that operator. */
+   out [ncell][3][Np]).  Runs the untiled phase kernels of that operator (A: loops 0-2 of the chain;
+   B: loops 3-5, whose Hooke step gives C E(v)).  Queued on `stream`; SLT_ERR_ARG for an op other
+   than 0 or 1 or a null pointer. */
 int slt_apply_operator(slt_mesh mesh, int32_t op, const double* in, double* out, void* stream);
 
 /* ------------------------------------------------------------------ misfit and gradient
