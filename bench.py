@@ -86,29 +86,42 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_hash():
-    """Hash of the executor sources without comments and blank space: a change to the code
-    invalidates a committed counter figure, a change to a comment does not."""
+KERNEL_SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "internal.h")
+
+
+def source_digest(texts):
+    """Hash of C++ sources without comments and blank space: a change to the code changes it, a
+    change to a comment does not."""
     import re
     h = hashlib.sha256()
-    for f in ("exec.cu", "exec_body.cuh", "dataflow.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_1708_03183_gb300", "csrc", f)) as fh:
-            src = fh.read()
+    for src in texts:
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload, steps):
+def kernel_hash():
+    """source_digest of the executor sources: a committed counter figure counts only for the code
+    it was taken on."""
+    texts = []
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1708_03183_gb300", "csrc", f)) as fh:
+            texts.append(fh.read())
+    return source_digest(texts)
+
+
+def ncu_traffic(kernel, workload, steps, table=None, current=None):
     """DRAM bytes (read + write) of one launch of `kernel` running `steps` time steps, from the
     committed ncu capture (bytes per step of a launch of that kernel on the same workload), if it
-    was taken on the current kernel source; otherwise None."""
+    was taken on the current kernel source; otherwise None.  `table` and `current` (the committed
+    table and the current source hash) are read from the repository when not given."""
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            d = json.load(f)
-        e = d[kernel][workload]
-        if e.get("source_hash") != kernel_hash():
+        if table is None:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+                table = json.load(f)
+        e = table[kernel][workload]
+        if e.get("source_hash") != (current if current is not None else kernel_hash()):
             return None
         return float(e["bytes_per_step"]) * steps
     except Exception:

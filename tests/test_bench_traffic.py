@@ -2,46 +2,38 @@
 executor sources they were taken on are unchanged (comments aside)."""
 import json
 import os
-import shutil
 
 import bench
 
-SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "internal.h")
+
+def _sources():
+    texts = []
+    for f in bench.KERNEL_SOURCES:
+        with open(os.path.join(bench.ROOT, "paper_1708_03183_gb300", "csrc", f)) as fh:
+            texts.append(fh.read())
+    return texts
 
 
-def _copy_tree(tmp_path):
-    csrc = tmp_path / "paper_1708_03183_gb300" / "csrc"
-    csrc.mkdir(parents=True)
-    for f in SOURCES:
-        shutil.copy(os.path.join(bench.ROOT, "paper_1708_03183_gb300", "csrc", f), csrc / f)
-    (tmp_path / "profiles").mkdir()
-    return csrc
-
-
-def test_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
-    csrc = _copy_tree(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    h0 = bench.kernel_hash()
+def test_source_digest_ignores_comments_but_not_code():
+    texts = _sources()
+    h0 = bench.source_digest(texts)
     assert h0 == bench.kernel_hash()
-    p = csrc / "exec_body.cuh"
-    src = p.read_text()
-    p.write_text(src.replace("#pragma once", "// a new remark\n/* and a block\n   comment */\n#pragma once", 1))
-    assert bench.kernel_hash() == h0
-    p.write_text(src.replace("#pragma once", "#pragma once\nconstexpr int kUnused = 1;", 1))
-    assert bench.kernel_hash() != h0
+    commented = list(texts)
+    commented[1] = commented[1].replace("#pragma once", "// a new remark\n/* and a block\n   comment */\n#pragma once", 1)
+    assert commented[1] != texts[1] and bench.source_digest(commented) == h0
+    respaced = [t.replace("\n", "\n\n") for t in texts]
+    assert bench.source_digest(respaced) == h0
+    changed = list(texts)
+    changed[1] = changed[1].replace("#pragma once", "#pragma once\nconstexpr int kUnused = 1;", 1)
+    assert bench.source_digest(changed) != h0
 
 
-def test_traffic_counts_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
-    _copy_tree(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    entry = {"bytes_per_step": 4.5e9, "source_hash": bench.kernel_hash()}
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k<2,256>": {"large": entry}}))
-    assert bench.ncu_traffic("k<2,256>", "large", 200) == 4.5e9 * 200
-    assert bench.ncu_traffic("k<2,256>", "other", 200) is None
-    assert bench.ncu_traffic("k<3,256>", "large", 200) is None
-    entry["source_hash"] = "0" * 16
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k<2,256>": {"large": entry}}))
-    assert bench.ncu_traffic("k<2,256>", "large", 200) is None
+def test_traffic_counts_only_for_the_source_it_was_taken_on():
+    table = {"k<2,256>": {"large": {"bytes_per_step": 4.5e9, "source_hash": "a" * 16}}}
+    assert bench.ncu_traffic("k<2,256>", "large", 200, table, "a" * 16) == 4.5e9 * 200
+    assert bench.ncu_traffic("k<2,256>", "large", 200, table, "b" * 16) is None
+    assert bench.ncu_traffic("k<2,256>", "other", 200, table, "a" * 16) is None
+    assert bench.ncu_traffic("k<3,256>", "large", 200, table, "a" * 16) is None
 
 
 def test_committed_traffic_entries_are_complete():
