@@ -23,11 +23,16 @@ Interior facet f = (c0, c1) with c0 < c1; n is the unit normal pointing out of c
 {a} = (a|c0 + a|c1)/2, [[a]] = a|c0 - a|c1.  Stress is stored as (xx, yy, xy); the xy test
 function is phi (e_xy + e_yx), so tau : grad v counts the xy entry twice.
 
-Every integral is exact (rational reference matrices from refelem.py); cell loops run over
-cells in ascending order, facet loops over facets in ascending order, each incrementing both
-of its cells, exactly as the loops of the chain are written.  No blocking, fusion or
-reordering: this is the untiled loop-by-loop chain, with the assembly of b and the solve with
-the block-diagonal mass matrix kept as separate steps.
+Every integral is exact (rational reference matrices from refelem.py).  Cell loops run over
+all cells at once (numpy rows in ascending cell order).  A facet loop visits its facets class by
+class, a class being the facets with the same (local face of c0, local face of c1, flip) and
+hence the same reference face matrices; within a class the facets are in ascending order, and
+each facet increments both of its cells (np.add.at).  Facet increments therefore reach a cell in
+class order rather than in plain facet order, which changes only the rounding of the sums; the
+loop-by-loop semantics are those of the chain (the paper lets iterations of a loop run in any
+order, Section 2).  No blocking, fusion or reordering of loops: this is the untiled
+loop-by-loop chain, with the assembly of b and the solve with the block-diagonal mass matrix
+kept as separate steps.
 
 Facets are numbered by (min vertex id, max vertex id) of the original vertex numbering.
 """

@@ -77,3 +77,34 @@ def test_mirror_symmetric_source_on_the_gpu(lib, p, ts):
         vg, sg = v.cpu().numpy(), s.cpu().numpy()
         assert mirror_defect(vg, sg, pairs) < 1e-12
         assert rel_l2(vg, vo) < TOL and rel_l2(sg, so) < TOL
+
+
+@pytest.mark.parametrize("where", ["edge", "vertex"])
+def test_source_on_a_shared_edge_or_vertex_goes_to_the_smallest_cell(lib, where):
+    # a point source on an edge or vertex shared by several cells: the library projects it into
+    # the smallest containing cell id, as the oracle does, so the fields agree from zero
+    import torch
+    import synth
+    m = synth.make_mesh(8, 6, seed=5)
+    c2v, coords = np.asarray(m["cell2vert"]), np.asarray(m["coords"])
+    p, nc = 2, c2v.shape[0]
+    Np = (p + 1) * (p + 2) // 2
+    mat = synth.homogeneous(m, 1.0, 2.0, 1.0)
+    dt = synth.cfl_dt(m, 2.0, p)
+    ricker = synth.ricker_series(5.0, dt, 12)
+    dg = ElasticDG(m, p, *mat)
+    if where == "edge":
+        c0, f0, c1 = (int(x) for x in dg.ifacets[len(dg.ifacets) // 2, :3])
+        a, b = c2v[c0, f0], c2v[c0, (f0 + 1) % 3]
+        xs, owners = 0.5 * (coords[a] + coords[b]), [c0, c1]
+    else:
+        v = next(v for v in range(coords.shape[0]) if (c2v == v).any(1).sum() == 6)
+        xs, owners = coords[v], list(np.nonzero((c2v == v).any(1))[0])
+    assert len(owners) >= 2 and dg.locate(xs)[0] == min(owners)
+    vo, so = dg.run(np.zeros((nc, 2, Np)), np.zeros((nc, 3, Np)), dt, 12, ricker, xs)
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], p, *mat, xs)
+    for sched in (None, lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=16, split=(9,))):
+        v = torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda")
+        s = torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda")
+        lib.slt_execute(mesh, sched, v, s, torch.tensor(ricker, device="cuda"), dt, 12)
+        assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL

@@ -324,3 +324,64 @@ def test_source_on_the_mirror_axis_gives_a_symmetric_field(p):
     # and the check itself is sharp: a source off the axis breaks the symmetry
     v2, s2 = dg.run(np.zeros_like(v), np.zeros_like(s), dt, 30, ricker, np.array([0.47, 0.70]))
     assert mirror_defect(v2, s2, _mirror_pairs(m, p)) > 1e-3
+
+
+# ----------------------------------------------------------------------- point source
+def _cell_integrals(X, p, q):
+    """int_K phi_i q dx for the nodal basis phi_i of the triangle with vertices X [3, 2] and a
+    function q(x, y) (vectorised), by a collapsed Gauss-Legendre rule (exact for the degree-2p
+    integrands here): (r, s) = (u (1 - v), v) on the unit square, Jacobian (1 - v)."""
+    t, w = np.polynomial.legendre.leggauss(p + 3)
+    t, w = 0.5 * (t + 1), 0.5 * w
+    u, v = np.meshgrid(t, t, indexing="ij")
+    wt = (w[:, None] * w[None, :] * (1 - v)).ravel()
+    r, s = (u * (1 - v)).ravel(), v.ravel()
+    x = X[0] + np.outer(r, X[1] - X[0]) + np.outer(s, X[2] - X[0])
+    J = np.array([X[1] - X[0], X[2] - X[0]]).T
+    phi = refelem.eval_basis(p, r, s)
+    return abs(np.linalg.det(J)) * (phi * (wt * q(x[:, 0], x[:, 1]))[:, None]).sum(0)
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+def test_point_source_reproduces_point_evaluation(p):
+    # The projected point source c = M_K^-1 phi(xs) / |det J_K| is the discrete delta: for every
+    # q in P_p on the source cell, sum_i c_i int_K phi_i q = q(xs).  A dropped 1/|det J|, phi(xs)
+    # in place of M^-1 phi(xs), or wrong reference coordinates of xs each break it.
+    m, dg = _dg(nx=5, ny=4, p=p, seed=3)
+    rng = np.random.default_rng(20 + p)
+    X = np.asarray(m["cellxy"], dtype=np.float64)
+    for _ in range(4):
+        c0 = int(rng.integers(dg.nc))
+        lam = rng.dirichlet(np.ones(3))
+        xs = lam @ X[c0]
+        cell, coef = dg.source_vector(xs)
+        assert cell == c0
+        for a in range(p + 1):
+            for b in range(p + 1 - a):
+                q = lambda x, y, a=a, b=b: x ** a * y ** b
+                lhs = coef @ _cell_integrals(X[cell], p, q)
+                assert abs(lhs - xs[0] ** a * xs[1] ** b) < 1e-12, (p, a, b, lhs)
+        # a random polynomial of full degree p
+        cf = rng.standard_normal((p + 1, p + 1))
+        q = lambda x, y: sum(cf[a, b] * x ** a * y ** b for a in range(p + 1) for b in range(p + 1 - a))
+        assert abs(coef @ _cell_integrals(X[cell], p, q) - q(xs[0], xs[1])) < 1e-11
+
+
+def test_point_source_location_takes_the_smallest_containing_cell():
+    # xs on an edge shared by two cells, and on a vertex shared by several: the cell is the
+    # smallest original id among the cells containing xs
+    m, dg = _dg(nx=6, ny=5, p=1, seed=4)
+    c2v = np.asarray(m["cell2vert"])
+    coords = np.asarray(m["coords"], dtype=np.float64)
+    rng = np.random.default_rng(7)
+    F = dg.ifacets
+    for k in rng.choice(len(F), 6, replace=False):
+        c0, f0, c1 = int(F[k, 0]), int(F[k, 1]), int(F[k, 2])
+        a, b = c2v[c0, f0], c2v[c0, (f0 + 1) % 3]
+        assert {a, b} <= set(c2v[c1].tolist())
+        xs = 0.5 * (coords[a] + coords[b])
+        assert dg.locate(xs)[0] == min(c0, c1)
+    interior = [v for v in range(coords.shape[0]) if (c2v == v).any(1).sum() == 6]
+    for v in rng.choice(interior, 4, replace=False):
+        owners = np.nonzero((c2v == v).any(1))[0]
+        assert dg.locate(coords[v])[0] == owners.min()
