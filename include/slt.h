@@ -333,7 +333,9 @@ int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const doub
  * 17.8 MB (17,826,560 bytes), held by every GPU that loads the library until the process exits.
  *  - n may not exceed 1,048,576 (SLT_ERR_ARG otherwise, nothing launched).
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *    that device current; make that first call before any stream capture.
+ *    that device current; make that first call before any stream capture.  Every later call
+ *    made outside stream capture looks it up again, so the address stays right after a
+ *    cudaDeviceReset (which reloads the module).
  *  - All calls share the array: calls whose GPU work overlaps (different streams or host
  *    threads without ordering) race and give wrong ranks; order them on one stream. */
 int slt_seed_rank_noalloc(const double* d_xy, int64_t n, int32_t* d_rank, void* stream);

@@ -30,13 +30,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
-unsigned char* scratch_address() {
+// Device address of g_scratch on the current device.  A call outside stream capture looks it
+// up afresh (a cudaDeviceReset reloads the module, and the array may then sit elsewhere); a call
+// on a capturing stream uses the address found by the last earlier call on that device.
+unsigned char* scratch_address(cudaStream_t s) {
   int dev = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) slt::fail(SLT_ERR_UNSUPPORTED, "device index beyond 63");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // unknown: keep the address already found
+  }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_addr[dev]) {
     void* p = nullptr;
     SLT_CUDA(cudaGetSymbolAddress(&p, g_scratch));
     g_addr[dev] = static_cast<unsigned char*>(p);
@@ -54,7 +61,7 @@ extern "C" int slt_seed_rank_noalloc(const double* d_xy, int64_t n, int32_t* d_r
     if (n > 0 && (!d_xy || !d_rank)) slt::fail(SLT_ERR_ARG, "null argument");
     if (n == 0) return SLT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned char* base = scratch_address();
+    unsigned char* base = scratch_address(s);
     auto* box = reinterpret_cast<unsigned long long*>(base);
     auto* keys = reinterpret_cast<uint32_t*>(base + kBoxBytes);
     auto* vals = keys + kMaxPoints;
