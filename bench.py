@@ -206,6 +206,51 @@ print(json.dumps({"t": t, "nc": nc, "Np": Np}))
     return 5 * d["Np"] * d["nc"] * nsteps / d["t"], d
 
 
+def oracle_all_cores(cfg_name, nsteps, scale=4, procs=None):
+    """The oracle on every host core at once: `procs` independent processes (default: every CPU
+    of the host), each running `nsteps` steps of the same sample as oracle_sample_rate on one
+    core.  The oracle's loops are single-threaded numpy, so replicas are how it uses the host;
+    the rate is the sum of the replicas' rates.  Returns (dof-updates/s, processes, seconds)."""
+    procs = procs or os.cpu_count() or 1
+    code = r"""
+import json, os, sys, time
+import numpy as np
+os.sched_setaffinity(0, range(os.cpu_count()))
+sys.path.insert(0, %r)
+import synth
+from oracle.dg import ElasticDG
+c = synth.CONFIGS[%r]
+cfg = synth.build_config(%r, nx=c["nx"] // %d, ny=c["ny"] // %d, nsteps=%d)
+dg = ElasticDG(cfg["mesh"], cfg["p"], cfg["rho"], cfg["lam"], cfg["mu"])
+nc, Np = dg.nc, dg.Np
+v, s = np.zeros((nc, 2, Np)), np.zeros((nc, 3, Np))
+sys.stdout.write("ready\n"); sys.stdout.flush()
+sys.stdin.readline()
+t = time.perf_counter()
+dg.run(v, s, cfg["dt"], %d, cfg["ricker"], cfg["src"])
+t = time.perf_counter() - t
+print(json.dumps({"t": t, "nc": nc, "Np": Np}))
+""" % (ROOT, cfg_name, cfg_name, scale, scale, nsteps, nsteps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    for q in ps:                    # every replica has built its mesh: start them together
+        if q.stdout.readline().strip() != "ready":
+            raise RuntimeError(q.stderr.read()[-2000:])
+    t0 = time.perf_counter()
+    for q in ps:
+        q.stdin.write("go\n")
+        q.stdin.flush()
+    rate = 0.0
+    for q in ps:
+        out, err = q.communicate(timeout=900)
+        if q.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        d = json.loads(out.strip().splitlines()[-1])
+        rate += 5 * d["Np"] * d["nc"] * nsteps / d["t"]
+    return rate, procs, time.perf_counter() - t0
+
+
 def inspector_timing(slt, synth, args, scale=4):
     """The GPU inspector against the oracle inspector (sequential C on one host core) on the same
     mesh: the bench workload's generator reduced by `scale` in each direction, the bench's tile
@@ -462,10 +507,10 @@ def main():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-p4", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
-    ap.add_argument("--p4-steps", type=int, default=100)
-    ap.add_argument("--multi-steps", type=int, default=40)
+    ap.add_argument("--p4-steps", type=int, default=200)
+    ap.add_argument("--multi-steps", type=int, default=200)
     ap.add_argument("--shots", type=int, default=64)
-    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64])
     ap.add_argument("--shots-per-cta", type=lambda t: [int(x) for x in t.split(",")], default=[16, 64])
     args = ap.parse_args()
@@ -543,6 +588,7 @@ def main():
     kern_s = prof["chain_ms"] * 1e-3
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
+    probe = slt.slt_fp64_peak()
     kname = ("k_dataflow<%d,%d>", "k_tiled<%d,%d>", "k_dataflow_cluster<%d,%d>")[args.executor] % (p, args.block)
     traffic = ncu_traffic(kname, args.config, args.steps) if args.scale == 1 and args.block == 256 else None
     tiled_bytes = cost["tiled_bytes_per_step"]
@@ -561,13 +607,20 @@ def main():
                         "frac": achieved / FP64_PEAK_TFLOPS,
                         "traffic": traffic, "kernel": kname,
                         "peak_kind": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal unit counts)",
+                        "measured_fp64": {"dfma_tflops": probe["dfma_tflops"], "dmma_tflops": probe["dmma_tflops"],
+                                          "dfma_and_dmma_tflops": probe["mixed_tflops"],
+                                          "how": "slt_fp64_peak: 8 independent DFMA chains per thread / 4 "
+                                                 "mma.sync.m8n8k4.f64 accumulators per warp, 8 x 256-thread "
+                                                 "blocks per SM, CUDA events"},
+                        "frac_of_measured_dfma": achieved / probe["dfma_tflops"],
                         "launch_ms_avg": prof["chain_ms"] / max(prof["chain_launches"], 1),
+                        "launches": prof["chain_launches"], "steps_per_launch": args.steps / max(prof["chain_launches"], 1),
                         "flops_per_step": flops},
            "hbm": {"algorithmic_bytes_per_step": tiled_bytes,
                    "achieved_gbs": tiled_bytes * args.steps / kern_s / 1e9, "peak_gbs": hbm_peak,
                    "frac": tiled_bytes * args.steps / kern_s / 1e9 / hbm_peak, "peak_kind": hbm_kind},
            "clocks": clocks,
-           "gpu_launches": prof["chain_launches"] + prof["layout_launches"]}
+           "gpu_launches": prof["chain_launches"] + prof["layout_launches"] + prof["setup_launches"]}
     if args.executor != 1:
         # the dependency graph the dataflow executor ran: time per step cannot fall below the
         # longest chain (in node times), and reaches the work bound only when the nodes of a step
@@ -637,8 +690,14 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, d = oracle_sample_rate(args.config, 10)
         out["cpu_baseline"] = {"value": rate, "unit": "dof-updates/s", "cores": 1, "kind": "oracle",
+                               "host_nproc": os.cpu_count(),
                                "sample": "10 time steps of the same generator's mesh reduced 4x per direction "
                                          "(%d cells, P%d), single BLAS thread, %.1f s" % (d["nc"], p, d["t"])}
+        arate, aprocs, asec = oracle_all_cores(args.config, 10)
+        out["cpu_baseline"]["all_cores"] = {
+            "value": arate, "unit": "dof-updates/s", "cores": aprocs, "kind": "oracle",
+            "sample": "%d independent oracle processes, one per host CPU, each the 1-core sample above; "
+                      "sum of their rates, %.1f s wall" % (aprocs, asec)}
         others = {}
         for name, steps, scale in (("tiny", 20, 1), ("p4", 3, 4)):
             r, dd = oracle_sample_rate(name, steps, scale)

@@ -217,10 +217,11 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
 int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                 double dt, int64_t nsteps, void* stream);
 /* slt_execute that also times every kernel launch with CUDA events recorded on `stream` and
-   synchronises before returning.  profile[0] = total ms of the chain kernels (the dataflow
-   executor's counter set-up included), [1] their number of kernel launches, [2] ms of the
+   synchronises before returning.  profile[0] = total ms of the chain kernels (with a dataflow
+   executor: its persistent kernel alone), [1] their number of kernel launches, [2] ms of the
    layout kernels (caller <-> work layout), [3] their launches, [4] longest and [5] shortest
-   timed chain interval in ms, [6..7] zero.  Not thread-safe:
+   timed chain interval in ms, [6] ms of the dataflow executor's queue set-up kernels (counter
+   reset and seeding) and [7] their launches (0 without a dataflow executor).  Not thread-safe:
    one profiled call at a time per process. */
 int slt_execute_profiled(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                          double dt, int64_t nsteps, void* stream, double profile[8]);
@@ -322,6 +323,17 @@ int slt_record(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const doubl
 int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
                 int64_t nsteps, const double* data, int32_t checkpoint_every, double* grad, double* misfit,
                 void* stream);
+
+/* ------------------------------------------------------------------ FP64 peak probe
+ * The paper has no counterpart: it measures the arithmetic roof of this library's kernels on the
+ * current GPU (the chain is FP64 arithmetic, and the driver's measured peaks cover only an HBM
+ * copy and a bf16 GEMM).  Runs three probe kernels on `stream` (8 blocks of 256 threads per SM,
+ * one warm-up launch each, CUDA-event timing) and synchronises:
+ * out[0] = FP64 fused multiply-add throughput (TFLOP/s, an FMA counts 2: 8 independent chains
+ * per thread), out[1] = FP64 warp-level tensor throughput (mma.sync.m8n8k4.f64, 512 flop per
+ * instruction; 4 independent accumulators per warp), out[2] = both issued at once (half the warps
+ * each, equal flops), out[3] = total ms of the three timed launches.  Allocates nothing. */
+int slt_fp64_peak(void* stream, double out[4]);
 
 /* ------------------------------------------------------------------ allocation-free ranking
  * The paper has no counterpart to this entry point: it serves callers who cannot allocate

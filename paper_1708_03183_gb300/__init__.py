@@ -62,6 +62,7 @@ _SIGS = {
     "slt_group_execute": (ctypes.c_int, [P, P, P, P, P, I64, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
+    "slt_fp64_peak": (ctypes.c_int, [P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
     "slt_mesh_set_source": (ctypes.c_int, [P, P, P]),
     "slt_receivers_create": (ctypes.c_int, [P, I32, P, P]),
@@ -267,6 +268,13 @@ def slt_mesh_cost(mesh):
                 nnz_dr_ds=int(c[3]))
 
 
+def slt_fp64_peak(stream=None):
+    """Measured FP64 throughput of this GPU (TFLOP/s): DFMA, DMMA (mma.sync m8n8k4), both at once."""
+    o = np.zeros(4, dtype=np.float64)
+    _check(lib.slt_fp64_peak(_stream(stream), ctypes.c_void_p(o.ctypes.data)))
+    return dict(dfma_tflops=float(o[0]), dmma_tflops=float(o[1]), mixed_tflops=float(o[2]), probe_ms=float(o[3]))
+
+
 def slt_mesh_chain(mesh):
     h = ctypes.c_void_p()
     _check(lib.slt_mesh_chain(mesh.ptr, ctypes.byref(h)))
@@ -298,7 +306,7 @@ def slt_execute_profiled(mesh, sched, v, sigma, ricker, dt, nsteps, stream=None)
                                     _dev(sigma, "float64"), _dev(ricker, "float64"), float(dt), int(nsteps),
                                     _stream(stream), ctypes.c_void_p(prof.ctypes.data)))
     return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
-                max_launch_ms=prof[4], min_launch_ms=prof[5])
+                max_launch_ms=prof[4], min_launch_ms=prof[5], setup_ms=prof[6], setup_launches=int(prof[7]))
 
 
 def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, stream=None, profile=False):
@@ -321,7 +329,7 @@ def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, strea
                                    _stream(stream), ctypes.c_void_p(prof.ctypes.data) if profile else None))
     if profile:
         return dict(chain_ms=prof[0], chain_launches=int(prof[1]), layout_ms=prof[2], layout_launches=int(prof[3]),
-                    max_launch_ms=prof[4], min_launch_ms=prof[5])
+                    max_launch_ms=prof[4], min_launch_ms=prof[5], setup_ms=prof[6], setup_launches=int(prof[7]))
 
 
 def _group_args(meshes, vs, sigmas, rickers, dts, nsteps):

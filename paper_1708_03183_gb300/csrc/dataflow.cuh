@@ -234,9 +234,11 @@ inline void dataflow_check(::slt_schedule_s* sched, cudaStream_t s) {
 }
 
 // The queue state and sub-chain table of one run of the schedule's plan (plan pointers into `a`),
-// the queue reset and seeded on s.  Returns false when there is nothing to run.
-template <class RB>
-bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaStream_t s, DF& df, RB rec_begin) {
+// the queue reset and seeded on s.  Returns false when there is nothing to run.  rec_begin(cls,
+// launches) / rec_end() bracket the two set-up kernels (class 2) for the caller's timing.
+template <class RB, class RE>
+bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaStream_t s, DF& df, RB rec_begin,
+                      RE rec_end) {
   slt::DataflowPlan& D = sched->df;
   df = DF{};
   DFQ& q = df.q;
@@ -269,20 +271,22 @@ bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaSt
   q.max_spins = sched->wait_spins;
   SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
   SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
-  rec_begin();
+  rec_begin(2, 2);
   k_df_init<<<(unsigned)std::min<long long>((q.total + 255) / 256, 152 * 16), 256, 0, s>>>(q, D.indeg0.p,
                                                                                           D.indeg.p);
   k_df_seed<<<(q.G + 255) / 256, 256, 0, s>>>(q, D.indeg0.p);
+  rec_end();
   SLT_CUDA(cudaGetLastError());
   return true;
 }
 
-// Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin` / `rec_end` bracket
-// the three kernels for the caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
+// Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin(cls, launches)` /
+// `rec_end()` bracket the set-up kernels (class 2) and the persistent kernel (class 0) for the
+// caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
 template <int P, bool BATCH, class RB, class RE>
 void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end) {
   DF df;
-  if (!prepare_dataflow(sched, a, nsteps, s, df, rec_begin)) return;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, rec_begin, rec_end)) return;
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -291,6 +295,7 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
     SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
     const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), df.q.total);
     sched->df.last_grid = grid;
+    rec_begin(0, 1);
     kernel<<<(unsigned)grid, threads, 0, s>>>(a, df);
   };
   if (bs == 128) launch(k_dataflow<P, 128, BATCH>, 128);

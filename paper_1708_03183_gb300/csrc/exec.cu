@@ -128,7 +128,7 @@ __global__ void k_from_work(const double* __restrict__ in, int rows, const int32
 // Optional per-launch timing: events recorded on the launch stream around every kernel.
 struct Recorder {
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)
-  std::vector<int> cls;         // 0 = chain kernel, 1 = layout kernel
+  std::vector<int> cls;         // 0 = chain kernel, 1 = layout kernel, 2 = dataflow queue set-up
   std::vector<int> nl;          // kernel launches inside each timed pair
   bool on = false;
   void begin(int c, cudaStream_t s, int launches = 1) {
@@ -148,7 +148,7 @@ struct Recorder {
   void finish(cudaStream_t s, double* out) {
     if (!on) return;
     SLT_CUDA(cudaStreamSynchronize(s));
-    double tot[2] = {0, 0}, cnt[2] = {0, 0}, mx = 0, mn = 1e300;
+    double tot[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, mx = 0, mn = 1e300;
     for (size_t i = 0; i < cls.size(); ++i) {
       float ms = 0;
       SLT_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
@@ -158,7 +158,7 @@ struct Recorder {
     }
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     out[0] = tot[0]; out[1] = cnt[0]; out[2] = tot[1]; out[3] = cnt[1];
-    out[4] = cnt[0] ? mx : 0; out[5] = cnt[0] ? mn : 0; out[6] = 0; out[7] = 0;
+    out[4] = cnt[0] ? mx : 0; out[5] = cnt[0] ? mn : 0; out[6] = tot[2]; out[7] = cnt[2];
   }
 };
 Recorder g_rec;
@@ -214,14 +214,17 @@ void io_grid(int64_t n, int& g) {
 
 template <int P>
 void run_dataflow(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
-  launch_dataflow<P, false>(sched, a, nsteps, s, [&] { g_rec.begin(0, s, 3); }, [&] { g_rec.end(s); });
+  launch_dataflow<P, false>(sched, a, nsteps, s, [&](int c, int n) { g_rec.begin(c, s, n); },
+                            [&] { g_rec.end(s); });
 }
 
 // executor 2: one cluster of `sched->cluster` 256-thread CTAs per tile, as many clusters as fit
 template <int P>
 void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
   DF df;
-  if (!prepare_dataflow(sched, a, nsteps, s, df, [&] { g_rec.begin(0, s, 3); })) return;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, [&](int c, int n) { g_rec.begin(c, s, n); },
+                        [&] { g_rec.end(s); }))
+    return;
   const int C = sched->cluster;
   auto kernel = k_dataflow_cluster<P, 256>;
   cudaLaunchConfig_t cfg = {};
@@ -243,6 +246,7 @@ void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStre
   sched->df.last_grid = nclusters;
   if (sched->df_slot.n < (size_t)nclusters) sched->df_slot.alloc(nclusters);
   cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+  g_rec.begin(0, s, 1);
   SLT_CUDA(cudaLaunchKernelEx(&cfg, kernel, a, df, sched->df_slot.p));
   g_rec.end(s);
   SLT_CUDA(cudaGetLastError());

@@ -62,9 +62,9 @@ __global__ void k_from_work_b(const double* __restrict__ in, int rows, int S, co
 
 struct Timer {
   std::vector<cudaEvent_t> ev;
-  std::vector<int> nl;
+  std::vector<int> nl, cls;  // launches and class (0 chain, 1 layout, 2 queue set-up) of each pair
   bool on = false;
-  void begin(cudaStream_t s, int n) {
+  void begin(cudaStream_t s, int n, int c = 0) {
     if (!on) return;
     cudaEvent_t e0, e1;
     SLT_CUDA(cudaEventCreate(&e0));
@@ -72,6 +72,7 @@ struct Timer {
     ev.push_back(e0);
     ev.push_back(e1);
     nl.push_back(n);
+    cls.push_back(c);
     SLT_CUDA(cudaEventRecord(e0, s));
   }
   void end(cudaStream_t s) {
@@ -86,7 +87,8 @@ void run_batched(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaS
     for (int32_t s0 = 0; s0 < a.S; s0 += g) {
       a.s0 = s0;
       a.sg = std::min(g, a.S - s0);
-      launch_dataflow<P, true>(sched, a, nsteps, s, [&] { tm.begin(s, 3); }, [&] { tm.end(s); });
+      launch_dataflow<P, true>(sched, a, nsteps, s, [&](int c, int n) { tm.begin(s, n, c); },
+                               [&] { tm.end(s); });
     }
     return;
   }
@@ -141,7 +143,7 @@ void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* 
   Timer tm;
   tm.on = profile != nullptr;
   const int g = (int)std::min<int64_t>((m->nc * 5 * Np * S + 255) / 256, 152 * 32);
-  tm.begin(s, 2);
+  tm.begin(s, 2, 1);
   k_to_work_b<<<g, 256, 0, s>>>(v, 2 * Np, S, m->d_perm.p, m->nc, ncp, a.buf[B_V]);
   k_to_work_b<<<g, 256, 0, s>>>(sigma, 3 * Np, S, m->d_perm.p, m->nc, ncp, a.buf[B_S]);
   tm.end(s);
@@ -152,26 +154,26 @@ void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* 
     case 3: run_batched<3>(m, sched, a, nsteps, s, tm); break;
     case 4: run_batched<4>(m, sched, a, nsteps, s, tm); break;
   }
-  tm.begin(s, 2);
+  tm.begin(s, 2, 1);
   k_from_work_b<<<g, 256, 0, s>>>(a.buf[B_V], 2 * Np, S, m->d_perm.p, m->nc, ncp, v);
   k_from_work_b<<<g, 256, 0, s>>>(a.buf[B_S], 3 * Np, S, m->d_perm.p, m->nc, ncp, sigma);
   tm.end(s);
   SLT_CUDA(cudaGetLastError());
   if (tm.on) {
     SLT_CUDA(cudaStreamSynchronize(s));
-    double tot[2] = {0, 0}, cnt[2] = {0, 0}, mx = 0, mn = 1e300;
+    double tot[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, mx = 0, mn = 1e300;
     const size_t npairs = tm.nl.size();
     for (size_t i = 0; i < npairs; ++i) {
       float ms = 0;
       SLT_CUDA(cudaEventElapsedTime(&ms, tm.ev[2 * i], tm.ev[2 * i + 1]));
-      const int cls = (i == 0 || i + 1 == npairs) ? 1 : 0;  // first and last pairs: layout kernels
+      const int cls = tm.cls[i];
       tot[cls] += ms;
       cnt[cls] += tm.nl[i];
       if (!cls) { mx = std::max(mx, (double)ms); mn = std::min(mn, (double)ms); }
     }
     for (cudaEvent_t e : tm.ev) cudaEventDestroy(e);
     profile[0] = tot[0]; profile[1] = cnt[0]; profile[2] = tot[1]; profile[3] = cnt[1];
-    profile[4] = cnt[0] ? mx : 0; profile[5] = cnt[0] ? mn : 0; profile[6] = 0; profile[7] = 0;
+    profile[4] = cnt[0] ? mx : 0; profile[5] = cnt[0] ? mn : 0; profile[6] = tot[2]; profile[7] = cnt[2];
   }
 }
 
