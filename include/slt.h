@@ -99,9 +99,11 @@ typedef struct {
   int32_t split[15];     /* strictly increasing loop indices in (0, nloops) */
   int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases,
                             2 = dataflow with one thread-block cluster of 256-thread CTAs per tile
-                            (for large tiles; single-field runs) */
+                            (for large tiles; single-field runs), 3 = staged dataflow (each
+                            tile's sub-chain out of shared memory; single-field runs) */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
-  int32_t block_threads; /* threads per tile CTA: 128, 256 or 384 (0 = 256) */
+  int32_t block_threads; /* threads per tile CTA: 128, 256 or 384, and 512 or 768 for executors
+                            0 and 3 (0 = 256) */
   int32_t sub_tile_size[16]; /* seed tile size of sub-chain k (0 = tile_size): a fusion scheme
                                 with its own tile size per sub-chain (Section 7.2) */
   int32_t cluster_size;      /* executor 2: CTAs per tile cluster, 1..8 (0 = 8) */
@@ -155,6 +157,15 @@ int slt_schedule_dataflow_info(slt_schedule sched, double info[6]);
      5 local-map footprint offsets [ntiles+1](loop, desc = indirect descriptor index)
      6 local-map footprints (sorted targets per tile)
      7 local maps: position of map[i*arity+k] in the footprint of tile sigma_j[i]
+     8 dataflow graph: successor offsets [G + 1] over the G tiles of all sub-chains (tile t of
+       sub-chain k is node cum_k + t, cum_k the tiles of the earlier sub-chains; loop, desc ignored)
+     9 dataflow graph: successors, (node << 1) | 1 when the successor is the next step's node,
+       ascending within each node's list (one entry per distinct dependency)
+    10 dataflow graph: dependencies of each node's first-step instance [G] (same-step edges)
+    11 dataflow graph: dependencies of each node's later instances [G] (all edges)
+    12 staged executor: footprint offsets [ntiles + 1] of sub-chain `loop`
+    13 staged executor: footprints, per tile the cells (caller numbering) its segments touch, in
+       slot order (the tile's local map of the cell set over the whole sub-chain)
    The sub-chain is the one containing `loop` (kinds 0, 1: the sub-chain index in `loop`). */
 int slt_schedule_export(slt_schedule sched, int32_t kind, int32_t loop, int32_t desc,
                         int32_t* host_out, int64_t* n);
@@ -209,10 +220,18 @@ int slt_mesh_chain(slt_mesh mesh, slt_chain* out);
  *    each (step, tile) node runs once the tiles it overlaps have finished (lower colours of its
  *    sub-chain, the previous sub-chain's tiles on its cells): a linear extension of the same
  *    order.  Waits are bounded: SLT_ERR_TIMEOUT if one gives up;
- *  - executor 2: as executor 0 with one thread-block cluster of cluster_size CTAs per tile.
+ *  - executor 2: as executor 0 with one thread-block cluster of cluster_size CTAs per tile;
+ *  - executor 3 (staged): as executor 0, with each node run out of shared memory: the tile's
+ *    footprint (export kinds 12, 13) gets one slot per cell, the operands the tile has not
+ *    produced itself are gathered once per segment, every segment runs as compacted passes
+ *    (volume part, interior faces 0, 1, 2, free-surface faces, later cell loop) separated by
+ *    barriers, and temporaries go to global memory only where another tile or sub-chain reads
+ *    them.  slt_inspect fails with SLT_ERR_UNSUPPORTED when a tile's footprint exceeds the
+ *    shared memory of one CTA (about 470 cells at p = 2, 180 at p = 4: use a smaller tile size).
  * The dataflow executors synchronise the stream before returning (they read their error flag);
  * the untiled and colour-phase executors return after queueing their launches on `stream`.
- * Results are bit-identical across the three executors for one schedule.
+ * Results are bit-identical across the four executors for one schedule (the same per-cell
+ * arithmetic in the same order), and to the untiled chain where a tile holds the whole mesh.
  * Work buffers are owned by the mesh. */
 int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                 double dt, int64_t nsteps, void* stream);

@@ -37,27 +37,28 @@ inline int grid_for(int64_t n, int threads = 256) {
   return g < 1 ? 1 : (int)g;
 }
 
-// traces[r][c] = sum_j phi_rj V[c Np + j][w_r]
-__global__ void k_record(const double* __restrict__ V, int64_t ncp, int Np, int nrec, const int32_t* __restrict__ rw,
-                         const double* __restrict__ phi, double* __restrict__ out) {
+// traces[s][r][c] = sum_j phi_rj V[c Np + j][w_r S + s] (rows of fs = ncp S doubles)
+__global__ void k_record(const double* __restrict__ V, int64_t fs, int S, int Np, int nrec,
+                         const int32_t* __restrict__ rw, const double* __restrict__ phi, double* __restrict__ out) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * nrec) return;
-  int r = t >> 1, c = t & 1;
+  if (t >= 2 * nrec * S) return;
+  const int sh = t / (2 * nrec), r = (t >> 1) % nrec, c = t & 1;
   double acc = 0.0;
-  for (int j = 0; j < Np; ++j) acc = fma(phi[r * Np + j], V[(int64_t)(c * Np + j) * ncp + rw[r]], acc);
+  for (int j = 0; j < Np; ++j)
+    acc = fma(phi[r * Np + j], V[(int64_t)(c * Np + j) * fs + (int64_t)rw[r] * S + sh], acc);
   out[t] = acc;
 }
 
-// vt[c Np + i][w_r] += dt (trace - data)[r][c] q_r[i] / rho, receivers in order (one block)
-__global__ void k_inject(double* __restrict__ VT, int64_t ncp, int Np, int nrec, const int32_t* __restrict__ rw,
+// vt[c Np + i][w_r S + s] += dt (trace - data)[s][r][c] q_r[i] / rho, receivers in order (one block)
+__global__ void k_inject(double* __restrict__ VT, int64_t fs, int S, int Np, int nrec, const int32_t* __restrict__ rw,
                          const double* __restrict__ q, const double* __restrict__ tr, const double* __restrict__ dat,
                          const double* __restrict__ irho, double dt) {
-  for (int t = threadIdx.x; t < 2 * Np; t += blockDim.x) {
-    int c = t / Np, i = t % Np;
+  for (int t = threadIdx.x; t < 2 * Np * S; t += blockDim.x) {
+    const int sh = t / (2 * Np), c = (t / Np) % 2, i = t % Np;
     for (int r = 0; r < nrec; ++r) {
       int64_t w = rw[r];
-      double res = tr[2 * r + c] - dat[2 * r + c];
-      VT[(int64_t)(c * Np + i) * ncp + w] += dt * res * q[r * Np + i] * irho[w];
+      double res = tr[(sh * nrec + r) * 2 + c] - dat[(sh * nrec + r) * 2 + c];
+      VT[(int64_t)(c * Np + i) * fs + w * S + sh] += dt * res * q[r * Np + i] * irho[w];
     }
   }
 }
@@ -179,18 +180,20 @@ template <int P>
 __global__ void k_grad_s(const double* __restrict__ st, const double* __restrict__ Ev, const double* __restrict__ EABv,
                          const double* __restrict__ EAst, const double* __restrict__ Ast, const double* __restrict__ ABv,
                          const double* __restrict__ mat, const double* __restrict__ adet, int64_t nc, int64_t ncp,
-                         double dt, double c, double* __restrict__ g) {
+                         int S, double dt, double c, double* __restrict__ g) {
   constexpr int Np = (P + 1) * (P + 2) / 2;
   const double* M = c_mass[P];
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nc; w += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t fs = ncp * S;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nc * S; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = t / S;
     const double lam = mat[ncp + w], mu = mat[2 * ncp + w], d = adet[w];
     double l1, m1, l2, m2, l3, m3;
-    cforms<Np>(M, st, Ev, ncp, w, true, lam, mu, l1, m1);
-    cforms<Np>(M, st, EABv, ncp, w, true, lam, mu, l2, m2);
-    cforms<Np>(M, EAst, Ev, ncp, w, false, lam, mu, l3, m3);
-    g[w] += c * dt * d * vform<Np>(M, Ast, ABv, ncp, w);
-    g[ncp + w] += dt * d * (l1 + c * l2 + c * l3);
-    g[2 * ncp + w] += dt * d * (m1 + c * m2 + c * m3);
+    cforms<Np>(M, st, Ev, fs, t, true, lam, mu, l1, m1);
+    cforms<Np>(M, st, EABv, fs, t, true, lam, mu, l2, m2);
+    cforms<Np>(M, EAst, Ev, fs, t, false, lam, mu, l3, m3);
+    g[t] += c * dt * d * vform<Np>(M, Ast, ABv, fs, t);
+    g[fs + t] += dt * d * (l1 + c * l2 + c * l3);
+    g[2 * fs + t] += dt * d * (m1 + c * m2 + c * m3);
   }
 }
 
@@ -200,26 +203,34 @@ __global__ void k_grad_v(const double* __restrict__ vt, const double* __restrict
                          const double* __restrict__ ABAsig, const double* __restrict__ ABvt,
                          const double* __restrict__ Evt, const double* __restrict__ EAsig,
                          const double* __restrict__ mat, const double* __restrict__ adet, int64_t nc, int64_t ncp,
-                         double dt, double c, double* __restrict__ g) {
+                         int S, double dt, double c, double* __restrict__ g) {
   constexpr int Np = (P + 1) * (P + 2) / 2;
   const double* M = c_mass[P];
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nc; w += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t fs = ncp * S;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nc * S; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = t / S;
     const double lam = mat[ncp + w], mu = mat[2 * ncp + w], d = adet[w];
-    const double f1 = vform<Np>(M, vt, Asig, ncp, w) + c * vform<Np>(M, vt, ABAsig, ncp, w);
-    const double f2 = vform<Np>(M, ABvt, Asig, ncp, w);
+    const double f1 = vform<Np>(M, vt, Asig, fs, t) + c * vform<Np>(M, vt, ABAsig, fs, t);
+    const double f2 = vform<Np>(M, ABvt, Asig, fs, t);
     double l, m;
-    cforms<Np>(M, Evt, EAsig, ncp, w, false, lam, mu, l, m);
-    g[w] += -dt * d * (f1 + c * f2);
-    g[ncp + w] += -c * dt * d * l;
-    g[2 * ncp + w] += -c * dt * d * m;
+    cforms<Np>(M, Evt, EAsig, fs, t, false, lam, mu, l, m);
+    g[t] += -dt * d * (f1 + c * f2);
+    g[fs + t] += -c * dt * d * l;
+    g[2 * fs + t] += -c * dt * d * m;
   }
 }
 
+// the gradient in caller numbering, summed over the shots in order
 __global__ void k_grad_out(const double* __restrict__ g, const int32_t* __restrict__ perm, int64_t nc, int64_t ncp,
-                           double* __restrict__ out) {
+                           int S, double* __restrict__ out) {
+  const int64_t fs = ncp * S;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nc; w += (int64_t)gridDim.x * blockDim.x) {
     int64_t cell = perm[w];
-    for (int k = 0; k < 3; ++k) out[k * nc + cell] = g[k * ncp + w];
+    for (int k = 0; k < 3; ++k) {
+      double acc = g[k * fs + w * S];
+      for (int sh = 1; sh < S; ++sh) acc += g[k * fs + w * S + sh];
+      out[k * nc + cell] = acc;
+    }
   }
 }
 
@@ -256,7 +267,7 @@ void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
   SLT_CUDA(cudaMemsetAsync(m->work.p, 0, 5 * (int64_t)m->Np * ncp * sizeof(double), s));
   for (int64_t n = 0; n < nsteps; ++n) {
     exec_steps_work(m, sched, ricker, dt, n, 1, s);
-    k_record<<<(2 * rec->n + 127) / 128, 128, 0, s>>>(V, ncp, m->Np, rec->n, rec->w.p, rec->phi.p,
+    k_record<<<(2 * rec->n + 127) / 128, 128, 0, s>>>(V, ncp, 1, m->Np, rec->n, rec->w.p, rec->phi.p,
                                                       traces + n * 2 * rec->n);
   }
   SLT_CUDA(cudaGetLastError());
@@ -302,7 +313,7 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
     if (n % k == 0)
       SLT_CUDA(cudaMemcpyAsync(ckpt.p + (n / k) * state, V, state * sizeof(double), cudaMemcpyDeviceToDevice, s));
     exec_steps_work(m, sched, ricker, dt, n, 1, s);
-    k_record<<<(2 * rec->n + 127) / 128, 128, 0, s>>>(V, ncp, Np, rec->n, rec->w.p, rec->phi.p,
+    k_record<<<(2 * rec->n + 127) / 128, 128, 0, s>>>(V, ncp, 1, Np, rec->n, rec->w.p, rec->phi.p,
                                                       traces.p + n * 2 * rec->n);
   }
   k_misfit<<<1, 1024, 0, s>>>(traces.p, data, N * 2 * rec->n, dt, Jd.p);
@@ -359,16 +370,16 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
       op_A(m, st, T2b, s);       // A st
       op_E(m, T2b, T3c, s);      // E(A st)
       switch (P) {
-        case 1: k_grad_s<1><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 2: k_grad_s<2><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 3: k_grad_s<3><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 4: k_grad_s<4><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 1: k_grad_s<1><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 2: k_grad_s<2><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 3: k_grad_s<3><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 4: k_grad_s<4><<<gr, 128, 0, s>>>(st, Ev, EABv, T3c, T2b, ABv, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
       }
       hooke(T3c, T3a);           // BA st
       op_A(m, T3a, T2a, s);      // ABA st
       axpy(vt, T2b, T2a, -dt, -dt * c, 2 * Np);
       // receivers
-      k_inject<<<1, 128, 0, s>>>(vt, ncp, Np, rec->n, rec->w.p, rec->q.p, traces.p + n * 2 * rec->n,
+      k_inject<<<1, 128, 0, s>>>(vt, ncp, 1, Np, rec->n, rec->w.p, rec->q.p, traces.p + n * 2 * rec->n,
                                  data + n * 2 * rec->n, m->mat.p, dt);
       // velocity update (adjoint vt of v^{n+1/2})
       if (!kept) {
@@ -384,10 +395,10 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
       hooke(T3b, T3c);           // B vt
       op_A(m, T3c, T2c, s);      // AB vt
       switch (P) {
-        case 1: k_grad_v<1><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 2: k_grad_v<2><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 3: k_grad_v<3><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
-        case 4: k_grad_v<4><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, dt, c, g.p); break;
+        case 1: k_grad_v<1><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 2: k_grad_v<2><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 3: k_grad_v<3><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
+        case 4: k_grad_v<4><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, T2c, T3b, EAsig, m->mat.p, m->adet.p, nc, ncp, 1, dt, c, g.p); break;
       }
       op_E(m, T2c, T3a, s);      // E(AB vt)
       hooke(T3a, T3b);           // BAB vt
@@ -395,7 +406,137 @@ void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double
       SLT_CUDA(cudaGetLastError());
     }
   }
-  k_grad_out<<<gr, 256, 0, s>>>(g.p, m->d_perm.p, nc, ncp, grad_out);
+  k_grad_out<<<gr, 256, 0, s>>>(g.p, m->d_perm.p, nc, ncp, 1, grad_out);
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaMemcpyAsync(J_host, Jd.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+
+// ------------------------------------------------------------------ many shots, tiled or untiled
+// The same misfit and gradient for S shots at once (their sum over the shots), on the multi-shot
+// work layout (rows of ncp S doubles, column cell S + shot), with every operator application
+// run by the chain executors: the untiled phase kernels when sched is null, else the dataflow
+// executor on the schedule's tiles ({velocity, stress} fusion).
+//  - forward: one step at a time (the receivers record after each), checkpoints of (v, sigma)
+//    every k steps;
+//  - segment recompute: each step as its two sub-chains, their temporaries written into the
+//    step's keep slot (A sigma, E(A sigma), ABA sigma from the velocity sub-chain; E(v), AB v,
+//    E(AB v) from the stress sub-chain, whose last strain goes to its own slot);
+//  - reverse sweep: the adjoint step is the leapfrog run with -dt on (vt, st), so each step is
+//    the velocity sub-chain on (vt, st) (leaving A st and E(A st)), the stress-update gradient
+//    terms, the receiver residuals, the stress sub-chain on (vt, st) (leaving E(vt) and AB vt),
+//    and the velocity-update gradient terms.  The forward schedule serves unchanged: under the
+//    skew identity the adjoint step is the same loop chain, so its tiles and colours are legal
+//    for it as they are.
+void record_run_b(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t S, const int32_t* d_src_w,
+                  const double* d_src, const double* ricker, double dt, int64_t nsteps, double* traces,
+                  cudaStream_t s) {
+  const int64_t Np = m->Np, fs = m->ncp * S;
+  DevBuf<double> fwd(15 * Np * fs);
+  SLT_CUDA(cudaMemsetAsync(fwd.p, 0, 5 * Np * fs * sizeof(double), s));
+  ChainRun r;
+  r.S = S;
+  for (int b = 0; b < 6; ++b) r.buf[b] = fwd.p + (b == 0 ? 0 : b == 1 ? 2 : b == 2 ? 5 : b == 3 ? 7 : b == 4 ? 9 : 12) * Np * fs;
+  r.dt = dt;
+  r.src_w = d_src_w;
+  r.src = d_src;
+  const int nrec = rec->n;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    r.ricker = ricker ? ricker + n : nullptr;
+    chain_part_b(m, sched, r, 2, s);
+    k_record<<<(2 * nrec * S + 127) / 128, 128, 0, s>>>(r.buf[0], fs, S, (int)Np, nrec, rec->w.p, rec->phi.p,
+                                                        traces + n * 2 * nrec * S);
+  }
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+void adjoint_run_b(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t S, const int32_t* d_src_w,
+                   const double* d_src, const double* ricker, double dt, int64_t N, const double* data, int32_t k,
+                   double* grad_out, double* J_host, cudaStream_t s) {
+  if (k < 1) fail(SLT_ERR_ARG, "checkpoint_every must be >= 1 for the multi-shot or tiled adjoint");
+  const int Np = m->Np, P = m->p;
+  const int64_t nc = m->nc, ncp = m->ncp, fs = ncp * S, R = Np * fs;  // R: Np rows
+  const int64_t nseg = (N + k - 1) / k;
+  const int nrec = rec->n;
+  DevBuf<double> fwd(15 * R), ckpt(std::max<int64_t>(nseg, 1) * 5 * R), keep((int64_t)k * 15 * R);
+  DevBuf<double> adj(18 * R), g(3 * fs), traces(std::max<int64_t>(N * 2 * nrec * S, 1)), Jd(1);
+  double* V = fwd.p;
+  double* Sg = fwd.p + 2 * R;
+  double* fU1 = fwd.p + 5 * R;
+  double* fU2 = fwd.p + 7 * R;
+  double* fE = fwd.p + 9 * R;
+  double* fS1 = fwd.p + 12 * R;
+  double* vt = adj.p;             // 2 Np
+  double* st = vt + 2 * R;        // 3 Np
+  double* TA = st + 3 * R;        // 2 Np: A st, then AB vt
+  double* TEA = TA + 2 * R;       // 3 Np: E(A st), then E(AB vt) (not used)
+  double* TU2 = TEA + 3 * R;      // 2 Np
+  double* TS1 = TU2 + 2 * R;      // 3 Np
+  double* TE3 = TS1 + 3 * R;      // 3 Np: E(vt)
+  const double c = dt * dt / 24.0;
+  auto run = [&](double* v, double* sg, double* u1, double* u2, double* e, double* s1, double* e5,
+                 const double* rk, double h, const int32_t* sw, const double* sv, int part) {
+    ChainRun r;
+    r.S = S;
+    r.buf[0] = v; r.buf[1] = sg; r.buf[2] = u1; r.buf[3] = u2; r.buf[4] = e; r.buf[5] = s1;
+    r.e5 = e5;
+    r.ricker = rk;
+    r.dt = h;
+    r.src_w = sw;
+    r.src = sv;
+    chain_part_b(m, sched, r, part, s);
+  };
+  // forward: checkpoints and traces
+  SLT_CUDA(cudaMemsetAsync(fwd.p, 0, 5 * R * sizeof(double), s));
+  for (int64_t n = 0; n < N; ++n) {
+    if (n % k == 0)
+      SLT_CUDA(cudaMemcpyAsync(ckpt.p + (n / k) * 5 * R, V, 5 * R * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    run(V, Sg, fU1, fU2, fE, fS1, nullptr, ricker ? ricker + n : nullptr, dt, d_src_w, d_src, 2);
+    k_record<<<(2 * nrec * S + 127) / 128, 128, 0, s>>>(V, fs, S, Np, nrec, rec->w.p, rec->phi.p,
+                                                        traces.p + n * 2 * nrec * S);
+  }
+  k_misfit<<<1, 1024, 0, s>>>(traces.p, data, N * 2 * nrec * S, dt, Jd.p);
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaMemsetAsync(adj.p, 0, adj.n * sizeof(double), s));
+  SLT_CUDA(cudaMemsetAsync(g.p, 0, g.n * sizeof(double), s));
+  const int gr = grid_for(nc * S);
+  for (int64_t j = nseg - 1; j >= 0; --j) {
+    const int64_t n0 = j * k, n1 = std::min<int64_t>(N, n0 + k);
+    SLT_CUDA(cudaMemcpyAsync(V, ckpt.p + j * 5 * R, 5 * R * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int64_t n = n0; n < n1; ++n) {  // recompute, keeping each step's operator intermediates
+      double* K = keep.p + (n - n0) * 15 * R;
+      const double* rk = ricker ? ricker + n : nullptr;
+      run(V, Sg, K, K + 5 * R, K + 2 * R, fS1, nullptr, rk, dt, d_src_w, d_src, 0);
+      run(V, Sg, K + 10 * R, fU2, K + 7 * R, fS1, K + 12 * R, rk, dt, d_src_w, d_src, 1);
+    }
+    for (int64_t n = n1 - 1; n >= n0; --n) {
+      const double* K = keep.p + (n - n0) * 15 * R;
+      const double *Asig = K, *EAsig = K + 2 * R, *ABAsig = K + 5 * R, *Ev = K + 7 * R, *ABv = K + 10 * R,
+                   *EABv = K + 12 * R;
+      // velocity sub-chain of the adjoint step: vt -= dt (A st + c ABA st); leaves A st, E(A st)
+      run(vt, st, TA, TU2, TEA, TS1, nullptr, nullptr, -dt, nullptr, nullptr, 0);
+      switch (P) {
+        case 1: k_grad_s<1><<<gr, 128, 0, s>>>(st, Ev, EABv, TEA, TA, ABv, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 2: k_grad_s<2><<<gr, 128, 0, s>>>(st, Ev, EABv, TEA, TA, ABv, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 3: k_grad_s<3><<<gr, 128, 0, s>>>(st, Ev, EABv, TEA, TA, ABv, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 4: k_grad_s<4><<<gr, 128, 0, s>>>(st, Ev, EABv, TEA, TA, ABv, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+      }
+      k_inject<<<1, 256, 0, s>>>(vt, fs, S, Np, nrec, rec->w.p, rec->q.p, traces.p + n * 2 * nrec * S,
+                                 data + n * 2 * nrec * S, m->mat.p, dt);
+      // stress sub-chain: st -= dt (B vt + c BAB vt); leaves E(vt) and AB vt
+      run(vt, st, TA, TU2, TE3, TS1, TEA, nullptr, -dt, nullptr, nullptr, 1);
+      switch (P) {
+        case 1: k_grad_v<1><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, TA, TE3, EAsig, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 2: k_grad_v<2><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, TA, TE3, EAsig, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 3: k_grad_v<3><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, TA, TE3, EAsig, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+        case 4: k_grad_v<4><<<gr, 128, 0, s>>>(vt, Asig, ABAsig, TA, TE3, EAsig, m->mat.p, m->adet.p, nc, ncp, S, dt, c, g.p); break;
+      }
+      SLT_CUDA(cudaGetLastError());
+    }
+  }
+  k_grad_out<<<grid_for(nc), 256, 0, s>>>(g.p, m->d_perm.p, nc, ncp, S, grad_out);
   SLT_CUDA(cudaGetLastError());
   SLT_CUDA(cudaMemcpyAsync(J_host, Jd.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaStreamSynchronize(s));

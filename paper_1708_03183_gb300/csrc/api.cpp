@@ -213,13 +213,16 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
   REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
-  REQUIRE(opt->executor >= 0 && opt->executor <= 2, "executor must be 0, 1 or 2");
+  REQUIRE(opt->executor >= 0 && opt->executor <= 3, "executor must be 0, 1, 2 or 3");
   REQUIRE(opt->cluster_size >= 0 && opt->cluster_size <= 8, "cluster_size must be in 0..8");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
   REQUIRE(opt->shots_per_cta >= 0, "shots_per_cta must be >= 0");
   REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
-              opt->block_threads == 384,
-          "block_threads must be 0, 128, 256 or 384");
+              opt->block_threads == 384 || opt->block_threads == 512 || opt->block_threads == 768,
+          "block_threads must be 0, 128, 256, 384, 512 or 768");
+  REQUIRE(opt->block_threads <= 384 || opt->executor == 0 || opt->executor == 3,
+          "512- and 768-thread tiles are for the dataflow executors (executors 0 and 3)");
+  REQUIRE(opt->executor != 3 || c->mesh, "the staged executor runs the elastic chain of a mesh");
   const int nl = (int)c->loops.size();
   int prev = 0;
   for (int k = 0; k < opt->nsplit; ++k) {
@@ -244,6 +247,10 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   s->set_size = c->set_size;
   s->mesh = c->mesh;
   s->executor = opt->executor;
+  // staged executor: temporaries stay in shared memory unless another tile reads them; with a
+  // fusion other than {all loops} or {velocity, stress} some are read by a later sub-chain, so
+  // every temporary is then written out as well
+  s->stage_cross = !(opt->nsplit == 0 || (opt->nsplit == 1 && opt->split[0] == 9));
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
   if (opt->block_threads) s->block = opt->block_threads;
   s->shots_per_cta = opt->shots_per_cta;
@@ -292,7 +299,35 @@ int slt_schedule_dataflow_info(slt_schedule s, double info[6]) {
 int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc, int32_t* host_out, int64_t* n) {
   API_BEGIN
   REQUIRE(s && n, "null argument");
-  REQUIRE(kind >= 0 && kind <= 7, "unknown kind");
+  REQUIRE(kind >= 0 && kind <= 13, "unknown kind");
+  if (kind == 12 || kind == 13) {  // the staged executor's tile footprints of sub-chain `loop`
+    REQUIRE(loop >= 0 && loop < (int32_t)s->subs.size(), "unknown sub-chain");
+    const SubSched& S = s->subs[loop];
+    REQUIRE(S.fp_ptr.p, "the schedule has no staged plan (inspect with executor 3)");
+    if (kind == 12) {
+      *n = S.m + 1;
+      if (host_out) SLT_CUDA(cudaMemcpy(host_out, S.fp_ptr.p, (S.m + 1) * 4, cudaMemcpyDeviceToHost));
+    } else {
+      int32_t tot = 0;
+      SLT_CUDA(cudaMemcpy(&tot, S.fp_ptr.p + S.m, 4, cudaMemcpyDeviceToHost));
+      *n = tot;
+      if (host_out && tot) {
+        std::vector<int32_t> w = S.fp_cell.download(nullptr, tot);
+        for (int32_t i = 0; i < tot; ++i) host_out[i] = s->mesh->perm[w[i] & 0x7fffffff];
+      }
+    }
+    return SLT_OK;
+  }
+  if (kind >= 8) {  // the dataflow executor's dependency graph
+    const DataflowPlan& D = s->df;
+    REQUIRE(!D.cum.empty(), "the schedule has no executor plan (not inspected on a mesh chain)");
+    const int32_t G = D.cum.back();
+    const int32_t* src = kind == 8 ? D.succ_ptr.p : kind == 9 ? D.succ.p : kind == 10 ? D.indeg0.p : D.indeg.p;
+    const int64_t len = kind == 8 ? G + 1 : kind == 9 ? D.ndeps : G;
+    *n = len;
+    if (host_out && len) SLT_CUDA(cudaMemcpy(host_out, src, len * 4, cudaMemcpyDeviceToHost));
+    return SLT_OK;
+  }
   const SubSched* S = nullptr;
   int jj = 0;
   if (kind <= 1) {
@@ -457,6 +492,7 @@ int slt_mesh_create(const int32_t* cell2vert, const double* cellxy, int64_t nc, 
   m->geo.alloc(4 * ncp); m->geo.upload(hgeo.data(), 4 * ncp, s);
   m->fgeo.alloc(9 * ncp); m->fgeo.upload(hfgeo.data(), 9 * ncp, s);
   m->mat.alloc(3 * ncp); m->mat.upload(hmat.data(), 3 * ncp, s);
+  build_pre(m.get(), s);
   m->nbr.alloc(3 * ncp); m->nbr.upload(hnbr.data(), 3 * ncp, s);
   m->d_perm.alloc(nc); m->d_perm.upload(m->perm.data(), nc, s);
   {
@@ -508,11 +544,13 @@ int slt_mesh_cost(slt_mesh m, double cost[4]) {
   double nnz = 0.0;
   for (double x : m->ref.Dr) nnz += std::fabs(x) > 1e-12 * mx;
   for (double x : m->ref.Ds) nnz += std::fabs(x) > 1e-12 * mx;
-  // FP64 flops of the kernels in exec.cu (an FMA counts 2), structural zeros skipped
-  const double volB = 12 * Np + 4 * nnz + 4, volD = 13 * Np + 4 * nnz, hookeB = 2 + 7 * Np + volB;
-  const double cell = volB + 2 * hookeB + 3 * volD + 8 * Np + 19 * Np + 2;
-  const double side = (4 + 9 * Nfp + 4 * Np * Nfp) + (3 + 2 * Nfp + Np * (4 * Nfp + 6));
-  const double ext = 3 + 6 * Nfp + 4 * Np * Nfp;
+  // FP64 flops of the kernels in exec.cu (an FMA counts 2), structural zeros skipped; the
+  // per-cell products of geometry and material (metric terms over rho, scaled face normals,
+  // lambda + 2 mu) are computed once per mesh, not per step
+  const double volB = 12 * Np + 4 * nnz, volD = 13 * Np + 4 * nnz, hookeB = 7 * Np + volB;
+  const double cell = volB + 2 * hookeB + 3 * volD + 8 * Np + 19 * Np;
+  const double side = (9 * Nfp + 4 * Np * Nfp) + (2 * Nfp + Np * (4 * Nfp + 6));
+  const double ext = 2 + 6 * Nfp + 4 * Np * Nfp;
   // (the facet loops accumulate onto the loaded field values: no separate increment adds)
   cost[0] = m->nc * cell + 2.0 * m->nfi * 3 * side + m->nfe * 3 * ext;
   cost[1] = m->nc * (80 * Np + 140);
@@ -627,6 +665,7 @@ int slt_mesh_set_material(slt_mesh m, const double* rho, const double* lam, cons
     hmat[2 * ncp + w] = mu[c];
   }
   m->mat.upload(hmat.data(), 3 * ncp, as_stream(stream));
+  build_pre(m, as_stream(stream));
   SLT_CUDA(cudaStreamSynchronize(as_stream(stream)));
   API_END
 }

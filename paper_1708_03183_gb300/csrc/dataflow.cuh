@@ -37,6 +37,7 @@ struct DFQ {
   unsigned long long* tail;       // next slot to publish
   int32_t* err;                   // set when a wait gave up
   long long max_spins;
+  int32_t g_lo, g_hi;             // nodes of this run: tiles g_lo .. g_hi - 1 (one sub-chain, or all)
 };
 // one mesh: sub-chain table by value
 struct DF {
@@ -112,7 +113,7 @@ __device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
   for (int i = q.succ_ptr[g] + (int)(threadIdx.x & 31); i < q.succ_ptr[g + 1]; i += 32) {
     const int e = q.succ[i];
     const long long s2 = st + (e & 1);
-    if (s2 >= q.nsteps) continue;
+    if (s2 >= q.nsteps || (e >> 1) < q.g_lo || (e >> 1) >= q.g_hi) continue;
     const long long n2 = s2 * q.G + (e >> 1);
     if (atom_add_acq_rel(&q.pending[n2], -1) == 1) {
       const unsigned long long j = atomicAdd(q.tail, 1ull);
@@ -269,6 +270,8 @@ bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaSt
   q.tail = D.head.p + 1;
   q.err = D.err.p;
   q.max_spins = sched->wait_spins;
+  q.g_lo = 0;
+  q.g_hi = q.G;
   SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
   SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
   rec_begin(2, 2);
@@ -280,13 +283,77 @@ bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaSt
   return true;
 }
 
+// One time step of sub-chain k alone (its tiles in colour order, nothing of the other sub-chains):
+// the queue holds the sub-chain's tiles, each waiting only for the same-step dependencies inside
+// the sub-chain.  Node ids are global tile ids at step 0.
+__global__ void k_df_init_sub(DFQ q, const int32_t* __restrict__ indeg_sub) {
+  const int32_t n = q.g_hi - q.g_lo;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    q.pending[q.g_lo + i] = indeg_sub[q.g_lo + i];
+    q.queue[i] = -1;
+  }
+}
+__global__ void k_df_seed_sub(DFQ q, const int32_t* __restrict__ indeg_sub) {
+  for (int g = q.g_lo + blockIdx.x * blockDim.x + threadIdx.x; g < q.g_hi; g += gridDim.x * blockDim.x)
+    if (indeg_sub[g] == 0) {
+      unsigned long long j = atomicAdd(q.tail, 1ull);
+      q.queue[j] = g;
+    }
+}
+template <class RB, class RE>
+bool prepare_dataflow_sub(::slt_schedule_s* sched, Params& a, int k, cudaStream_t s, DF& df, RB rec_begin,
+                          RE rec_end) {
+  slt::DataflowPlan& D = sched->df;
+  df = DF{};
+  DFQ& q = df.q;
+  q.G = D.cum.back();
+  q.nsteps = 1;
+  q.g_lo = D.cum[k];
+  q.g_hi = D.cum[k + 1];
+  q.total = q.g_hi - q.g_lo;
+  if (q.total == 0) return false;
+  for (size_t j = 0; j < D.cum.size(); ++j) df.cum[j] = D.cum[j];
+  for (size_t j = 0; j < sched->subs.size(); ++j) {
+    const slt::SubSched& sub = sched->subs[j];
+    df.first[j] = sub.first;
+    df.last[j] = sub.last;
+    for (int jj = sub.first; jj < sub.last; ++jj) {
+      a.plan_ptr[jj] = sub.plan_ptr[jj - sub.first].p;
+      a.plan_items[jj] = sub.plan_items[jj - sub.first].p;
+    }
+  }
+  if (D.pending.n < (size_t)q.G) {
+    D.pending.alloc(q.G);
+    D.queue.alloc(q.G);
+  }
+  q.succ_ptr = D.succ_ptr.p;
+  q.succ = D.succ.p;
+  q.pending = D.pending.p;
+  q.queue = D.queue.p;
+  q.head = D.head.p;
+  q.tail = D.head.p + 1;
+  q.err = D.err.p;
+  q.max_spins = sched->wait_spins;
+  SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
+  SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
+  rec_begin(2, 2);
+  k_df_init_sub<<<(unsigned)std::min<long long>((q.total + 255) / 256, 152 * 16), 256, 0, s>>>(q, D.indeg_sub.p);
+  k_df_seed_sub<<<(unsigned)((q.total + 255) / 256), 256, 0, s>>>(q, D.indeg_sub.p);
+  rec_end();
+  SLT_CUDA(cudaGetLastError());
+  return true;
+}
+
 // Launch the dataflow executor for nsteps on the schedule's plan; `rec_begin(cls, launches)` /
 // `rec_end()` bracket the set-up kernels (class 2) and the persistent kernel (class 0) for the
 // caller's timing.  Synchronises; SLT_ERR_TIMEOUT when a wait gave up.
 template <int P, bool BATCH, class RB, class RE>
-void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end) {
+void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStream_t s, RB rec_begin, RE rec_end,
+                     int sub = -1) {
   DF df;
-  if (!prepare_dataflow(sched, a, nsteps, s, df, rec_begin, rec_end)) return;
+  if (sub >= 0 ? !prepare_dataflow_sub(sched, a, sub, s, df, rec_begin, rec_end)
+               : !prepare_dataflow(sched, a, nsteps, s, df, rec_begin, rec_end))
+    return;
   int dev = 0, nsm = 0, per = 0;
   SLT_CUDA(cudaGetDevice(&dev));
   SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -300,6 +367,11 @@ void launch_dataflow(::slt_schedule_s* sched, Params a, int64_t nsteps, cudaStre
   };
   if (bs == 128) launch(k_dataflow<P, 128, BATCH>, 128);
   else if (bs == 384) launch(k_dataflow<P, 384, BATCH>, 384);
+  else if (bs == 512 || bs == 768) {
+    if constexpr (BATCH) slt::fail(SLT_ERR_UNSUPPORTED, "the multi-shot dataflow executor takes 128-384 threads");
+    else if (bs == 512) launch(k_dataflow<P, 512, false>, 512);
+    else launch(k_dataflow<P, 768, false>, 768);
+  }
   else launch(k_dataflow<P, 256, BATCH>, 256);
   rec_end();
   SLT_CUDA(cudaGetLastError());

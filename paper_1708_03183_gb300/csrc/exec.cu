@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(128) k_phase(Params a) {
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
 #include "dataflow.cuh"
+#include "staged.cuh"
 
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every segment of the
 // sub-chain [first, last) in order, segments separated by a CTA barrier.
@@ -171,6 +172,7 @@ Params make_params(slt_mesh m) {
   a.fgeo = m->fgeo.p;
   a.mat = m->mat.p;
   a.nbr = m->nbr.p;
+  a.pre = m->pre.p;
   const int64_t Np = m->Np, n = m->ncp;
   double* base = m->work.p;
   a.buf[B_V] = base;
@@ -253,6 +255,57 @@ void run_dataflow_cluster(slt_schedule sched, Params a, int64_t nsteps, cudaStre
   dataflow_check(sched, s);
 }
 
+// executor 3: the staged dataflow executor, one CTA per SM (as many as the shared memory of the
+// largest tile footprint allows)
+template <int P, int BS>
+void launch_staged(slt_schedule sched, const Params& a, const DF& df, const StageArgs& g, cudaStream_t s) {
+  auto kernel = k_staged<P, BS>;
+  const int64_t bytes = stage_smem_bytes(P, g.cap);
+  SLT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  int dev = 0, nsm = 0, per = 0;
+  SLT_CUDA(cudaGetDevice(&dev));
+  SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, BS, (size_t)bytes));
+  if (per < 1) fail(SLT_ERR_UNSUPPORTED, "the staged executor's tile CTA does not fit on an SM");
+  const long long grid = std::min<long long>((long long)nsm * per, df.q.total);
+  sched->df.last_grid = grid;
+  g_rec.begin(0, s, 1);
+  kernel<<<(unsigned)grid, BS, (size_t)bytes, s>>>(a, df, g);
+  g_rec.end(s);
+  SLT_CUDA(cudaGetLastError());
+}
+
+template <int P>
+void run_staged(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
+  DF df;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, [&](int c, int n) { g_rec.begin(c, s, n); },
+                        [&] { g_rec.end(s); }))
+    return;
+  StageArgs g{};
+  int32_t cap = 4;
+  for (size_t k = 0; k < sched->subs.size(); ++k) {
+    const SubSched& sub = sched->subs[k];
+    cap = std::max(cap, sub.max_fp);
+    g.fp_ptr[k] = sub.fp_ptr.p;
+    g.fp_cell[k] = sub.fp_cell.p;
+    g.fp_nsl[k] = sub.fp_nsl.p;
+    for (int j = sub.first; j < sub.last; ++j) {
+      g.off[j] = sub.st_off[j - sub.first].p;
+      g.ent[j] = sub.st_ent[j - sub.first].p;
+    }
+  }
+  g.cap = (cap + 3) / 4 * 4;
+  g.cross = sched->stage_cross;
+  switch (sched->block) {
+    case 128: launch_staged<P, 128>(sched, a, df, g, s); break;
+    case 384: launch_staged<P, 384>(sched, a, df, g, s); break;
+    case 512: launch_staged<P, 512>(sched, a, df, g, s); break;
+    case 768: launch_staged<P, 768>(sched, a, df, g, s); break;
+    default: launch_staged<P, 256>(sched, a, df, g, s); break;
+  }
+  dataflow_check(sched, s);
+}
+
 // The untiled step as one CUDA graph (the 6 phase kernels and the step-counter increment), captured
 // on the mesh's private stream and launched nsteps times on s: the host issues one launch per
 // step instead of six.  The step index comes from a device counter the graph advances.
@@ -305,6 +358,10 @@ void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStr
     run_dataflow_cluster<P>(sched, a, nsteps, s);
     return;
   }
+  if (sched && sched->executor == 3) {
+    run_staged<P>(sched, a, nsteps, s);
+    return;
+  }
   if (!sched && nsteps >= kGraphMinSteps) {
     run_untiled_graph<P>(m, a, nsteps, s);
     return;
@@ -330,6 +387,36 @@ void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStr
 }  // namespace
 
 void upload_constants(const RefElem& r) { upload_ref(r); }
+
+namespace {
+// the expressions the parts evaluated per application, once per cell
+__global__ void k_build_pre(const double* __restrict__ geo, const double* __restrict__ fgeo,
+                            const double* __restrict__ mat, int64_t nc, int64_t n, double* __restrict__ pre) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const double ir = mat[c];
+    for (int k = 0; k < 4; ++k) pre[(PRE_RXR + k) * n + c] = geo[k * n + c] * ir;
+    for (int f = 0; f < 3; ++f) {
+      const double F = fgeo[(3 * f + 2) * n + c], fx = fgeo[(3 * f) * n + c], fy = fgeo[(3 * f + 1) * n + c];
+      const double sc = -0.5 * F * ir;
+      pre[(PRE_NB + 2 * f) * n + c] = sc * fx;
+      pre[(PRE_NB + 2 * f + 1) * n + c] = sc * fy;
+      const double h = -0.5 * F;
+      pre[(PRE_ND + 2 * f) * n + c] = h * fx;
+      pre[(PRE_ND + 2 * f + 1) * n + c] = h * fy;
+    }
+    pre[PRE_L2M * n + c] = fma(2.0, mat[2 * n + c], mat[n + c]);
+  }
+}
+}  // namespace
+
+void build_pre(slt_mesh m, cudaStream_t s) {
+  if (m->pre.n < (size_t)kPreRows * m->ncp) m->pre.alloc((size_t)kPreRows * m->ncp);
+  SLT_CUDA(cudaMemsetAsync(m->pre.p, 0, (size_t)kPreRows * m->ncp * sizeof(double), s));
+  int g;
+  io_grid(m->nc, g);
+  k_build_pre<<<g, 256, 0, s>>>(m->geo.p, m->fgeo.p, m->mat.p, m->nc, m->ncp, m->pre.p);
+  SLT_CUDA(cudaGetLastError());
+}
 
 void exec_steps_work(slt_mesh m, slt_schedule sched, const double* ricker, double dt, int64_t step0,
                      int64_t nsteps, cudaStream_t s) {
@@ -461,6 +548,7 @@ void group_build(slt_group grp) {
     for (size_t mi = 0; mi < part.members.size(); ++mi) {
       slt_schedule sc = grp->scheds[part.members[mi]];
       if (sc->block != part.block) fail(SLT_ERR_UNSUPPORTED, "tiled meshes of one degree need one block size");
+      if (sc->block > 384) fail(SLT_ERR_UNSUPPORTED, "group members take 128-384-thread tiles");
       part.wait_spins = std::max<int64_t>(part.wait_spins, sc->wait_spins);
       const DataflowPlan& D = sc->df;
       const int32_t G = D.cum.back();
@@ -526,6 +614,8 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
   q.tail = part.head.p + 1;
   q.err = part.err.p;
   q.max_spins = part.wait_spins;
+  q.g_lo = 0;
+  q.g_hi = q.G;
   df.K = part.K;
   df.cum = part.cum.p;
   df.first = part.first.p;

@@ -100,7 +100,67 @@ void run_batched(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaS
   }
 }
 
+template <int P>
+void part_b(slt_schedule sched, Params a, int part, cudaStream_t s) {
+  if (!sched) {
+    const unsigned blocks = (unsigned)((a.nc * a.S + 127) / 128);
+    if (part != 1) {
+      k_phase_b<P, 0><<<blocks, 128, 0, s>>>(a);
+      k_phase_b<P, 1><<<blocks, 128, 0, s>>>(a);
+      k_phase_b<P, 2><<<blocks, 128, 0, s>>>(a);
+    }
+    if (part != 0) {
+      k_phase_b<P, 3><<<blocks, 128, 0, s>>>(a);
+      k_phase_b<P, 4><<<blocks, 128, 0, s>>>(a);
+      k_phase_b<P, 5><<<blocks, 128, 0, s>>>(a);
+    }
+    SLT_CUDA(cudaGetLastError());
+    return;
+  }
+  const int32_t g = sched->shots_per_cta > 0 ? std::min(sched->shots_per_cta, a.S) : a.S;
+  for (int32_t s0 = 0; s0 < a.S; s0 += g) {
+    a.s0 = s0;
+    a.sg = std::min(g, a.S - s0);
+    launch_dataflow<P, true>(sched, a, 1, s, [](int, int) {}, [] {}, part == 2 ? -1 : part);
+  }
+}
+
 }  // namespace
+
+void chain_part_b(slt_mesh m, slt_schedule sched, const ChainRun& r, int part, cudaStream_t s) {
+  if (sched && part != 2) {
+    if (sched->executor != 0 || sched->subs.size() != 2 || sched->subs[0].last != 9)
+      fail(SLT_ERR_UNSUPPORTED, "a sub-chain at a time needs the {velocity, stress} fusion and the dataflow executor");
+  }
+  Params a{};
+  a.ncp = m->ncp;
+  a.nc = m->nc;
+  a.geo = m->geo.p;
+  a.fgeo = m->fgeo.p;
+  a.mat = m->mat.p;
+  a.nbr = m->nbr.p;
+  a.pre = m->pre.p;
+  for (int b = 0; b < 6; ++b) a.buf[b] = r.buf[b];
+  a.e5 = r.e5;
+  a.ricker = r.ricker;
+  a.src = nullptr;
+  a.src_w = -1;
+  a.dt = r.dt;
+  a.c24 = r.dt * r.dt / 24.0;
+  a.S = r.S;
+  a.s0 = 0;
+  a.sg = r.S;
+  a.fs = m->ncp * r.S;
+  a.src_wb = r.src_w;
+  a.src_b = r.src;
+  switch (m->p) {
+    case 1: part_b<1>(sched, a, part, s); break;
+    case 2: part_b<2>(sched, a, part, s); break;
+    case 3: part_b<3>(sched, a, part, s); break;
+    case 4: part_b<4>(sched, a, part, s); break;
+  }
+  if (sched) dataflow_check(sched, s);
+}
 
 void upload_constants_batched(const RefElem& r) { upload_ref(r); }
 
@@ -123,6 +183,7 @@ void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* 
   a.fgeo = m->fgeo.p;
   a.mat = m->mat.p;
   a.nbr = m->nbr.p;
+  a.pre = m->pre.p;
   a.buf[B_V] = base;
   a.buf[B_S] = base + 2 * Np * fs;
   a.buf[B_U1] = base + 5 * Np * fs;

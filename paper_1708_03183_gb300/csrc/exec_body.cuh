@@ -45,12 +45,20 @@ __device__ __forceinline__ double ld(const double* p) {
 // buffers of the work layout, each `rows` rows of fs doubles
 enum Buf { B_V = 0, B_S = 1, B_U1 = 2, B_U2 = 3, B_E = 4, B_S1 = 5 };
 
+// Per-cell products of geometry and material that every application of the operators would
+// otherwise recompute (rows of ncp, work order): the metric terms over rho (volume part of A),
+// the face normals scaled by -F / (2 rho) (interior facets of A; twice that on free-surface
+// facets) and by -F / 2 (interior facets of E), and lambda + 2 mu (Hooke's law).  Each is the
+// same expression the parts evaluated before, so the results do not change.
+constexpr int PRE_RXR = 0, PRE_NB = 4, PRE_ND = 10, PRE_L2M = 16, kPreRows = 17;
+
 struct Params {
   int64_t ncp, nc;
   const double* __restrict__ geo;   // [4][ncp]: rx ry sx sy
   const double* __restrict__ fgeo;  // [9][ncp]: nx ny F for faces 0, 1, 2
   const double* __restrict__ mat;   // [3][ncp]: 1/rho, lambda, mu
   const int32_t* __restrict__ nbr;  // [3][ncp]: (w_nb << 3) | (face_nb << 1) | flip, or -1
+  const double* __restrict__ pre;   // [kPreRows][ncp]: per-cell products hoisted out of the parts
   double* buf[6];
   const double* ricker;             // [nsteps] or null
   const double* src;                // [Np] source coefficients (one field)
@@ -66,6 +74,7 @@ struct Params {
   int64_t fs;                       // field row stride: ncp * S
   const int32_t* src_wb;            // [S] source cell of every shot
   const double* src_b;              // [S][Np] source coefficients of every shot
+  double* e5;                       // if set, phase 5 accumulates its strain here instead of buf[B_E]
 };
 
 // one (cell, shot) work item: c = cell work id, f = field column, s = shot
@@ -89,14 +98,19 @@ __device__ __forceinline__ int64_t ncol(const Params& a, int64_t wn, int s) {  /
 // consecutive loops of one cell (volume, then interior faces, then free-surface faces) before a
 // single store, in the order the loops would apply them one by one.
 
+// The parts work on field views: a field as rows of `fs` doubles, the cell's values in column w
+// (a neighbour's in column wn).  The views are global work buffers for the untiled, dataflow and
+// multi-shot executors and shared-memory slots for the staged executor, which therefore runs the
+// same arithmetic in the same order.  Per-cell data (geometry, material) comes from Params at
+// work id c.
+
 // volume part of A: u[comp * Np + i] = (div S)_i, the metric terms (rx .. sy) already over rho;
 // x row from (sxx, sxy), y row from (sxy, syy)
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const double* S, double* u, double rx,
-                                        double ry, double sx, double sy) {
+template <int P, bool CG>
+__device__ __forceinline__ void vol_div_v(const double* S, int64_t fs, int64_t w, double* u, double rx, double ry,
+                                          double sx, double sy) {
   constexpr int Np = np_of(P);
   const RefC& R = c_ref[P];
-  const int64_t fs = fstride<BATCH>(a), w = q.f;
 #pragma unroll
   for (int comp = 0; comp < 2; ++comp) {
     double A[Np], B[Np];
@@ -120,86 +134,76 @@ __device__ __forceinline__ void vol_div(const Params& a, const Pos& q, const dou
   }
 }
 
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void volB_part(const Params& a, const Pos& q, const double* S, double* u) {
-  const int64_t n = a.ncp, c = q.c;
-  double ir = a.mat[c];
-  vol_div<P, CG, BATCH>(a, q, S, u, a.geo[c] * ir, a.geo[n + c] * ir, a.geo[2 * n + c] * ir, a.geo[3 * n + c] * ir);
+template <int P, bool CG>
+__device__ __forceinline__ void volB_v(const Params& a, int64_t c, const double* S, int64_t fs, int64_t w,
+                                       double* u) {
+  const int64_t n = a.ncp;
+  vol_div_v<P, CG>(S, fs, w, u, a.pre[PRE_RXR * n + c], a.pre[(PRE_RXR + 1) * n + c], a.pre[(PRE_RXR + 2) * n + c],
+                   a.pre[(PRE_RXR + 3) * n + c]);
 }
 
-// interior faces of A (faces in mask): u += -(F/2 rho) Lift ((S - S_nb) n)
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void intB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
+// interior face f of A: u += -(F/2 rho) Lift_f ((S - S_nb) n); the neighbour's face fn, flip
+template <int P, bool CG>
+__device__ __forceinline__ void intB_face(const Params& a, int64_t c, int f, const double* S, int64_t fs, int64_t w,
+                                          int64_t wn, int fn, int flip, double* u) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  const double ir = a.mat[c];
+  const int64_t n = a.ncp;
+  const double nx = a.pre[(PRE_NB + 2 * f) * n + c], ny = a.pre[(PRE_NB + 2 * f + 1) * n + c];
+  double gx[Nfp], gy[Nfp];
 #pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    if (!((mask >> f) & 1)) continue;
-    const int32_t nb = a.nbr[f * n + c];
-    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
-    const int fn = (nb >> 1) & 3, flip = nb & 1;
-    const double sc = -0.5 * a.fgeo[(3 * f + 2) * n + c] * ir;
-    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
-    double gx[Nfp], gy[Nfp];
+  for (int k = 0; k < Nfp; ++k) {
+    const int i0 = fnode<P>(f, k);
+    const int i1 = fnode<P>(fn, flip ? P - k : k);
+    double dxx = ld<CG>(&S[(int64_t)i0 * fs + w]) - ld<CG>(&S[(int64_t)i1 * fs + wn]);
+    double dyy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(Np + i1) * fs + wn]);
+    double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * fs + wn]);
+    gx[k] = fma(dxy, ny, dxx * nx);
+    gy[k] = fma(dyy, ny, dxy * nx);
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i)
 #pragma unroll
     for (int k = 0; k < Nfp; ++k) {
-      const int i0 = fnode<P>(f, k);
-      const int i1 = fnode<P>(fn, flip ? P - k : k);
-      double dxx = ld<CG>(&S[(int64_t)i0 * fs + w]) - ld<CG>(&S[(int64_t)i1 * fs + wn]);
-      double dyy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(Np + i1) * fs + wn]);
-      double dxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]) - ld<CG>(&S[(int64_t)(2 * Np + i1) * fs + wn]);
-      gx[k] = fma(dxy, ny, dxx * nx);
-      gy[k] = fma(dyy, ny, dxy * nx);
+      u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
+      u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
     }
-#pragma unroll
-    for (int i = 0; i < Np; ++i)
-#pragma unroll
-      for (int k = 0; k < Nfp; ++k) {
-        u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
-        u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
-      }
-  }
 }
 
-// free-surface faces of A (faces in mask): u += -(F/rho) Lift (S n)
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void extB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
+// free-surface face f of A: u += -(F/rho) Lift_f (S n)
+template <int P, bool CG>
+__device__ __forceinline__ void extB_face(const Params& a, int64_t c, int f, const double* S, int64_t fs, int64_t w,
+                                          double* u) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
-  const double ir = a.mat[c];
+  const int64_t n = a.ncp;
+  // (-F / rho) n = 2 (-F / 2 rho) n exactly: scaling by 2 commutes with rounding
+  const double nx = 2.0 * a.pre[(PRE_NB + 2 * f) * n + c], ny = 2.0 * a.pre[(PRE_NB + 2 * f + 1) * n + c];
+  double gx[Nfp], gy[Nfp];
 #pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    if (!((mask >> f) & 1)) continue;
-    const double sc = -a.fgeo[(3 * f + 2) * n + c] * ir;
-    const double nx = sc * a.fgeo[(3 * f) * n + c], ny = sc * a.fgeo[(3 * f + 1) * n + c];
-    double gx[Nfp], gy[Nfp];
+  for (int k = 0; k < Nfp; ++k) {
+    const int i0 = fnode<P>(f, k);
+    double sxx = ld<CG>(&S[(int64_t)i0 * fs + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]),
+           sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]);
+    gx[k] = fma(sxy, ny, sxx * nx);
+    gy[k] = fma(syy, ny, sxy * nx);
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i)
 #pragma unroll
     for (int k = 0; k < Nfp; ++k) {
-      const int i0 = fnode<P>(f, k);
-      double sxx = ld<CG>(&S[(int64_t)i0 * fs + w]), syy = ld<CG>(&S[(int64_t)(Np + i0) * fs + w]),
-             sxy = ld<CG>(&S[(int64_t)(2 * Np + i0) * fs + w]);
-      gx[k] = fma(sxy, ny, sxx * nx);
-      gy[k] = fma(syy, ny, sxy * nx);
+      u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
+      u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
     }
-#pragma unroll
-    for (int i = 0; i < Np; ++i)
-#pragma unroll
-      for (int k = 0; k < Nfp; ++k) {
-        u[i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gx[k], u[i]);
-        u[Np + i] = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], gy[k], u[Np + i]);
-      }
-  }
 }
 
 // volume part of E: e = (dvx/dx, dvy/dy, dvx/dy + dvy/dx) at the nodes, e[comp * Np + i]
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void volD_part(const Params& a, const Pos& q, const double* V, double* e) {
+template <int P, bool CG>
+__device__ __forceinline__ void volD_v(const Params& a, int64_t c, const double* V, int64_t fs, int64_t w,
+                                       double* e) {
   constexpr int Np = np_of(P);
   const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const int64_t n = a.ncp;
   double rx = a.geo[c], ry = a.geo[n + c], sx = a.geo[2 * n + c], sy = a.geo[3 * n + c];
   double vx[Np], vy[Np];
 #pragma unroll
@@ -227,40 +231,71 @@ __device__ __forceinline__ void volD_part(const Params& a, const Pos& q, const d
   }
 }
 
-// interior faces of E (faces in mask): e += -(F/2) Lift sym((V - V_nb) (x) n)
-template <int P, bool CG, bool BATCH>
-__device__ __forceinline__ void intD_part(const Params& a, const Pos& q, int mask, const double* V, double* e) {
+// interior face f of E: e += -(F/2) Lift_f sym((V - V_nb) (x) n)
+template <int P, bool CG>
+__device__ __forceinline__ void intD_face(const Params& a, int64_t c, int f, const double* V, int64_t fs, int64_t w,
+                                          int64_t wn, int fn, int flip, double* e) {
   constexpr int Np = np_of(P), Nfp = P + 1;
   const RefC& R = c_ref[P];
-  const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
+  const int64_t n = a.ncp;
+  const double cx = a.pre[(PRE_ND + 2 * f) * n + c], cy = a.pre[(PRE_ND + 2 * f + 1) * n + c];
+  double dx[Nfp], dy[Nfp];
+#pragma unroll
+  for (int k = 0; k < Nfp; ++k) {
+    const int i0 = fnode<P>(f, k);
+    const int i1 = fnode<P>(fn, flip ? P - k : k);
+    dx[k] = ld<CG>(&V[(int64_t)i0 * fs + w]) - ld<CG>(&V[(int64_t)i1 * fs + wn]);
+    dy[k] = ld<CG>(&V[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&V[(int64_t)(Np + i1) * fs + wn]);
+  }
+#pragma unroll
+  for (int i = 0; i < Np; ++i) {
+    double lx = R.Lift[(f * MAXNP + i) * MAXNFP] * dx[0], ly = R.Lift[(f * MAXNP + i) * MAXNFP] * dy[0];
+#pragma unroll
+    for (int k = 1; k < Nfp; ++k) {
+      lx = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dx[k], lx);
+      ly = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dy[k], ly);
+    }
+    e[i] = fma(cx, lx, e[i]);
+    e[Np + i] = fma(cy, ly, e[Np + i]);
+    e[2 * Np + i] = fma(cy, lx, fma(cx, ly, e[2 * Np + i]));
+  }
+}
+
+// The same parts on the global work layout at work item q: every face of the mask in turn
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void volB_part(const Params& a, const Pos& q, const double* S, double* u) {
+  volB_v<P, CG>(a, q.c, S, fstride<BATCH>(a), q.f, u);
+}
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void intB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
+  const int64_t n = a.ncp, c = q.c;
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!((mask >> f) & 1)) continue;
     const int32_t nb = a.nbr[f * n + c];
-    const int64_t wn = ncol<BATCH>(a, nb >> 3, q.s);
-    const int fn = (nb >> 1) & 3, flip = nb & 1;
-    const double h = -0.5 * a.fgeo[(3 * f + 2) * n + c];
-    const double cx = h * a.fgeo[(3 * f) * n + c], cy = h * a.fgeo[(3 * f + 1) * n + c];
-    double dx[Nfp], dy[Nfp];
+    intB_face<P, CG>(a, c, f, S, fstride<BATCH>(a), q.f, ncol<BATCH>(a, nb >> 3, q.s), (nb >> 1) & 3, nb & 1, u);
+  }
+}
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void extB_part(const Params& a, const Pos& q, int mask, const double* S, double* u) {
 #pragma unroll
-    for (int k = 0; k < Nfp; ++k) {
-      const int i0 = fnode<P>(f, k);
-      const int i1 = fnode<P>(fn, flip ? P - k : k);
-      dx[k] = ld<CG>(&V[(int64_t)i0 * fs + w]) - ld<CG>(&V[(int64_t)i1 * fs + wn]);
-      dy[k] = ld<CG>(&V[(int64_t)(Np + i0) * fs + w]) - ld<CG>(&V[(int64_t)(Np + i1) * fs + wn]);
-    }
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    extB_face<P, CG>(a, q.c, f, S, fstride<BATCH>(a), q.f, u);
+  }
+}
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void volD_part(const Params& a, const Pos& q, const double* V, double* e) {
+  volD_v<P, CG>(a, q.c, V, fstride<BATCH>(a), q.f, e);
+}
+template <int P, bool CG, bool BATCH>
+__device__ __forceinline__ void intD_part(const Params& a, const Pos& q, int mask, const double* V, double* e) {
+  const int64_t n = a.ncp, c = q.c;
 #pragma unroll
-    for (int i = 0; i < Np; ++i) {
-      double lx = R.Lift[(f * MAXNP + i) * MAXNFP] * dx[0], ly = R.Lift[(f * MAXNP + i) * MAXNFP] * dy[0];
-#pragma unroll
-      for (int k = 1; k < Nfp; ++k) {
-        lx = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dx[k], lx);
-        ly = fma(R.Lift[(f * MAXNP + i) * MAXNFP + k], dy[k], ly);
-      }
-      e[i] = fma(cx, lx, e[i]);
-      e[Np + i] = fma(cy, ly, e[Np + i]);
-      e[2 * Np + i] = fma(cy, lx, fma(cx, ly, e[2 * Np + i]));
-    }
+  for (int f = 0; f < 3; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const int32_t nb = a.nbr[f * n + c];
+    intD_face<P, CG>(a, c, f, V, fstride<BATCH>(a), q.f, ncol<BATCH>(a, nb >> 3, q.s), (nb >> 1) & 3, nb & 1, e);
   }
 }
 
@@ -311,7 +346,7 @@ __device__ __forceinline__ void segEB(const Params& a, const Pos& q, bool pa, bo
   if (!pb) return;
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
   const double lam = a.mat[n + c], mu = a.mat[2 * n + c];
-  const double l2m = fma(2.0, mu, lam);
+  const double l2m = a.pre[PRE_L2M * n + c];
 #pragma unroll
   for (int j = 0; j < Np; ++j) {
     S1[(int64_t)j * fs + w] = fma(lam, e[Np + j], l2m * e[j]);
@@ -352,17 +387,18 @@ template <int P, bool CG, bool BATCH>
 __device__ __forceinline__ void segES(const Params& a, const Pos& q, bool pa, bool pb, int imask, int64_t step) {
   constexpr int Np = np_of(P);
   double* const* b = a.buf;
+  double* const E = a.e5 ? a.e5 : b[B_E];
   double e[3 * Np];
   if (pa) volD_part<P, CG, BATCH>(a, q, b[B_U1], e);
-  else load_rows<3 * Np, CG, BATCH>(a, q, b[B_E], e);
+  else load_rows<3 * Np, CG, BATCH>(a, q, E, e);
   intD_part<P, CG, BATCH>(a, q, imask, b[B_U1], e);
-  if (pa || imask) store_rows<3 * Np, BATCH>(a, q, b[B_E], e);
+  if (pa || imask) store_rows<3 * Np, BATCH>(a, q, E, e);
   if (!pb) return;
   const int64_t n = a.ncp, c = q.c, fs = fstride<BATCH>(a), w = q.f;
   double* S = b[B_S];
   const double* S1 = b[B_S1];
   const double lam = a.mat[n + c], mu = a.mat[2 * n + c];
-  const double l2m = fma(2.0, mu, lam);
+  const double l2m = a.pre[PRE_L2M * n + c];
   int32_t sw;
   const double* sv;
   if constexpr (BATCH) {

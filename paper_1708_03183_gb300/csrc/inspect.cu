@@ -739,6 +739,14 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
         if (L.descs[d].map >= 0) export_local_map(X, L.descs[d].map, sub.sigma[jj].p, n, m, sub.lmaps[jj][d]);
     }
     if (c->mesh) build_plan(out, c->mesh, sub, s);
+    if (c->mesh && out->executor == 3) {
+      stage_build(out, c->mesh, sub, s);
+      const int32_t cap = stage_capacity(c->mesh->p);
+      if (sub.max_fp > cap)
+        fail(SLT_ERR_UNSUPPORTED, "staged executor: a tile touches " + std::to_string(sub.max_fp) +
+                                      " cells, more than the " + std::to_string(cap) +
+                                      " its shared memory holds at this degree; use a smaller tile size");
+    }
   }
   if (c->mesh) build_dataflow(out, c->mesh, s);
 }
@@ -781,99 +789,463 @@ void critical_path(DataflowPlan& D, const std::vector<std::vector<int32_t>>& dep
 }
 
 // Dependencies between tiles for the dataflow executor, from the cells each tile touches in
-// each sub-chain (its plan items; both cells of an interior facet are items of the facet's tile): inside a sub-chain, a tile waits for the lower-colour tiles
-// that touch one of its cells; across sub-chains, for the tiles of the previous sub-chain (in
-// chain order, wrapping to the previous step) that touched the same cell.  Every access to a
-// cell is thereby ordered as in the untiled chain.
+// each sub-chain (its plan items; both cells of an interior facet are items of the facet's tile):
+// inside a sub-chain, a tile waits for the lower-colour tiles that touch one of its cells; across
+// sub-chains, for the tiles of the previous sub-chain (in chain order, wrapping to the previous
+// step) that touched the same cell.  Every access to a cell is thereby ordered as in the untiled
+// chain.  Built on the device: per sub-chain the sorted, de-duplicated (cell, tile) pairs of the
+// plan items give each cell's touching tiles; one pass counts each cell's edges, a scan places
+// them, a second pass emits (dependency, node << 1 | previous step) pairs, and a sort removes the
+// duplicates and leaves the successor lists in CSR order.
+namespace {
+
+constexpr int kMaxSub = 16;
+struct TouchTables {
+  const int32_t* ptr[kMaxSub];     // [nc + 1] per sub-chain
+  const int32_t* tile[kMaxSub];    // tiles touching each cell, ascending
+  const int32_t* colour[kMaxSub];  // colour of each tile
+  int32_t cum[kMaxSub + 1];        // global tile id base
+  int32_t K;
+};
+
+// (cell, tile) of every plan item of one segment: one thread per tile
+__global__ void k_plan_pairs(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items, int32_t m,
+                             uint32_t* __restrict__ cell, uint32_t* __restrict__ tile) {
+  GRID_STRIDE(t, m) {
+    for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
+      cell[i] = (uint32_t)(items[i] >> 5);
+      tile[i] = (uint32_t)t;
+    }
+  }
+}
+
+// the dependency edges of cell w: count (out == nullptr) or emit at pos
+template <bool EMIT>
+__device__ __forceinline__ int32_t cell_edges(const TouchTables& T, int64_t w, uint32_t* src, uint32_t* dst,
+                                              int64_t pos) {
+  int32_t n = 0;
+  int first = -1, last = -1;
+  for (int k = 0; k < T.K; ++k)
+    if (T.ptr[k][w + 1] > T.ptr[k][w]) {
+      if (first < 0) first = k;
+      last = k;
+    }
+  int prev = last;  // the previous touching sub-chain, wrapping to the last one of the previous step
+  for (int k = first; k >= 0 && k < T.K; ++k) {
+    const int32_t b0 = T.ptr[k][w], b1 = T.ptr[k][w + 1];
+    if (b1 == b0) continue;
+    const uint32_t wrap = k == first ? 1u : 0u;
+    const int32_t p0 = T.ptr[prev][w], p1 = T.ptr[prev][w + 1];
+    for (int32_t x = b0; x < b1; ++x) {
+      const int32_t tb = T.tile[k][x], gb = T.cum[k] + tb;
+      const int32_t cb = T.colour[k][tb];
+      for (int32_t y = b0; y < b1; ++y) {
+        const int32_t ta = T.tile[k][y];
+        if (T.colour[k][ta] < cb) {
+          if (EMIT) {
+            src[pos + n] = (uint32_t)(T.cum[k] + ta);
+            dst[pos + n] = ((uint32_t)gb << 1);
+          }
+          ++n;
+        }
+      }
+      for (int32_t y = p0; y < p1; ++y) {
+        if (EMIT) {
+          src[pos + n] = (uint32_t)(T.cum[prev] + T.tile[prev][y]);
+          dst[pos + n] = ((uint32_t)gb << 1) | wrap;
+        }
+        ++n;
+      }
+    }
+    prev = k;
+  }
+  return n;
+}
+__global__ void k_edge_count(TouchTables T, int64_t nc, int32_t* __restrict__ cnt) {
+  GRID_STRIDE(w, nc) cnt[w] = cell_edges<false>(T, w, nullptr, nullptr, 0);
+}
+__global__ void k_edge_emit(TouchTables T, int64_t nc, const int32_t* __restrict__ pos, uint32_t* __restrict__ src,
+                            uint32_t* __restrict__ dst) {
+  GRID_STRIDE(w, nc) cell_edges<true>(T, w, src, dst, pos[w]);
+}
+// in-degrees: every distinct edge once; the ones from the same step also count for the first step
+__global__ void k_indeg(const uint32_t* __restrict__ dst, int64_t n, int32_t* __restrict__ indeg0,
+                        int32_t* __restrict__ indeg) {
+  GRID_STRIDE(e, n) {
+    const uint32_t d = dst[e];
+    atomicAdd(&indeg[d >> 1], 1);
+    if (!(d & 1)) atomicAdd(&indeg0[d >> 1], 1);
+  }
+}
+
+// sort (a, b) pairs by a then b, drop repeats; returns the count (pairs compacted in place)
+int64_t sort_unique_pairs(DevBuf<uint32_t>& a, int abits, DevBuf<uint32_t>& b, int bbits, int64_t n, cudaStream_t s) {
+  if (n == 0) return 0;
+  DevBuf<uint32_t> order;
+  sort_by_two(a, abits, b, bbits, n, order, s);  // a sorted in place
+  DevBuf<uint32_t> sb(n);
+  k_gather_div<<<grid_for(n), 256, 0, s>>>((const int32_t*)b.p, order.p, n, 1, sb.p);
+  DevBuf<int32_t> flag(n), pos(n + 1);
+  k_run_heads<<<grid_for(n), 256, 0, s>>>(a.p, sb.p, n, flag.p);
+  exclusive_scan_i32(flag.p, pos.p, n, s);
+  int32_t nu = 0;
+  SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + n, 4, cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  DevBuf<uint32_t> ua(std::max(nu, 1)), ub(std::max(nu, 1));
+  k_compact2<<<grid_for(n), 256, 0, s>>>(a.p, sb.p, flag.p, pos.p, n, ua.p, (int32_t*)ub.p);
+  SLT_CUDA(cudaGetLastError());
+  a = std::move(ua);
+  b = std::move(ub);
+  return nu;
+}
+
+}  // namespace
+
 void build_dataflow(slt_schedule sched, slt_mesh mesh, cudaStream_t s) {
   DataflowPlan& D = sched->df;
   const int K = (int)sched->subs.size();
+  if (K > kMaxSub) fail(SLT_ERR_UNSUPPORTED, "more than 16 sub-chains");
   const int64_t nc = mesh->nc;
-  constexpr int CAP = 16;
   D.cum.assign(K + 1, 0);
   for (int k = 0; k < K; ++k) D.cum[k + 1] = D.cum[k] + sched->subs[k].m;
   const int32_t G = D.cum[K];
-  std::vector<int32_t> colour(G);
-  std::vector<std::vector<int32_t>> touch(K, std::vector<int32_t>(nc * CAP));
-  std::vector<std::vector<uint8_t>> ntouch(K, std::vector<uint8_t>(nc, 0));
+  TouchTables T{};
+  T.K = K;
+  std::vector<DevBuf<int32_t>> tptr(K), ttile(K);
   std::vector<double> items_of(G, 0.0);  // plan items of each node
   for (int k = 0; k < K; ++k) {
     SubSched& sub = sched->subs[k];
-    std::vector<int32_t> col = sub.colour.download(s, sub.m);
-    for (int32_t i = 0; i < sub.m; ++i) colour[D.cum[k] + i] = col[i];
+    T.cum[k] = D.cum[k];
+    T.colour[k] = sub.colour.p;
+    // (cell, tile) pairs of every segment's items
+    std::vector<int32_t> seg_n;
+    int64_t n = 0;
     for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+      std::vector<int32_t> ptr = sub.plan_ptr[J0 - sub.first].download(s, sub.m + 1);
+      for (int32_t t = 0; t < sub.m; ++t) items_of[D.cum[k] + t] += ptr[t + 1] - ptr[t];
+      seg_n.push_back(ptr[sub.m]);
+      n += ptr[sub.m];
+    }
+    DevBuf<uint32_t> cell(std::max<int64_t>(n, 1)), tile(std::max<int64_t>(n, 1));
+    int64_t o = 0, si = 0;
+    for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last), ++si) {
       const int jj = J0 - sub.first;
-      std::vector<int32_t> ptr = sub.plan_ptr[jj].download(s, sub.m + 1);
-      std::vector<int32_t> items = sub.plan_items[jj].download(s, std::max(ptr[sub.m], 1));
-      for (int32_t t = 0; t < sub.m; ++t) {
-        items_of[D.cum[k] + t] += ptr[t + 1] - ptr[t];
-        for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
-          const int64_t w = items[i] >> 5;
-          int32_t* T = &touch[k][w * CAP];
-          uint8_t& n = ntouch[k][w];
-          bool have = false;
-          for (int q = 0; q < n; ++q) have |= T[q] == t;
-          if (have) continue;
-          if (n == CAP) fail(SLT_ERR_UNSUPPORTED, "a cell is touched by more than 16 tiles of one sub-chain");
-          T[n++] = t;
-        }
-      }
+      if (seg_n[si]) k_plan_pairs<<<grid_for(sub.m), 256, 0, s>>>(sub.plan_ptr[jj].p, sub.plan_items[jj].p, sub.m,
+                                                                  cell.p + o, tile.p + o);
+      o += seg_n[si];
     }
+    SLT_CUDA(cudaGetLastError());
+    const int64_t nu = sort_unique_pairs(cell, bits_for(std::max<int64_t>(nc - 1, 1)), tile,
+                                         bits_for(std::max(sub.m - 1, 1)), n, s);
+    tptr[k].alloc(nc + 1);
+    lower_bound_offsets(cell.p, nu, nc, tptr[k].p, s);
+    ttile[k].alloc(std::max<int64_t>(nu, 1));
+    if (nu) SLT_CUDA(cudaMemcpyAsync(ttile[k].p, tile.p, nu * 4, cudaMemcpyDeviceToDevice, s));
+    T.ptr[k] = tptr[k].p;
+    T.tile[k] = ttile[k].p;
   }
-  std::vector<std::vector<int32_t>> deps(G);
-  auto push = [&](int32_t g, int32_t e) {
-    if (deps[g].empty() || deps[g].back() != e) deps[g].push_back(e);
-  };
-  std::vector<int> seq;
-  for (int64_t w = 0; w < nc; ++w) {
-    seq.clear();
-    for (int k = 0; k < K; ++k) if (ntouch[k][w]) seq.push_back(k);
-    for (size_t i = 0; i < seq.size(); ++i) {
-      const int k = seq[i];
-      const int prev = i ? seq[i - 1] : seq.back();
-      const int wrap = i ? 0 : 1;
-      const int32_t* T = &touch[k][w * CAP];
-      const int32_t* Tp = &touch[prev][w * CAP];
-      for (int x = 0; x < ntouch[k][w]; ++x) {
-        const int32_t gb = D.cum[k] + T[x];
-        for (int y = 0; y < ntouch[k][w]; ++y) {
-          const int32_t ga = D.cum[k] + T[y];
-          if (colour[ga] < colour[gb]) push(gb, ga << 1);
-        }
-        for (int y = 0; y < ntouch[prev][w]; ++y) push(gb, ((D.cum[prev] + Tp[y]) << 1) | wrap);
-      }
-    }
-  }
-  // successors (dependency edges reversed) and in-degrees of first-step and later nodes
-  std::vector<std::vector<int32_t>> succ(G);
-  std::vector<int32_t> indeg0(G, 0), indeg(G, 0);
-  for (int32_t g = 0; g < G; ++g) {
-    std::sort(deps[g].begin(), deps[g].end());
-    deps[g].erase(std::unique(deps[g].begin(), deps[g].end()), deps[g].end());
-    for (int32_t e : deps[g]) {
-      succ[e >> 1].push_back((g << 1) | (e & 1));
-      indeg[g] += 1;
-      indeg0[g] += (e & 1) ? 0 : 1;
-    }
-    D.ndeps += (int64_t)deps[g].size();
-  }
-  critical_path(D, deps, colour, items_of);
-  std::vector<int32_t> ptr(G + 1, 0), flat;
-  for (int32_t g = 0; g < G; ++g) {
-    ptr[g + 1] = ptr[g] + (int32_t)succ[g].size();
-    flat.insert(flat.end(), succ[g].begin(), succ[g].end());
-  }
+  T.cum[K] = D.cum[K];
+  // edges: count per cell, place, emit; then distinct (dependency, node code) pairs in order
+  DevBuf<int32_t> cnt(nc), pos(nc + 1);
+  k_edge_count<<<grid_for(nc), 256, 0, s>>>(T, nc, cnt.p);
+  exclusive_scan_i32(cnt.p, pos.p, nc, s);
+  int32_t ne = 0;
+  SLT_CUDA(cudaMemcpyAsync(&ne, pos.p + nc, 4, cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  DevBuf<uint32_t> esrc(std::max(ne, 1)), edst(std::max(ne, 1));
+  if (ne) k_edge_emit<<<grid_for(nc), 256, 0, s>>>(T, nc, pos.p, esrc.p, edst.p);
+  SLT_CUDA(cudaGetLastError());
+  const int64_t nd = sort_unique_pairs(esrc, bits_for(std::max(G - 1, 1)), edst,
+                                       bits_for(std::max<int64_t>(2 * (int64_t)G - 1, 1)), ne, s);
+  D.ndeps = nd;
   D.succ_ptr.alloc(G + 1);
-  D.succ_ptr.upload(ptr.data(), G + 1, s);
-  D.succ.alloc(std::max<size_t>(flat.size(), 1));
-  D.succ.upload(flat.data(), flat.size(), s);
+  lower_bound_offsets(esrc.p, nd, G, D.succ_ptr.p, s);
+  D.succ.alloc(std::max<int64_t>(nd, 1));
+  if (nd) SLT_CUDA(cudaMemcpyAsync(D.succ.p, edst.p, nd * 4, cudaMemcpyDeviceToDevice, s));
   D.indeg0.alloc(G);
-  D.indeg0.upload(indeg0.data(), G, s);
   D.indeg.alloc(G);
-  D.indeg.upload(indeg.data(), G, s);
+  SLT_CUDA(cudaMemsetAsync(D.indeg0.p, 0, G * 4, s));
+  SLT_CUDA(cudaMemsetAsync(D.indeg.p, 0, G * 4, s));
+  if (nd) k_indeg<<<grid_for(nd), 256, 0, s>>>(edst.p, nd, D.indeg0.p, D.indeg.p);
+  SLT_CUDA(cudaGetLastError());
   D.err.alloc(1);
   D.head.alloc(2);
+  // the longest chain per step, on the host over the (small) graph
+  std::vector<int32_t> sp = D.succ_ptr.download(s, G + 1);
+  std::vector<int32_t> sv = D.succ.download(s, std::max<int64_t>(nd, 1));
+  std::vector<std::vector<int32_t>> deps(G);
+  std::vector<int32_t> sub_of(G), indeg_sub(G, 0);
+  for (int k = 0; k < K; ++k)
+    for (int32_t g = D.cum[k]; g < D.cum[k + 1]; ++g) sub_of[g] = k;
+  for (int32_t g = 0; g < G; ++g)
+    for (int32_t i = sp[g]; i < sp[g + 1]; ++i) {
+      deps[sv[i] >> 1].push_back((g << 1) | (sv[i] & 1));
+      if (!(sv[i] & 1) && sub_of[sv[i] >> 1] == sub_of[g]) ++indeg_sub[sv[i] >> 1];
+    }
+  D.indeg_sub.alloc(std::max(G, 1));
+  D.indeg_sub.upload(indeg_sub.data(), G, s);
+  std::vector<int32_t> colour(G);
+  for (int k = 0; k < K; ++k) {
+    std::vector<int32_t> col = sched->subs[k].colour.download(s, sched->subs[k].m);
+    for (int32_t i = 0; i < sched->subs[k].m; ++i) colour[D.cum[k] + i] = col[i];
+  }
+  critical_path(D, deps, colour, items_of);
   SLT_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ staged executor plan
+// The staged executor (executor 3) runs one tile's sub-chain out of shared memory.  Its plan:
+//   footprint   the cells the tile's segments touch (items of any segment), ascending work id; a
+//               cell's slot is its position.  This is the tile's local map of the cell set
+//               (Algorithm 1, compute_local_maps) for every loop of the sub-chain at once.  Each
+//               entry carries a "shared" bit (another tile of the sub-chain touches the cell, so
+//               values the tile writes for it go out to global memory) and the slots of the
+//               cell's three face neighbours (kNoSlot: free surface, kNoSlot - 1: not in the
+//               footprint).
+//   lists       per segment and tile, seven lists of slot entries run as passes separated by a
+//               barrier: gather (inputs read by the segment that no earlier segment of the tile
+//               left in shared memory: slot | kind << 11, kind 0 the segment's operand, kind 1 the
+//               later cell loop's own extra operand), init (the first cell loop, or the stored
+//               partial value), interior faces 0, 1, 2, free-surface faces, later cell loop
+//               (slot | flags << 11).  A cell's operations keep the order of the loop-by-loop chain.
+// Residency of the temporaries, tracked per slot across the tile's segments (bits):
+constexpr uint8_t RB_U1A = 1, RB_S1A = 2, RB_U2 = 4, RB_S1B = 8, RB_U1B = 16;
+namespace {
+
+__device__ __forceinline__ int32_t fp_find(const int32_t* __restrict__ fp, int32_t lo, int32_t hi, int32_t w) {
+  int32_t a = lo, b = hi;  // first position with (fp & mask) >= w
+  while (a < b) {
+    const int32_t mid = (a + b) >> 1;
+    if ((fp[mid] & 0x7fffffff) < w) a = mid + 1;
+    else b = mid;
+  }
+  return (a < hi && (fp[a] & 0x7fffffff) == w) ? a - lo : -1;
+}
+__global__ void k_cell_count(const uint32_t* __restrict__ cell, int64_t n, int32_t* __restrict__ cnt) {
+  GRID_STRIDE(e, n) atomicAdd(&cnt[cell[e]], 1);
+}
+// footprint entries: work id | shared << 31, neighbour slots (11 bits per face)
+__global__ void k_fp_info(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ cell, int64_t n,
+                          const int32_t* __restrict__ cnt, const int32_t* __restrict__ fp_ptr,
+                          const int32_t* __restrict__ nbr, int64_t ncp, int32_t* __restrict__ fp_cell,
+                          int32_t* __restrict__ fp_nsl) {
+  GRID_STRIDE(e, n) fp_cell[e] = (int32_t)cell[e] | (cnt[cell[e]] > 1 ? (int32_t)0x80000000 : 0);
+}
+__global__ void k_fp_nsl(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ cell, int64_t n,
+                         const int32_t* __restrict__ fp_ptr, const int32_t* __restrict__ fp_cell,
+                         const int32_t* __restrict__ nbr, int64_t ncp, int32_t* __restrict__ fp_nsl) {
+  GRID_STRIDE(e, n) {
+    const int32_t t = (int32_t)tile[e], w = (int32_t)cell[e];
+    int32_t packed = 0;
+    for (int f = 0; f < 3; ++f) {
+      const int32_t nb = nbr[f * ncp + w];
+      int32_t sl = kNoSlot;
+      if (nb >= 0) {
+        sl = fp_find(fp_cell, fp_ptr[t], fp_ptr[t + 1], nb >> 3);
+        if (sl < 0) sl = kNoSlot - 1;
+      }
+      packed |= sl << (kSlotBits * f);
+    }
+    fp_nsl[e] = packed;
+  }
+}
+// the segment's items as flags per footprint slot (| 64: the slot is an item)
+__global__ void k_item_flags(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items, int32_t m,
+                             const int32_t* __restrict__ fp_ptr, const int32_t* __restrict__ fp_cell,
+                             uint8_t* __restrict__ iflag) {
+  GRID_STRIDE(t, m) {
+    for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) {
+      const int32_t sl = fp_find(fp_cell, fp_ptr[t], fp_ptr[t + 1], items[i] >> 5);
+      if (sl >= 0) iflag[fp_ptr[t] + sl] = (uint8_t)((items[i] & 31) | 64);
+    }
+  }
+}
+
+// One tile per thread, slots ascending.  COUNT: need bits and list lengths; otherwise emit the
+// lists at off and update the residency bits.
+struct StageSeg {
+  int H;            // phase
+  uint8_t in_rb;    // residency bit of the segment's operand (0: never resident)
+  uint8_t x_rb;     // residency bit of the later cell loop's extra operand (0: none)
+  bool has_x;       // the later cell loop reads its own extra operand (phases 2, 5)
+  uint8_t set_all;  // residency bits every item leaves
+  uint8_t set_pb;   // residency bits the later cell loop leaves
+  uint8_t acc_rb;   // residency bit of the accumulated value (phases 2, 4; else the first cell loop)
+};
+template <bool COUNT>
+__global__ void k_stage_lists(StageSeg sg, int32_t m, const int32_t* __restrict__ fp_ptr,
+                              const int32_t* __restrict__ fp_nsl, const uint8_t* __restrict__ iflag,
+                              uint8_t* __restrict__ need, uint8_t* __restrict__ res, int32_t* __restrict__ cnt,
+                              const int32_t* __restrict__ off, int32_t* __restrict__ ent, int32_t* __restrict__ bad) {
+  GRID_STRIDE(t, m) {
+    const int32_t b = fp_ptr[t], nF = fp_ptr[t + 1] - b;
+    int32_t c[SL_N] = {0, 0, 0, 0, 0, 0, 0};
+    int32_t o[SL_N];
+    if (!COUNT)
+      for (int L = 0; L < SL_N; ++L) o[L] = off[t * SL_N + L];
+    if (COUNT) {
+      for (int32_t sl = 0; sl < nF; ++sl) need[b + sl] = 0;
+      for (int32_t sl = 0; sl < nF; ++sl) {
+        const int fl = iflag[b + sl];
+        if (!(fl & 64)) continue;
+        const int32_t ns = fp_nsl[b + sl];
+        if ((fl & 8) || (fl & 7)) need[b + sl] |= 1;
+        for (int f = 0; f < 3; ++f) {
+          const int32_t nsf = (ns >> (kSlotBits * f)) & kNoSlot;
+          if (((fl >> f) & 1) && nsf < kNoSlot - 1) need[b + nsf] |= 1;
+          if (((fl >> f) & 1) && nsf == kNoSlot - 1) atomicAdd(bad, 1);  // a facet with one cell outside
+        }
+        if (sg.has_x && (fl & 16)) need[b + sl] |= 2;
+      }
+    }
+    auto put = [&](int L, int32_t v) {
+      if (COUNT) ++c[L];
+      else ent[o[L]++] = v;
+    };
+    // gather: operands read here that no earlier segment of the tile left in shared memory
+    for (int32_t sl = 0; sl < nF; ++sl) {
+      const uint8_t nd = need[b + sl], r = res[b + sl];
+      if ((nd & 1) && !(sg.in_rb && (r & sg.in_rb))) put(SL_GATHER, sl);
+      if ((nd & 2) && !(sg.x_rb && (r & sg.x_rb))) put(SL_GATHER, sl | (1 << kSlotBits));
+    }
+    // init: first cell loop items first, then the others (partial values, or already resident)
+    for (int pass = 0; pass < 2; ++pass)
+      for (int32_t sl = 0; sl < nF; ++sl) {
+        int fl = iflag[b + sl];
+        if (!(fl & 64) || (((fl & 8) != 0) != (pass == 0))) continue;
+        fl &= 31;
+        const bool load = (sg.acc_rb ? !(res[b + sl] & sg.acc_rb) : !(fl & 8));
+        put(SL_INIT, sl | ((fl | (load ? kLoadBit : 0)) << kSlotBits));
+      }
+    for (int f = 0; f < 3; ++f)
+      for (int32_t sl = 0; sl < nF; ++sl) {
+        const int fl = iflag[b + sl];
+        const int32_t nsf = (fp_nsl[b + sl] >> (kSlotBits * f)) & kNoSlot;
+        if ((fl & 64) && ((fl >> f) & 1) && nsf != kNoSlot) put(SL_INT0 + f, sl | ((fl & 31) << kSlotBits));
+      }
+    for (int32_t sl = 0; sl < nF; ++sl) {
+      const int fl = iflag[b + sl];
+      if (!(fl & 64)) continue;
+      bool ext = false;
+      for (int f = 0; f < 3; ++f)
+        ext |= ((fl >> f) & 1) && (((fp_nsl[b + sl] >> (kSlotBits * f)) & kNoSlot) == kNoSlot);
+      if (ext) put(SL_EXT, sl | ((fl & 31) << kSlotBits));
+    }
+    for (int32_t sl = 0; sl < nF; ++sl) {
+      const int fl = iflag[b + sl];
+      if ((fl & 64) && (fl & 16)) put(SL_PB, sl | ((fl & 31) << kSlotBits));
+    }
+    if (COUNT) {
+      for (int L = 0; L < SL_N; ++L) cnt[t * SL_N + L] = c[L];
+    } else {
+      for (int32_t sl = 0; sl < nF; ++sl) {
+        const int fl = iflag[b + sl];
+        if (!(fl & 64)) continue;
+        res[b + sl] |= sg.set_all | ((fl & 16) ? sg.set_pb : 0);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int32_t stage_capacity(int p) {
+  int dev = 0, smem = 0;
+  SLT_CUDA(cudaGetDevice(&dev));
+  SLT_CUDA(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int Np = (p + 1) * (p + 2) / 2;
+  // regions of 8 Np doubles per slot plus two int32 per slot; 1 KB for the kernel's own variables
+  const int64_t per = 64 * (int64_t)Np + 8;
+  return (int32_t)(std::min<int64_t>(kNoSlot - 1, (smem - 1024) / per) / 4 * 4);  // the kernel pads to 4
+}
+
+void stage_build(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s) {
+  const int32_t m = sub.m;
+  const int64_t nc = mesh->nc;
+  std::vector<int32_t> seg_n;
+  int64_t n = 0;
+  for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+    int32_t tot = 0;
+    SLT_CUDA(cudaMemcpyAsync(&tot, sub.plan_ptr[J0 - sub.first].p + m, 4, cudaMemcpyDeviceToHost, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    seg_n.push_back(tot);
+    n += tot;
+  }
+  DevBuf<uint32_t> cell(std::max<int64_t>(n, 1)), tile(std::max<int64_t>(n, 1));
+  {
+    int64_t o = 0, si = 0;
+    for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last), ++si) {
+      const int jj = J0 - sub.first;
+      if (seg_n[si]) k_plan_pairs<<<grid_for(m), 256, 0, s>>>(sub.plan_ptr[jj].p, sub.plan_items[jj].p, m,
+                                                              cell.p + o, tile.p + o);
+      o += seg_n[si];
+    }
+  }
+  const int64_t nu = sort_unique_pairs(tile, bits_for(std::max(m - 1, 1)), cell,
+                                       bits_for(std::max<int64_t>(nc - 1, 1)), n, s);
+  sub.fp_ptr.alloc(m + 1);
+  lower_bound_offsets(tile.p, nu, m, sub.fp_ptr.p, s);
+  sub.fp_cell.alloc(std::max<int64_t>(nu, 1));
+  sub.fp_nsl.alloc(std::max<int64_t>(nu, 1));
+  {
+    DevBuf<int32_t> cnt(nc);
+    SLT_CUDA(cudaMemsetAsync(cnt.p, 0, nc * 4, s));
+    if (nu) {
+      k_cell_count<<<grid_for(nu), 256, 0, s>>>(cell.p, nu, cnt.p);
+      k_fp_info<<<grid_for(nu), 256, 0, s>>>(tile.p, cell.p, nu, cnt.p, sub.fp_ptr.p, mesh->nbr.p, mesh->ncp,
+                                             sub.fp_cell.p, sub.fp_nsl.p);
+      k_fp_nsl<<<grid_for(nu), 256, 0, s>>>(tile.p, cell.p, nu, sub.fp_ptr.p, sub.fp_cell.p, mesh->nbr.p, mesh->ncp,
+                                            sub.fp_nsl.p);
+    }
+    SLT_CUDA(cudaGetLastError());
+    SLT_CUDA(cudaStreamSynchronize(s));
+  }
+  {
+    std::vector<int32_t> fp = sub.fp_ptr.download(s, m + 1);
+    sub.max_fp = 0;
+    for (int32_t t = 0; t < m; ++t) sub.max_fp = std::max(sub.max_fp, fp[t + 1] - fp[t]);
+  }
+  const int nl = sub.last - sub.first;
+  sub.st_off.clear();
+  sub.st_ent.clear();
+  sub.st_off.resize(nl);
+  sub.st_ent.resize(nl);
+  DevBuf<uint8_t> res(std::max<int64_t>(nu, 1)), need(std::max<int64_t>(nu, 1)), iflag(std::max<int64_t>(nu, 1));
+  SLT_CUDA(cudaMemsetAsync(res.p, 0, std::max<int64_t>(nu, 1), s));
+  DevBuf<int32_t> cnt((size_t)m * SL_N), bad(1);
+  SLT_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
+  for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+    const int jj = J0 - sub.first;
+    const int H = phase_of(J0);
+    StageSeg sg{};
+    sg.H = H;
+    switch (H) {
+      case 0: sg.in_rb = 0; sg.set_all = RB_U1A; break;
+      case 1: sg.in_rb = RB_U1A; sg.set_pb = RB_S1A | RB_U2; break;
+      case 2: sg.in_rb = RB_S1A; sg.has_x = true; sg.x_rb = RB_U1A; sg.acc_rb = RB_U2; break;
+      case 3: sg.in_rb = 0; sg.set_pb = RB_S1B | RB_U1B; break;
+      case 4: sg.in_rb = RB_S1B; sg.acc_rb = RB_U1B; sg.set_all = RB_U1B; break;
+      default: sg.in_rb = RB_U1B; sg.has_x = true; sg.x_rb = RB_S1B; break;
+    }
+    SLT_CUDA(cudaMemsetAsync(iflag.p, 0, std::max<int64_t>(nu, 1), s));
+    k_item_flags<<<grid_for(m), 256, 0, s>>>(sub.plan_ptr[jj].p, sub.plan_items[jj].p, m, sub.fp_ptr.p,
+                                             sub.fp_cell.p, iflag.p);
+    k_stage_lists<true><<<grid_for(m, 64), 64, 0, s>>>(sg, m, sub.fp_ptr.p, sub.fp_nsl.p, iflag.p, need.p, res.p,
+                                                        cnt.p, nullptr, nullptr, bad.p);
+    sub.st_off[jj].alloc((size_t)m * SL_N + 1);
+    exclusive_scan_i32(cnt.p, sub.st_off[jj].p, (int64_t)m * SL_N, s);
+    int32_t tot = 0;
+    SLT_CUDA(cudaMemcpyAsync(&tot, sub.st_off[jj].p + (int64_t)m * SL_N, 4, cudaMemcpyDeviceToHost, s));
+    SLT_CUDA(cudaStreamSynchronize(s));
+    sub.st_ent[jj].alloc(std::max(tot, 1));
+    k_stage_lists<false><<<grid_for(m, 64), 64, 0, s>>>(sg, m, sub.fp_ptr.p, sub.fp_nsl.p, iflag.p, need.p, res.p,
+                                                         nullptr, sub.st_off[jj].p, sub.st_ent[jj].p, bad.p);
+    SLT_CUDA(cudaGetLastError());
+  }
+  int32_t hbad = 0;
+  SLT_CUDA(cudaMemcpyAsync(&hbad, bad.p, 4, cudaMemcpyDeviceToHost, s));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  if (hbad) fail(SLT_ERR_UNSUPPORTED, "staged plan: a facet iteration's cell is outside its tile's footprint");
 }
 
 }  // namespace slt

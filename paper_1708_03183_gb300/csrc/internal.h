@@ -169,7 +169,18 @@ struct SubSched {
   std::vector<int32_t> colour_ptr;                     // host, ncolours + 1
   DevBuf<int32_t> tiles_by_colour;
   std::vector<DevBuf<int32_t>> plan_ptr, plan_items;   // per segment, at its first loop (others empty)
+  // staged executor (executor 3): each tile's footprint (the cells its segments touch, ascending
+  // work id, slot = position), per segment seven lists of slot entries (see stage_build)
+  DevBuf<int32_t> fp_ptr, fp_cell, fp_nsl;             // [m + 1]; work id | shared << 31; neighbour slots
+  std::vector<DevBuf<int32_t>> st_off, st_ent;         // per segment: [7 m + 1] list offsets, entries
+  int32_t max_fp = 0;                                  // largest footprint
 };
+// the seven lists of a segment of a tile, in the order the staged executor runs them
+enum StageList : int32_t { SL_GATHER = 0, SL_INIT, SL_INT0, SL_INT1, SL_INT2, SL_EXT, SL_PB, SL_N };
+constexpr int32_t kSlotBits = 11, kNoSlot = (1 << kSlotBits) - 1;  // at most 2047 slots per tile
+// item flags of the staged lists: faces (3 bits), first cell loop (8), later cell loop (16), and
+// 32 = the accumulated value starts from global memory (contributions made by another tile)
+constexpr int32_t kLoadBit = 32;
 
 }  // namespace slt
 
@@ -179,6 +190,7 @@ struct DataflowPlan {
   std::vector<int32_t> cum;          // global tile id base per sub-chain, size nsub + 1
   DevBuf<int32_t> succ_ptr, succ;    // CSR over global tiles: (global tile << 1) | next step
   DevBuf<int32_t> indeg0, indeg;     // dependencies of a tile's first-step node / later nodes
+  DevBuf<int32_t> indeg_sub;         // same-step dependencies inside the tile's own sub-chain
   DevBuf<int32_t> pending, queue;    // per run: [nsteps * tiles]
   DevBuf<unsigned long long> head;   // head, tail
   DevBuf<int32_t> err;
@@ -191,7 +203,8 @@ struct DataflowPlan {
 }  // namespace slt
 
 struct slt_schedule_s {
-  int32_t executor = 0;              // 0 dataflow, 1 colour phases, 2 dataflow with tile clusters
+  int32_t executor = 0;              // 0 dataflow, 1 colour phases, 2 dataflow with tile clusters, 3 staged
+  int32_t stage_cross = 0;           // staged: temporaries cross sub-chains, so every one is written out
   int32_t block = 256;               // threads per tile CTA (128, 256 or 384)
   int32_t shots_per_cta = 0;         // multi-shot dataflow runs: shots per queue pass (0 = all)
   int32_t cluster = 8;               // executor 2: CTAs per tile cluster
@@ -239,6 +252,7 @@ struct slt_mesh_s {
   int64_t cells_int = 0, cells_ext = 0;  // cells with an interior / exterior face
   // device, work layout (SoA, stride ncp)
   slt::DevBuf<double> geo, fgeo, mat, src;
+  slt::DevBuf<double> pre;          // products of geometry and material hoisted out of the loops
   slt::DevBuf<int32_t> nbr, d_perm, d_iperm;
   int32_t src_w = -1;
   // work fields: V[2 Np], S[3 Np], U1[2 Np], U2[2 Np], E[3 Np], S1[3 Np] rows of ncp
@@ -285,6 +299,8 @@ struct slt_receivers_s {
 namespace slt {
 // exec.cu
 void upload_constants(const RefElem& r);
+// the mesh's hoisted per-cell products (pre) from its geometry and material, on s
+void build_pre(slt_mesh m, cudaStream_t s);
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile = nullptr);
 void group_build(slt_group g);
@@ -300,6 +316,20 @@ void op_A(slt_mesh m, const double* in3, double* out2, cudaStream_t s);
 void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s);
 // exec_batched.cu
 void upload_constants_batched(const RefElem& r);
+// One part of one time step on a multi-shot work layout (S shots; every buffer rows of ncp * S
+// doubles, column cell * S + shot): part 0 the velocity sub-chain (loops 0-8), 1 the stress
+// sub-chain (9-16), 2 the whole step.  Untiled when sched is null, else the dataflow executor (a
+// part alone needs a {velocity, stress} schedule).  Synchronises when tiled.
+struct ChainRun {
+  int32_t S = 1;
+  double* buf[6] = {};          // V, S, U1, U2, E, S1
+  double* e5 = nullptr;         // where phase 5 leaves its strain (null: buf[4])
+  const double* ricker = nullptr;  // source series at this step, or null (no source)
+  double dt = 0;
+  const int32_t* src_w = nullptr;  // [S] source cell of each shot (work id, -1 none), device
+  const double* src = nullptr;     // [S][Np] source coefficients, device
+};
+void chain_part_b(slt_mesh m, slt_schedule sched, const ChainRun& r, int part, cudaStream_t s);
 void exec_run_batched(slt_mesh m, slt_schedule sched, int32_t S, const int32_t* d_src_w, const double* d_src,
                       double* v, double* sigma, const double* ricker, double dt, int64_t nsteps, cudaStream_t s,
                       double* profile);
@@ -313,8 +343,18 @@ void record_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
                 double* traces, cudaStream_t s);
 void adjoint_run(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t N,
                  const double* data, int32_t k, double* grad_out, double* J_host, cudaStream_t s);
+// S shots (sources d_src_w [S], d_src [S][Np], device), untiled or tiled: traces / data are
+// [nsteps][S][nrec][2]; the gradient is summed over the shots
+void record_run_b(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t S, const int32_t* d_src_w,
+                  const double* d_src, const double* ricker, double dt, int64_t nsteps, double* traces,
+                  cudaStream_t s);
+void adjoint_run_b(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t S, const int32_t* d_src_w,
+                   const double* d_src, const double* ricker, double dt, int64_t N, const double* data, int32_t k,
+                   double* grad_out, double* J_host, cudaStream_t s);
 void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
+void stage_build(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
+int32_t stage_capacity(int p);  // slots of shared memory the staged executor has per tile CTA
 // inspect.cu
 void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out);
 }  // namespace slt

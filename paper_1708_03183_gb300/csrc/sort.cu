@@ -95,6 +95,69 @@ __global__ void k_scan_single(const int32_t* __restrict__ in, int32_t* __restric
   if (threadIdx.x == T - 1) out[n] = (int32_t)part[T - 1];
 }
 
+// Multi-block exclusive scan: each block takes a tile of SC_THREADS x SC_ITEMS consecutive
+// values (SC_ITEMS per thread); pass 1 writes the tile totals, a single block scans them, pass 2
+// scans each tile from its offset.  Integer sums, so the result does not depend on the order.
+constexpr int SC_THREADS = 512, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ int32_t block_exclusive(int32_t x, int32_t* total) {
+  __shared__ int32_t warp_sum[SC_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = lane < SC_THREADS / 32 ? warp_sum[lane] : 0, wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < SC_THREADS / 32) warp_sum[lane] = wi - w;  // exclusive prefix of the warps
+    if (lane == SC_THREADS / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  return warp_sum[wid] + incl - x;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int32_t* __restrict__ in, int64_t n,
+                                                           int32_t* __restrict__ tsum) {
+  __shared__ int32_t total;
+  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  int32_t s = 0;
+#pragma unroll
+  for (int v = 0; v < SC_ITEMS; ++v)
+    if (base + v < n) s += in[base + v];
+  block_exclusive(s, &total);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_apply(const int32_t* __restrict__ in, int64_t n,
+                                                           const int32_t* __restrict__ toff,
+                                                           int32_t* __restrict__ out) {
+  __shared__ int32_t total;
+  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  int32_t v[SC_ITEMS], s = 0;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    s += v[k];
+  }
+  int32_t acc = toff[blockIdx.x] + block_exclusive(s, &total);
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k)
+    if (base + k < n) {
+      out[base + k] = acc;
+      acc += v[k];
+    }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = toff[gridDim.x];
+}
+
 __global__ void k_lower_bound(const uint32_t* __restrict__ sorted, int64_t n, int64_t nkeys, int32_t* __restrict__ offs) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= n; p += (int64_t)gridDim.x * blockDim.x) {
     int64_t prev = p == 0 ? -1 : (int64_t)sorted[p - 1];
@@ -226,8 +289,19 @@ int bits_for(int64_t maxval) {
 }
 
 void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
-  k_scan_single<<<1, 1024, 0, s>>>(in, out, n);
+  if (n <= 4 * SC_TILE) {  // small: one block
+    k_scan_single<<<1, 1024, 0, s>>>(in, out, n);
+    SLT_CUDA(cudaGetLastError());
+    return;
+  }
+  const int64_t nt = (n + SC_TILE - 1) / SC_TILE;
+  DevBuf<int32_t> tsum(nt), toff(nt + 1);
+  k_scan_tiles<<<(unsigned)nt, SC_THREADS, 0, s>>>(in, n, tsum.p);
+  k_scan_single<<<1, 1024, 0, s>>>(tsum.p, toff.p, nt);
+  k_scan_apply<<<(unsigned)nt, SC_THREADS, 0, s>>>(in, n, toff.p, out);
   SLT_CUDA(cudaGetLastError());
+  // the temporaries are freed on return; the stream must have consumed them first
+  SLT_CUDA(cudaStreamSynchronize(s));
 }
 
 void lower_bound_offsets(const uint32_t* sorted, int64_t n, int64_t nkeys, int32_t* offs, cudaStream_t s) {

@@ -56,7 +56,7 @@ def _recount(lib, sched, cfg, bounds):
             cur[g] = 1.0 + max([prev_l[e] if w else cur[e] for e, w in by_node[g]], default=0.0)
         top.append(max(cur))
         prev_l = cur
-    return G, len(deps), (top[11] - top[6]) / 5
+    return G, deps, (top[11] - top[6]) / 5
 
 
 def cols_of(cols, base, g):
@@ -70,10 +70,23 @@ def test_dataflow_graph_figures_match_a_recount(lib, name, ts, split):
     mesh = gpu_mesh(lib, cfg)
     sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=ts, split=split)
     bounds = list(zip((0,) + tuple(split), tuple(split) + (17,)))
-    G, ndeps, cp = _recount(lib, sched, cfg, bounds)
+    G, deps, cp = _recount(lib, sched, cfg, bounds)
     info = lib.slt_schedule_dataflow_info(sched)
     assert info["nodes_per_step"] == G
-    assert info["deps_per_step"] == ndeps
+    assert info["deps_per_step"] == len(deps)
+    # the graph itself, edge by edge: successor lists in ascending order, in-degrees
+    sp, sv = lib.slt_schedule_export(sched, "succ_ptr", 0), lib.slt_schedule_export(sched, "succ", 0)
+    assert sp[0] == 0 and sp[-1] == len(sv) and len(sp) == G + 1 and np.all(np.diff(sp) >= 0)
+    got = set()
+    for a in range(G):
+        lst = sv[sp[a]:sp[a + 1]]
+        assert np.all(np.diff(lst) > 0)
+        got |= {(int(e) >> 1, a, int(e) & 1) for e in lst}
+    assert got == deps
+    indeg = np.bincount([g for g, _, _ in deps], minlength=G)
+    indeg0 = np.bincount([g for g, _, w in deps if not w], minlength=G)
+    assert np.array_equal(lib.slt_schedule_export(sched, "indeg", 0), indeg)
+    assert np.array_equal(lib.slt_schedule_export(sched, "indeg0", 0), indeg0)
     assert info["critical_path_nodes"] == pytest.approx(cp, rel=0, abs=1e-12)
     assert len(bounds) <= info["critical_path_nodes"] <= G
     assert info["tiles_in_flight"] == 0
