@@ -322,42 +322,50 @@ def run_reference(args, rank):
 
 
 def adjoint_timing(slt, synth, args, barrier):
-    """Forward (slt_record) and gradient (slt_adjoint) time on the adjoint workload's mesh: 448x224
-    squares (200k cells, P2, layered +-5 % per cell), one shot of the top row of the 8x8 source
-    grid, 50 receivers along the top edge, checkpoints every 50 steps, `--adjoint-steps` steps.
-    Both record the receivers after every step, so their forward steps run as the untiled
-    chain (six fused phases per step): the persistent tiled executor needs many steps per launch."""
+    """Forward (slt_record_batched) and gradient (slt_adjoint_batched) time on the adjoint
+    workload: 448x224 squares (200k cells, P2, layered +-5 % per cell), the 8 shots of the top row
+    of the 8x8 source grid in one call (fields with the shots innermost), 50 receivers along the
+    top edge, checkpoints every 50 steps, `--adjoint-steps` steps; untiled, and on the tiles of
+    a {velocity, stress} schedule (ts `--adjoint-ts`, every operator application of the forward
+    run, the segment recompute and the reverse sweep on the dataflow executor).  The forward
+    records the receivers after every step, so it runs one step per launch."""
     import numpy as np
     import torch
     n = args.adjoint_steps
     cfg = synth.build_config("adjoint", nsteps=n)
     m = cfg["mesh"]
     nc = m["cell2vert"].shape[0]
-    shot = np.array([(0 + 0.5) * 300.0 / 8, (7 + 0.5) * 150.0 / 8])
+    shots = np.array([((i + 0.5) * 300.0 / 8, (7 + 0.5) * 150.0 / 8) for i in range(8)])
     rec = np.stack([(np.arange(50) + 0.5) * 6.0, np.full(50, 149.0)], 1)
     base = synth.layered(m)
-    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], *base, shot)
-    sched = None
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], cfg["p"], *base)
     r = slt.slt_receivers_create(mesh, rec)
     rk = torch.tensor(cfg["ricker"], device="cuda")
-    data = torch.zeros((n, 50, 2), dtype=torch.float64, device="cuda")
-    slt.slt_record(mesh, sched, r, rk, cfg["dt"], n, data)          # synthetic data, unperturbed model
-    slt.slt_mesh_set_material(mesh, cfg["rho"], cfg["lam"], cfg["mu"])  # perturbed model
-    tr = torch.zeros_like(data)
-    g = torch.zeros((3, nc), dtype=torch.float64, device="cuda")
-    barrier()
-    t0 = time.perf_counter()
-    slt.slt_record(mesh, sched, r, rk, cfg["dt"], n, tr)
-    barrier()
-    t_fwd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    J = slt.slt_adjoint(mesh, sched, r, rk, cfg["dt"], n, data, 50, g)
-    barrier()
-    t_adj = time.perf_counter() - t0
-    return {"workload": "448x224 squares (%d cells), P2, 1 shot, 50 receivers, %d steps, checkpoints every 50" % (nc, n),
-            "forward_ms_per_step": 1e3 * t_fwd / n, "gradient_ms_per_step": 1e3 * t_adj / n,
-            "adjoint_over_forward": t_adj / t_fwd, "misfit": J,
-            "note": "gradient = forward with checkpoints + segment recompute + reverse sweep"}
+    S = len(shots)
+    data = torch.zeros((n, S, 50, 2), dtype=torch.float64, device="cuda")
+    slt.slt_record_batched(mesh, None, r, shots, rk, cfg["dt"], n, data)   # synthetic data, unperturbed model
+    slt.slt_mesh_set_material(mesh, cfg["rho"], cfg["lam"], cfg["mu"])      # perturbed model
+    out = {"workload": "448x224 squares (%d cells), P2, %d shots in one call, 50 receivers, %d steps, "
+                       "checkpoints every 50" % (nc, S, n)}
+    sched = slt.slt_inspect(slt.slt_mesh_chain(mesh), tile_size=args.adjoint_ts, split=(9,))
+    for name, sc in (("untiled", None), ("tiled_ts%d" % args.adjoint_ts, sched)):
+        tr = torch.zeros_like(data)
+        g = torch.zeros((3, nc), dtype=torch.float64, device="cuda")
+        barrier()
+        t0 = time.perf_counter()
+        slt.slt_record_batched(mesh, sc, r, shots, rk, cfg["dt"], n, tr)
+        barrier()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        J = slt.slt_adjoint_batched(mesh, sc, r, shots, rk, cfg["dt"], n, data, 50, g)
+        barrier()
+        t_adj = time.perf_counter() - t0
+        out[name] = {"forward_ms_per_step": 1e3 * t_fwd / n, "gradient_ms_per_step": 1e3 * t_adj / n,
+                     "adjoint_over_forward": t_adj / t_fwd, "misfit": J,
+                     "shot_steps_per_s_gradient": S * n / t_adj}
+    out["note"] = ("gradient = forward with checkpoints + segment recompute keeping the operator "
+                   "intermediates + reverse sweep; all shots of a step in each launch")
+    return out
 
 
 def batched_timing(slt, synth, args, barrier):
@@ -520,6 +528,7 @@ def main():
     ap.add_argument("--scale", type=int, default=1, help="divide nx, ny of the workload (small profiling cases)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=1000)
+    ap.add_argument("--adjoint-ts", type=int, default=64)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-p4", action="store_true")

@@ -342,6 +342,26 @@ int slt_record(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const doubl
 int slt_adjoint(slt_mesh mesh, slt_schedule sched, slt_receivers rec, const double* ricker, double dt,
                 int64_t nsteps, const double* data, int32_t checkpoint_every, double* grad, double* misfit,
                 void* stream);
+/* Many shots at once (Section 7.1's explosive source, one per shot; the shots of the batched
+   form, fields with the shots innermost), untiled (sched = NULL) or on the tiles of an executor-0
+   schedule with the {velocity, stress} fusion (split at loop 9; SLT_ERR_UNSUPPORTED otherwise).
+   src_xy: host [nshots][2] source points (NULL: no sources); traces and data are device arrays
+   [nsteps][nshots][nrec][2].  slt_record_batched records the traces of runs from rest.
+   slt_adjoint_batched returns J = sum over the shots of the single-shot misfit and its gradient
+   grad [3][ncell] (device, caller numbering, summed over the shots), by the discrete adjoint:
+   the forward run keeps (v, sigma) every checkpoint_every = k >= 1 steps; each segment is
+   recomputed one sub-chain at a time with every step's operator intermediates written to a keep
+   slot (15 Np ncell nshots doubles per step, k steps); the reverse sweep runs, per step, the
+   velocity sub-chain on the adjoint variables with -dt, the stress-update gradient terms, the
+   receiver residuals, the stress sub-chain with -dt and the velocity-update gradient terms - the
+   adjoint step is the same loop chain (the skew identity), so the forward schedule's tiles serve
+   it as they are.  Synchronises.  slt_adjoint with such a schedule and checkpoint_every > 0 runs
+   its single shot the same way. */
+int slt_record_batched(slt_mesh mesh, slt_schedule sched, slt_receivers rec, int32_t nshots, const double* src_xy,
+                       const double* ricker, double dt, int64_t nsteps, double* traces, void* stream);
+int slt_adjoint_batched(slt_mesh mesh, slt_schedule sched, slt_receivers rec, int32_t nshots, const double* src_xy,
+                        const double* ricker, double dt, int64_t nsteps, const double* data, int32_t checkpoint_every,
+                        double* grad, double* misfit, void* stream);
 
 /* ------------------------------------------------------------------ FP64 peak probe
  * The paper has no counterpart: it measures the arithmetic roof of this library's kernels on the

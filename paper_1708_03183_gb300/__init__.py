@@ -69,6 +69,8 @@ _SIGS = {
     "slt_receivers_destroy": (ctypes.c_int, [P]),
     "slt_record": (ctypes.c_int, [P, P, P, P, F64, I64, P, P]),
     "slt_adjoint": (ctypes.c_int, [P, P, P, P, F64, I64, P, I32, P, P, P]),
+    "slt_record_batched": (ctypes.c_int, [P, P, P, I32, P, P, F64, I64, P, P]),
+    "slt_adjoint_batched": (ctypes.c_int, [P, P, P, I32, P, P, F64, I64, P, I32, P, P, P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -498,3 +500,33 @@ def exported_symbols():
     import re
     hdr = open(os.path.join(_build_mod.ROOT, "include", "slt.h")).read()
     return sorted(set(re.findall(r"\b(slt_[a-z_]+)\s*\(", hdr)))
+
+
+def slt_record_batched(mesh, sched, rec, src_xy, ricker, dt, nsteps, traces, stream=None):
+    """Runs from rest of every shot (src_xy [nshots, 2], host); traces: CUDA float64
+    [nsteps, nshots, nrec, 2], written."""
+    xy, xyp = _host(np.asarray(src_xy).reshape(-1, 2), np.float64)
+    S = xy.shape[0]
+    if traces.numel() != nsteps * S * rec.n * 2 or (ricker is not None and ricker.numel() < nsteps):
+        raise ValueError("traces need nsteps * nshots * nrec * 2 values and the source series nsteps")
+    _check(lib.slt_record_batched(mesh.ptr, sched.ptr if sched is not None else None, rec.ptr, S, xyp,
+                                  _dev(ricker, "float64"), float(dt), int(nsteps), _dev(traces, "float64"),
+                                  _stream(stream)))
+
+
+def slt_adjoint_batched(mesh, sched, rec, src_xy, ricker, dt, nsteps, data, checkpoint_every, grad, stream=None):
+    """Summed misfit of every shot against data [nsteps, nshots, nrec, 2] (CUDA float64) and its
+    gradient written to grad [3, ncell]; returns the misfit."""
+    xy, xyp = _host(np.asarray(src_xy).reshape(-1, 2), np.float64)
+    S = xy.shape[0]
+    n = slt_mesh_info(mesh)["ncell"]
+    if data.numel() != nsteps * S * rec.n * 2 or grad.numel() != 3 * n:
+        raise ValueError("data needs nsteps * nshots * nrec * 2 values and grad 3 * ncell")
+    if ricker is not None and ricker.numel() < nsteps:
+        raise ValueError("the source series is shorter than nsteps")
+    J = ctypes.c_double()
+    _check(lib.slt_adjoint_batched(mesh.ptr, sched.ptr if sched is not None else None, rec.ptr, S, xyp,
+                                   _dev(ricker, "float64"), float(dt), int(nsteps), _dev(data, "float64"),
+                                   int(checkpoint_every), _dev(grad, "float64"), ctypes.byref(J), _stream(stream)))
+    return J.value
+

@@ -1,15 +1,18 @@
 """Seismogram misfit as a torch.autograd.Function.
 
 J(rho, lambda, mu) = sum over shots s of 1/2 dt sum_n sum_r |P_r v_s^{n+1/2} - d_{s,r}^n|^2, each
-shot a run from rest with its own point source.  The forward pass calls slt_adjoint once per
-shot (misfit and gradient together, by the discrete adjoint of the time step); backward
-returns the stored gradient scaled by the incoming gradient.  Material tensors are per-cell
-float64 (any device); they are copied to the mesh before the run.
+shot a run from rest with its own point source.  The forward pass computes the misfit and its
+gradient together by the discrete adjoint of the time step, all shots in one call
+(slt_adjoint_batched: fields with the shots innermost, untiled or on the schedule's tiles); a
+schedule the batched adjoint does not take falls back to one slt_adjoint call per shot.
+Backward returns the stored gradient scaled by the incoming gradient.  Material tensors are
+per-cell float64 (any device); they are copied to the mesh before the run.
 """
 import numpy as np
 import torch
 
-from . import slt_adjoint, slt_mesh_info, slt_mesh_set_material, slt_mesh_set_source, slt_receivers_create
+from . import (SltError, slt_adjoint, slt_adjoint_batched, slt_mesh_info, slt_mesh_set_material,
+               slt_mesh_set_source, slt_receivers_create)
 
 
 class MisfitProblem:
@@ -36,12 +39,23 @@ class SeismogramMisfit(torch.autograd.Function):
         slt_mesh_set_material(problem.mesh, *host)
         total = 0.0
         grad = torch.zeros((3, problem.ncell), dtype=torch.float64, device="cuda")
-        g = torch.empty_like(grad)
-        for s, xy in enumerate(problem.shots):
-            slt_mesh_set_source(problem.mesh, xy)
-            total += slt_adjoint(problem.mesh, problem.sched, problem.rec, problem.ricker, problem.dt,
-                                 problem.nsteps, problem.data[s], problem.k, g)
-            grad += g
+        batched = problem.k >= 1
+        if batched:
+            try:
+                data = problem.data.permute(1, 0, 2, 3).contiguous()   # [nsteps, nshots, nrec, 2]
+                total = slt_adjoint_batched(problem.mesh, problem.sched, problem.rec, problem.shots, problem.ricker,
+                                            problem.dt, problem.nsteps, data, problem.k, grad)
+            except SltError as e:
+                if e.code != -6:   # a schedule the batched adjoint does not take
+                    raise
+                batched = False
+        if not batched:
+            g = torch.empty_like(grad)
+            for s, xy in enumerate(problem.shots):
+                slt_mesh_set_source(problem.mesh, xy)
+                total += slt_adjoint(problem.mesh, problem.sched, problem.rec, problem.ricker, problem.dt,
+                                     problem.nsteps, problem.data[s], problem.k, g)
+                grad += g
         ctx.save_for_backward(grad)
         ctx.devices = [t.device for t in (rho, lam, mu)]
         return torch.tensor(total, dtype=torch.float64, device=rho.device)

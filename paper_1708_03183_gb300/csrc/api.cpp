@@ -711,6 +711,11 @@ int slt_receivers_destroy(slt_receivers r) {
   API_END
 }
 
+// the tiled adjoint runs one sub-chain at a time on the dataflow executor
+static bool tiled_adjoint_ok(slt_schedule sched) {
+  return sched->executor == 0 && sched->subs.size() == 2 && sched->subs[0].last == 9;
+}
+
 int slt_record(slt_mesh m, slt_schedule sched, slt_receivers rec, const double* ricker, double dt, int64_t nsteps,
                double* traces, void* stream) {
   API_BEGIN
@@ -730,7 +735,70 @@ int slt_adjoint(slt_mesh m, slt_schedule sched, slt_receivers rec, const double*
   REQUIRE(nsteps >= 1 && std::isfinite(dt), "nsteps >= 1 and finite dt required");
   REQUIRE(checkpoint_every != 0 && checkpoint_every != INT32_MIN, "checkpoint_every must be nonzero");
   if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
-  adjoint_run(m, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, as_stream(stream));
+  if (sched && tiled_adjoint_ok(sched) && checkpoint_every > 0) {
+    // the whole adjoint on the schedule's tiles: one shot of the chain-executor path
+    cudaStream_t s = as_stream(stream);
+    DevBuf<int32_t> w(1);
+    const int32_t hw = m->src_w;
+    w.upload(&hw, 1, s);
+    DevBuf<double> coef(m->Np);
+    if (m->src.p) SLT_CUDA(cudaMemcpyAsync(coef.p, m->src.p, m->Np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else SLT_CUDA(cudaMemsetAsync(coef.p, 0, m->Np * sizeof(double), s));
+    adjoint_run_b(m, sched, rec, 1, w.p, coef.p, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, s);
+  } else {
+    adjoint_run(m, sched, rec, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, as_stream(stream));
+  }
+  API_END
+}
+
+// per-shot source cells (work ids) and coefficients on the device
+static void shot_sources(slt_mesh m, int32_t nshots, const double* src_xy, DevBuf<int32_t>& w, DevBuf<double>& c,
+                         cudaStream_t s) {
+  const int Np = m->Np;
+  std::vector<int32_t> hw(nshots, -1);
+  std::vector<double> hs((size_t)nshots * Np, 0.0);
+  if (src_xy)
+    for (int32_t k = 0; k < nshots; ++k) hw[k] = m->iperm[source_coeffs(m, src_xy + 2 * k, hs.data() + (size_t)k * Np)];
+  w.alloc(nshots);
+  c.alloc((size_t)nshots * Np);
+  w.upload(hw.data(), nshots, s);
+  c.upload(hs.data(), (size_t)nshots * Np, s);
+}
+
+int slt_record_batched(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t nshots, const double* src_xy,
+                       const double* ricker, double dt, int64_t nsteps, double* traces, void* stream) {
+  API_BEGIN
+  REQUIRE(m && rec && traces, "null argument");
+  REQUIRE(rec->mesh == m, "the receivers belong to another mesh");
+  REQUIRE(nshots >= 1 && nshots <= 4096, "nshots must be in 1..4096");
+  REQUIRE(nsteps >= 0 && std::isfinite(dt), "nsteps >= 0 and finite dt required");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  if (sched && sched->executor != 0) fail(SLT_ERR_UNSUPPORTED, "many shots run untiled or with executor 0");
+  cudaStream_t s = as_stream(stream);
+  DevBuf<int32_t> w;
+  DevBuf<double> c;
+  shot_sources(m, nshots, src_xy, w, c, s);
+  record_run_b(m, sched, rec, nshots, w.p, c.p, ricker, dt, nsteps, traces, s);
+  API_END
+}
+
+int slt_adjoint_batched(slt_mesh m, slt_schedule sched, slt_receivers rec, int32_t nshots, const double* src_xy,
+                        const double* ricker, double dt, int64_t nsteps, const double* data, int32_t checkpoint_every,
+                        double* grad, double* misfit, void* stream) {
+  API_BEGIN
+  REQUIRE(m && rec && data && grad && misfit, "null argument");
+  REQUIRE(rec->mesh == m, "the receivers belong to another mesh");
+  REQUIRE(nshots >= 1 && nshots <= 4096, "nshots must be in 1..4096");
+  REQUIRE(nsteps >= 1 && std::isfinite(dt), "nsteps >= 1 and finite dt required");
+  REQUIRE(checkpoint_every >= 1, "checkpoint_every must be >= 1");
+  if (sched && sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
+  if (sched && !tiled_adjoint_ok(sched))
+    fail(SLT_ERR_UNSUPPORTED, "the tiled adjoint needs executor 0 and the {velocity, stress} fusion (split at 9)");
+  cudaStream_t s = as_stream(stream);
+  DevBuf<int32_t> w;
+  DevBuf<double> c;
+  shot_sources(m, nshots, src_xy, w, c, s);
+  adjoint_run_b(m, sched, rec, nshots, w.p, c.p, ricker, dt, nsteps, data, checkpoint_every, grad, misfit, s);
   API_END
 }
 
