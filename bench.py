@@ -368,7 +368,7 @@ def adjoint_timing(slt, synth, args, barrier):
     return out
 
 
-def batched_timing(slt, synth, args, barrier):
+def batched_timing(slt, synth, args, barrier, keep):
     """Multi-shot form: the 708x354 P2 layered mesh (501k cells) with `--shots` point sources on
     the 8x8 grid x = (i+1/2) 300/8, y = (j+1/2) 150/8 (the first `--shots` of them), shots
     innermost.  The library's autotuner picks among the untiled chain and the dataflow executor
@@ -404,6 +404,7 @@ def batched_timing(slt, synth, args, barrier):
     fl = slt.slt_mesh_cost(mesh)["flops_per_step"] * S
     pick = ("untiled" if not best.tile_size else
             "ts%d, %d shots per CTA" % (best.tile_size, best.shots_per_cta or S))
+    keep.update(big_mesh=mesh, big_cfg=cfg, shots=pts, S=S, nc=nc, Np=Np)
     return {"workload": "708x354 squares on 300x150 (%d cells), P2 FP64, layered, %d shots on the 8x8 grid, "
                         "%d steps, fields [cell][comp][node][shot] (%.1f GB)" % (nc, S, K, 5 * Np * nc * S * 8 / 1e9),
             "value": units / (ms * 1e-3), "unit": "dof-updates/s", "best": pick, "ms_per_step": ms,
@@ -412,7 +413,7 @@ def batched_timing(slt, synth, args, barrier):
                                                      for r in table]}}
 
 
-def multi_timing(slt, synth, args, barrier):
+def multi_timing(slt, synth, args, barrier, keep):
     """Many uneven meshes: 16 meshes with cell counts log-uniform in [20k, 400k] (seed 4), degree
     1 + (i mod 3), each sparse-tiled (ts 256, dataflow executor) and advanced `--multi-steps`
     steps as one group (one combined ready queue per degree) against the same meshes run one
@@ -433,6 +434,7 @@ def multi_timing(slt, synth, args, barrier):
     units = sum(5 * ((c["p"] + 1) * (c["p"] + 2) // 2) * c["mesh"]["cell2vert"].shape[0] for c in cfgs)
     vs, ss, rs = [list(x) for x in zip(*fields)]
     dts = [c["dt"] for c in cfgs]
+    keep.update(meshes=meshes, scheds=scheds, cfgs=cfgs, units_multi=units)
     grp = slt.slt_group_create(meshes, scheds)
     slt.slt_group_execute(grp, vs, ss, rs, dts, W)
     barrier()
@@ -453,6 +455,55 @@ def multi_timing(slt, synth, args, barrier):
                 min(ncs), max(ncs), sum(ncs), K),
             "value": units * K / (t_many * 1e-3), "unit": "dof-updates/s", "ms_per_step": t_many / K,
             "one_after_another_ms_per_step": t_seq / K, "overlap_speedup": t_seq / t_many}
+
+
+def one_launch_timing(slt, synth, args, barrier, keep):
+    """The whole batched configuration in one persistent launch: the 64 shots of the batched
+    block (708x354 P2 mesh, tiled at ts `--batched-ts`[0], all shots of a tile in its CTA) and the
+    16 uneven meshes of the multi block (ts 256), all from one ready queue
+    (slt_group_create_batched), the step captured once as a CUDA graph and replayed; against the
+    same two workloads run one after the other (the 64-shot launch, then the group of meshes)."""
+    import torch
+    K, W = args.batched_steps, 3
+    big, cfgs, meshes, scheds = keep["big_mesh"], keep["cfgs"], keep["meshes"], keep["scheds"]
+    S, nc, Np, bcfg = keep["S"], keep["nc"], keep["Np"], keep["big_cfg"]
+    ts = args.batched_ts[0]
+    bsched = slt.slt_inspect(slt.slt_mesh_chain(big), tile_size=ts, split=(9,))
+    grp = slt.slt_group_create_batched([big] + meshes, [bsched] + scheds, [S] + [1] * len(meshes),
+                                       [keep["shots"]] + [None] * len(meshes))
+    bv = torch.zeros((nc, 2, Np, S), dtype=torch.float64, device="cuda")
+    bs = torch.zeros((nc, 3, Np, S), dtype=torch.float64, device="cuda")
+    fields = [(torch.zeros((c["mesh"]["cell2vert"].shape[0], 2, (c["p"] + 1) * (c["p"] + 2) // 2),
+                           dtype=torch.float64, device="cuda"),
+               torch.zeros((c["mesh"]["cell2vert"].shape[0], 3, (c["p"] + 1) * (c["p"] + 2) // 2),
+                           dtype=torch.float64, device="cuda")) for c in cfgs]
+    vs, ss = [bv] + [f[0] for f in fields], [bs] + [f[1] for f in fields]
+    K = min(K, len(bcfg["ricker"]) - W, min(len(c["ricker"]) for c in cfgs) - W)
+    brk = torch.tensor(bcfg["ricker"][:W + K], device="cuda")
+    rks = [brk] + [torch.tensor(c["ricker"][:W + K], device="cuda") for c in cfgs]
+    dts = [bcfg["dt"]] + [c["dt"] for c in cfgs]
+    slt.slt_group_execute(grp, vs, ss, rks, dts, W)          # captures the graph (W steps)
+    slt.slt_group_execute(grp, vs, ss, rks, dts, W)          # replays it
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    slt.slt_group_execute(grp, vs, ss, [r[W:] for r in rks], dts, K)
+    e1.record()
+    barrier()
+    t_one = e0.elapsed_time(e1)
+    # the same work as two launches: the 64 shots alone, then the group of meshes
+    grp2 = slt.slt_group_create(meshes, scheds)
+    e0.record()
+    slt.slt_execute_batched(big, bsched, keep["shots"], bv, bs, brk[W:], bcfg["dt"], K)
+    slt.slt_group_execute(grp2, vs[1:], ss[1:], [r[W:] for r in rks[1:]], dts[1:], K)
+    e1.record()
+    barrier()
+    t_two = e0.elapsed_time(e1)
+    units = 5 * Np * nc * S + keep["units_multi"]
+    return {"workload": "the 64-shot 708x354 P2 mesh (ts %d) and the 16 uneven meshes (ts 256) in one persistent "
+                        "launch, graph-captured, %d steps" % (ts, K),
+            "value": units * K / (t_one * 1e-3), "unit": "dof-updates/s", "ms_per_step": t_one / K,
+            "two_launches_ms_per_step": t_two / K, "graph_replays": slt.slt_group_graph_replays(grp)}
 
 
 def p4_timing(slt, synth, args, barrier):
@@ -714,13 +765,17 @@ def main():
         out["p4"] = p4_timing(slt, synth, args, barrier)
     if not args.no_adjoint:
         out["adjoint"] = adjoint_timing(slt, synth, args, barrier)
+    keep = {}
     if not args.no_batched:
         del sched, mesh
         torch.cuda.empty_cache()
-        out["batched"] = batched_timing(slt, synth, args, barrier)
+        out["batched"] = batched_timing(slt, synth, args, barrier, keep)
     if not args.no_multi:
         torch.cuda.empty_cache()
-        out["multi"] = multi_timing(slt, synth, args, barrier)
+        out["multi"] = multi_timing(slt, synth, args, barrier, keep)
+    if not args.no_batched and not args.no_multi:
+        torch.cuda.empty_cache()
+        out["batched_one_launch"] = one_launch_timing(slt, synth, args, barrier, keep)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, d = oracle_sample_rate(args.config, 10)

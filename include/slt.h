@@ -244,7 +244,10 @@ int slt_execute(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, con
    one profiled call at a time per process. */
 int slt_execute_profiled(slt_mesh mesh, slt_schedule sched, double* v, double* sigma, const double* ricker,
                          double dt, int64_t nsteps, void* stream, double profile[8]);
-/* The same with HOST fields and source series: copies in, runs, copies out, synchronises. */
+/* The same with HOST fields and source series (page-locked memory lets the copies run
+   asynchronously): copies in, runs, copies out, synchronises.  The fields cross the host link in
+   four chunks of cells on a private copy stream, and each chunk is converted into (out of) the
+   work layout while the next one is on the link. */
 int slt_execute_host(slt_mesh mesh, slt_schedule sched, double* host_v, double* host_sigma,
                      const double* host_ricker, double dt, int64_t nsteps, void* stream);
 /* Many shots of the same mesh and material at once (the batched form): nshots runs with their
@@ -277,6 +280,21 @@ int slt_execute_batched(slt_mesh mesh, slt_schedule sched, int32_t nshots, const
    meshes of one degree use different CTA sizes.  slt_execute_many = create, execute once,
    destroy. */
 int slt_group_create(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, slt_group* out);
+/* The batched form in one persistent launch: as slt_group_create, with member i carrying
+   nshots[i] shots (1 = one field; several: fields [cell][comp][node][shot] in
+   slt_group_execute, sources at host src_xy[i] [nshots[i]][2], src_xy or src_xy[i] NULL = no
+   sources; such a member needs a dataflow-executor schedule).  Every tiled member, whatever its
+   degree (1-3) and layout, runs from one ready queue in one persistent kernel; the conversion of
+   the fields into the work layout and back, the queue reset and seeding and the kernel are
+   captured as one CUDA graph on the first slt_group_execute and replayed while nsteps and the
+   field pointers stay the same (the source series and time steps may change between calls).
+   Untiled members run after it.  SLT_ERR_UNSUPPORTED for a tiled member of degree 4 or with
+   other than 256-thread tiles, or a member with several shots and no such schedule.
+   slt_group_graph_replays: how often the group's cached graph has been launched since it was
+   (re)captured. */
+int slt_group_create_batched(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, const int32_t* nshots,
+                             const double* const* src_xy, slt_group* out);
+int slt_group_graph_replays(slt_group group, int64_t* replays);
 int slt_group_destroy(slt_group group);
 int slt_group_execute(slt_group group, double* const* v, double* const* sigma, const double* const* ricker,
                       const double* dt, int64_t nsteps, void* stream);

@@ -60,6 +60,8 @@ _SIGS = {
     "slt_group_create": (ctypes.c_int, [I32, P, P, P]),
     "slt_group_destroy": (ctypes.c_int, [P]),
     "slt_group_execute": (ctypes.c_int, [P, P, P, P, P, I64, P]),
+    "slt_group_create_batched": (ctypes.c_int, [I32, P, P, P, P, P]),
+    "slt_group_graph_replays": (ctypes.c_int, [P, P]),
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_fp64_peak": (ctypes.c_int, [P, P]),
@@ -284,9 +286,9 @@ def slt_mesh_chain(mesh):
     return Chain(h)
 
 
-def _check_fields(mesh, v, sigma, ricker, nsteps):
+def _check_fields(mesh, v, sigma, ricker, nsteps, nshots=1):
     info = slt_mesh_info(mesh)
-    nv, ns = info["ncell"] * 2 * info["Np"], info["ncell"] * 3 * info["Np"]
+    nv, ns = info["ncell"] * 2 * info["Np"] * nshots, info["ncell"] * 3 * info["Np"] * nshots
     if v.numel() != nv or sigma.numel() != ns:
         raise ValueError("v needs %d and sigma %d float64 values" % (nv, ns))
     if ricker is not None and ricker.numel() < nsteps:
@@ -335,12 +337,12 @@ def slt_execute_batched(mesh, sched, src_xy, v, sigma, ricker, dt, nsteps, strea
                     max_launch_ms=prof[4], min_launch_ms=prof[5], setup_ms=prof[6], setup_launches=int(prof[7]))
 
 
-def _group_args(meshes, vs, sigmas, rickers, dts, nsteps):
+def _group_args(meshes, vs, sigmas, rickers, dts, nsteps, nshots=None):
     n = len(meshes)
     if not (len(vs) == len(sigmas) == len(rickers) == len(dts) == n):
         raise ValueError("one field pair, source series and dt per mesh")
-    for m, v, s_, r in zip(meshes, vs, sigmas, rickers):
-        _check_fields(m, v, s_, r, nsteps)
+    for i, (m, v, s_, r) in enumerate(zip(meshes, vs, sigmas, rickers)):
+        _check_fields(m, v, s_, r, nsteps, nshots[i] if nshots else 1)
     arr = lambda xs: (ctypes.c_void_p * n)(*xs)
     return (arr([_dev(v, "float64") for v in vs]), arr([_dev(x, "float64") for x in sigmas]),
             arr([_dev(r, "float64") for r in rickers]), (ctypes.c_double * n)(*[float(d) for d in dts]))
@@ -365,10 +367,41 @@ def slt_group_create(meshes, scheds):
     return g
 
 
+def slt_group_create_batched(meshes, scheds, nshots, src_xy):
+    """The batched form in one persistent, graph-captured launch: members of any degree 1-3,
+    member i with nshots[i] shots (sources src_xy[i] [nshots[i], 2], host, or None)."""
+    n = len(meshes)
+    if not (len(scheds) == len(nshots) == len(src_xy) == n):
+        raise ValueError("one schedule, shot count and source array per mesh")
+    arr = lambda xs: (ctypes.c_void_p * n)(*xs)
+    keep = [None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 2))
+            for x in src_xy]
+    for k, x in zip(nshots, keep):
+        if x is not None and x.shape[0] != k:
+            raise ValueError("src_xy[i] needs nshots[i] points")
+    h = ctypes.c_void_p()
+    _check(lib.slt_group_create_batched(n, arr([m.ptr for m in meshes]),
+                                        arr([s.ptr if s is not None else None for s in scheds]),
+                                        (ctypes.c_int32 * n)(*[int(k) for k in nshots]),
+                                        arr([None if x is None else x.ctypes.data for x in keep]), ctypes.byref(h)))
+    g = Group(h)
+    g.meshes = list(meshes)
+    g.scheds = list(scheds)
+    g.nshots = [int(k) for k in nshots]
+    return g
+
+
+def slt_group_graph_replays(group):
+    r = I64()
+    _check(lib.slt_group_graph_replays(group.ptr, ctypes.byref(r)))
+    return r.value
+
+
 def slt_group_execute(group, vs, sigmas, rickers, dts, nsteps, stream=None):
     """Advance every mesh of the group; per mesh: v [ncell, 2, Np] and sigma [ncell, 3, Np] CUDA
-    float64 tensors updated in place, ricker (CUDA float64 or None), dt."""
-    v, s_, r, d = _group_args(group.meshes, vs, sigmas, rickers, dts, nsteps)
+    float64 tensors updated in place ([ncell, 2, Np, nshots], [ncell, 3, Np, nshots] for a member
+    with several shots), ricker (CUDA float64 or None), dt."""
+    v, s_, r, d = _group_args(group.meshes, vs, sigmas, rickers, dts, nsteps, getattr(group, "nshots", None))
     _check(lib.slt_group_execute(group.ptr, v, s_, r, d, int(nsteps), _stream(stream)))
 
 

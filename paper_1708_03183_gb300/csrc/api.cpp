@@ -626,18 +626,7 @@ int slt_execute_host(slt_mesh m, slt_schedule sched, double* hv, double* hs, con
   if (sched) {
     if (sched->mesh != m) fail(SLT_ERR_STATE, "the schedule was not inspected on this mesh's chain");
   }
-  cudaStream_t s = as_stream(stream);
-  const int64_t nv = m->nc * 2 * m->Np, ns = m->nc * 3 * m->Np;
-  if (m->io_v.n < (size_t)nv) m->io_v.alloc(nv);
-  if (m->io_s.n < (size_t)ns) m->io_s.alloc(ns);
-  if (hr && m->ricker_buf.n < (size_t)std::max<int64_t>(nsteps, 1)) m->ricker_buf.alloc(std::max<int64_t>(nsteps, 1));
-  m->io_v.upload(hv, nv, s);
-  m->io_s.upload(hs, ns, s);
-  if (hr) m->ricker_buf.upload(hr, nsteps, s);
-  exec_run(m, sched, m->io_v.p, m->io_s.p, hr ? m->ricker_buf.p : nullptr, dt, nsteps, s);
-  SLT_CUDA(cudaMemcpyAsync(hv, m->io_v.p, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SLT_CUDA(cudaMemcpyAsync(hs, m->io_s.p, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SLT_CUDA(cudaStreamSynchronize(s));
+  exec_run_host(m, sched, hv, hs, hr, dt, nsteps, as_stream(stream));
   API_END
 }
 
@@ -710,6 +699,9 @@ int slt_receivers_destroy(slt_receivers r) {
   delete r;
   API_END
 }
+
+static void shot_sources(slt_mesh m, int32_t nshots, const double* src_xy, DevBuf<int32_t>& w, DevBuf<double>& c,
+                         cudaStream_t s);
 
 // the tiled adjoint runs one sub-chain at a time on the dataflow executor
 static bool tiled_adjoint_ok(slt_schedule sched) {
@@ -843,6 +835,45 @@ int slt_group_create(int32_t n, const slt_mesh* meshes, const slt_schedule* sche
   }
   group_build(g.get());
   *out = g.release();
+  API_END
+}
+
+int slt_group_create_batched(int32_t n, const slt_mesh* meshes, const slt_schedule* scheds, const int32_t* nshots,
+                             const double* const* src_xy, slt_group* out) {
+  API_BEGIN
+  REQUIRE(out, "null argument");
+  *out = nullptr;
+  REQUIRE(n >= 1 && n <= 256, "n must be in 1..256");
+  REQUIRE(meshes && scheds && nshots, "null argument");
+  std::set<slt_mesh> seen;
+  std::unique_ptr<slt_group_s> g(new slt_group_s());
+  g->mixed = true;
+  for (int32_t i = 0; i < n; ++i) {
+    REQUIRE(meshes[i], "null mesh");
+    REQUIRE(seen.insert(meshes[i]).second, "a mesh appears twice");
+    REQUIRE(nshots[i] >= 1 && nshots[i] <= 4096, "nshots must be in 1..4096");
+    if (scheds[i] && scheds[i]->mesh != meshes[i])
+      fail(SLT_ERR_STATE, "a schedule was not inspected on its mesh's chain");
+    if (nshots[i] > 1 && !(scheds[i] && scheds[i]->executor == 0))
+      fail(SLT_ERR_UNSUPPORTED, "a member with several shots needs a schedule with the dataflow executor");
+    g->meshes.push_back(meshes[i]);
+    g->scheds.push_back(scheds[i]);
+    g->nshots.push_back(nshots[i]);
+  }
+  g->src_w.resize(n);
+  g->src.resize(n);
+  for (int32_t i = 0; i < n; ++i)
+    if (nshots[i] > 1) shot_sources(meshes[i], nshots[i], src_xy ? src_xy[i] : nullptr, g->src_w[i], g->src[i], nullptr);
+  SLT_CUDA(cudaDeviceSynchronize());
+  group_build(g.get());
+  *out = g.release();
+  API_END
+}
+
+int slt_group_graph_replays(slt_group g, int64_t* replays) {
+  API_BEGIN
+  REQUIRE(g && replays, "null argument");
+  *replays = g->graph_launches;
   API_END
 }
 

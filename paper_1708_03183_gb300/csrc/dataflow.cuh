@@ -191,6 +191,46 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
   }
 }
 
+// One queue over the tiles of meshes of several degrees, single-field or many-shot: the batched
+// form as one persistent launch.  Each tile runs the phase bodies of its mesh's degree (Params.p)
+// and layout (Params.S shots innermost when above 1, every shot of the tile's items in the tile);
+// the kernel holds the bodies of degrees 1 to 3 and takes the registers of the largest.
+template <int BS>
+__global__ void __launch_bounds__(BS, 2) k_dataflow_mixed(DFM df) {
+  __shared__ long long s_node;
+  __shared__ Params sp;
+  static_assert(sizeof(Params) % 4 == 0, "Params is copied as 32-bit words");
+  for (;;) {
+    if (threadIdx.x == 0) s_node = df_take(df.q);
+    __syncthreads();
+    const long long node = s_node;
+    if (node < 0) return;
+    const long long st = node / df.q.G;
+    const int g = (int)(node % df.q.G);
+    int lo = 0, hi = df.K;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (df.cum[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    const int k = lo;
+    const int32_t* src = reinterpret_cast<const int32_t*>(&df.params[df.mesh_of[k]]);
+    int32_t* dst = reinterpret_cast<int32_t*>(&sp);
+    for (int i = threadIdx.x; i < (int)(sizeof(Params) / 4); i += BS) dst[i] = src[i];
+    __syncthreads();
+    const int t = g - df.cum[k], f = df.first[k], l = df.last[k];
+    switch (sp.p * 2 + (sp.S > 1 ? 1 : 0)) {
+      case 2: run_tile<1, BS, false>(sp, f, l, t, st); break;
+      case 3: run_tile<1, BS, true>(sp, f, l, t, st); break;
+      case 4: run_tile<2, BS, false>(sp, f, l, t, st); break;
+      case 5: run_tile<2, BS, true>(sp, f, l, t, st); break;
+      case 6: run_tile<3, BS, false>(sp, f, l, t, st); break;
+      default: run_tile<3, BS, true>(sp, f, l, t, st); break;
+    }
+    if (threadIdx.x < 32) df_publish(df.q, g, st);
+  }
+}
+
 // The same executor with one thread-block cluster per tile (large tiles, few boundary cells):
 // the cluster's CTAs share each segment's items of the tile, separated by a cluster barrier.  The
 // leader CTA's first thread takes nodes from the queue and publishes their successors; the node

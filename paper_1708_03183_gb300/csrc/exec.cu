@@ -54,6 +54,7 @@ __global__ void k_step_inc(long long* step) { *step += 1; }
 
 #include "dataflow.cuh"
 #include "staged.cuh"
+#include "layout.cuh"
 
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every segment of the
 // sub-chain [first, last) in order, segments separated by a CTA barrier.
@@ -496,6 +497,96 @@ void op_E(slt_mesh m, const double* in2, double* out3, cudaStream_t s) {
   }
 }
 
+namespace {
+// caller cells [c0, c1) <-> work layout, one caller row block per cell (the pipelined host path
+// converts each chunk as soon as it has arrived)
+__global__ void k_to_work_cells(const double* __restrict__ in, int rows, const int32_t* __restrict__ iperm, int64_t c0,
+                                int64_t c1, int64_t ncp, double* __restrict__ out) {
+  const int64_t n = (c1 - c0) * rows;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + i / rows, q = i % rows;
+    out[q * ncp + iperm[c]] = in[c * rows + q];
+  }
+}
+__global__ void k_from_work_cells(const double* __restrict__ in, int rows, const int32_t* __restrict__ iperm,
+                                  int64_t c0, int64_t c1, int64_t ncp, double* __restrict__ out) {
+  const int64_t n = (c1 - c0) * rows;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + i / rows, q = i % rows;
+    out[c * rows + q] = in[q * ncp + iperm[c]];
+  }
+}
+}  // namespace
+
+// Host fields: the copies overlap the layout conversion.  The fields go over in kHostChunks
+// chunks of cells on a copy stream; each chunk is converted into the work layout on the
+// compute stream as soon as its copy has finished, while the next chunk is on the link; the
+// result comes back the same way (convert a chunk, copy it while the next converts).
+void exec_run_host(slt_mesh m, slt_schedule sched, double* hv, double* hs, const double* hr, double dt,
+                   int64_t nsteps, cudaStream_t s) {
+  constexpr int kHostChunks = 4;
+  g_rec = Recorder();
+  const int Np = m->Np;
+  const int64_t nc = m->nc, nv = nc * 2 * Np, ns = nc * 3 * Np;
+  if (m->io_v.n < (size_t)nv) m->io_v.alloc(nv);
+  if (m->io_s.n < (size_t)ns) m->io_s.alloc(ns);
+  if (hr && m->ricker_buf.n < (size_t)std::max<int64_t>(nsteps, 1)) m->ricker_buf.alloc(std::max<int64_t>(nsteps, 1));
+  if (!m->copy) SLT_CUDA(cudaStreamCreateWithFlags(&m->copy, cudaStreamNonBlocking));
+  cudaStream_t cs = m->copy;
+  cudaEvent_t ev[2 * kHostChunks + 1];
+  for (auto& e : ev) SLT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  Params a = make_params(m);
+  a.dt = dt;
+  a.c24 = dt * dt / 24.0;
+  a.ricker = hr ? m->ricker_buf.p : nullptr;
+  auto chunk = [&](int k, int64_t& c0, int64_t& c1) {
+    c0 = nc * k / kHostChunks;
+    c1 = nc * (k + 1) / kHostChunks;
+  };
+  SLT_CUDA(cudaEventRecord(ev[2 * kHostChunks], s));  // the copies start after earlier work on s
+  SLT_CUDA(cudaStreamWaitEvent(cs, ev[2 * kHostChunks], 0));
+  if (hr) SLT_CUDA(cudaMemcpyAsync(m->ricker_buf.p, hr, nsteps * sizeof(double), cudaMemcpyHostToDevice, cs));
+  for (int k = 0; k < kHostChunks; ++k) {
+    int64_t c0, c1;
+    chunk(k, c0, c1);
+    SLT_CUDA(cudaMemcpyAsync(m->io_v.p + c0 * 2 * Np, hv + c0 * 2 * Np, (c1 - c0) * 2 * Np * sizeof(double),
+                             cudaMemcpyHostToDevice, cs));
+    SLT_CUDA(cudaMemcpyAsync(m->io_s.p + c0 * 3 * Np, hs + c0 * 3 * Np, (c1 - c0) * 3 * Np * sizeof(double),
+                             cudaMemcpyHostToDevice, cs));
+    SLT_CUDA(cudaEventRecord(ev[k], cs));
+    SLT_CUDA(cudaStreamWaitEvent(s, ev[k], 0));
+    int g;
+    io_grid((c1 - c0) * 3 * Np, g);
+    k_to_work_cells<<<g, 256, 0, s>>>(m->io_v.p, 2 * Np, m->d_iperm.p, c0, c1, m->ncp, a.buf[B_V]);
+    k_to_work_cells<<<g, 256, 0, s>>>(m->io_s.p, 3 * Np, m->d_iperm.p, c0, c1, m->ncp, a.buf[B_S]);
+  }
+  SLT_CUDA(cudaGetLastError());
+  switch (m->p) {
+    case 1: run_steps<1>(m, sched, a, nsteps, s); break;
+    case 2: run_steps<2>(m, sched, a, nsteps, s); break;
+    case 3: run_steps<3>(m, sched, a, nsteps, s); break;
+    case 4: run_steps<4>(m, sched, a, nsteps, s); break;
+  }
+  for (int k = 0; k < kHostChunks; ++k) {
+    int64_t c0, c1;
+    chunk(k, c0, c1);
+    int g;
+    io_grid((c1 - c0) * 3 * Np, g);
+    k_from_work_cells<<<g, 256, 0, s>>>(a.buf[B_V], 2 * Np, m->d_iperm.p, c0, c1, m->ncp, m->io_v.p);
+    k_from_work_cells<<<g, 256, 0, s>>>(a.buf[B_S], 3 * Np, m->d_iperm.p, c0, c1, m->ncp, m->io_s.p);
+    SLT_CUDA(cudaEventRecord(ev[kHostChunks + k], s));
+    SLT_CUDA(cudaStreamWaitEvent(cs, ev[kHostChunks + k], 0));
+    SLT_CUDA(cudaMemcpyAsync(hv + c0 * 2 * Np, m->io_v.p + c0 * 2 * Np, (c1 - c0) * 2 * Np * sizeof(double),
+                             cudaMemcpyDeviceToHost, cs));
+    SLT_CUDA(cudaMemcpyAsync(hs + c0 * 3 * Np, m->io_s.p + c0 * 3 * Np, (c1 - c0) * 3 * Np * sizeof(double),
+                             cudaMemcpyDeviceToHost, cs));
+  }
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(cs));
+  SLT_CUDA(cudaStreamSynchronize(s));
+  for (auto& e : ev) cudaEventDestroy(e);
+}
+
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile) {
   g_rec = Recorder();
@@ -534,7 +625,7 @@ void group_build(slt_group grp) {
   std::map<int, std::vector<int32_t>> by_degree;
   for (size_t i = 0; i < grp->meshes.size(); ++i) {
     slt_schedule sc = grp->scheds[i];
-    if (sc && sc->executor == 0) by_degree[grp->meshes[i]->p].push_back((int32_t)i);
+    if (sc && sc->executor == 0) by_degree[grp->mixed ? 0 : grp->meshes[i]->p].push_back((int32_t)i);
     else grp->untiled.push_back((int32_t)i);  // untiled, or the colour-phase or cluster executor
   }
   for (auto& kv : by_degree) {
@@ -548,6 +639,8 @@ void group_build(slt_group grp) {
     for (size_t mi = 0; mi < part.members.size(); ++mi) {
       slt_schedule sc = grp->scheds[part.members[mi]];
       if (sc->block != part.block) fail(SLT_ERR_UNSUPPORTED, "tiled meshes of one degree need one block size");
+      if (grp->mixed && (sc->block != 256 || grp->meshes[part.members[mi]]->p > 3))
+        fail(SLT_ERR_UNSUPPORTED, "one launch over all degrees takes degrees 1-3 and 256-thread tiles");
       if (sc->block > 384) fail(SLT_ERR_UNSUPPORTED, "group members take 128-384-thread tiles");
       part.wait_spins = std::max<int64_t>(part.wait_spins, sc->wait_spins);
       const DataflowPlan& D = sc->df;
@@ -602,7 +695,7 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
   q.total = (long long)nsteps * part.G;
   if (q.total == 0) return;
   if (q.total >= (1ll << 31)) fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
-  if (part.pending.n < (size_t)q.total) {
+  if (part.pending.n < (size_t)q.total) {  // (allocated ahead of a captured run: group_run_mixed)
     part.pending.alloc(q.total);
     part.queue.alloc(q.total);
   }
@@ -636,7 +729,8 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
     const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), q.total);
     kernel<<<(unsigned)grid, threads, 0, s>>>(df);
   };
-  if (part.block == 128) launch(k_dataflow_group<P, 128>, 128);
+  if constexpr (P == 0) launch(k_dataflow_mixed<256>, 256);
+  else if (part.block == 128) launch(k_dataflow_group<P, 128>, 128);
   else if (part.block == 384) launch(k_dataflow_group<P, 384>, 384);
   else launch(k_dataflow_group<P, 256>, 256);
   SLT_CUDA(cudaGetLastError());
@@ -647,8 +741,15 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
 // One call: every member's fields into its work layout; each degree's tiled members as one
 // persistent kernel over their combined queue (one degree after the other, each with the whole
 // GPU); the untiled members side by side on private streams; fields back.
+void group_run_mixed(slt_group grp, double* const* v, double* const* sigma, const double* const* ricker,
+                     const double* dt, int64_t nsteps, cudaStream_t s);
+
 void group_run(slt_group grp, double* const* v, double* const* sigma, const double* const* ricker, const double* dt,
                int64_t nsteps, cudaStream_t s) {
+  if (grp->mixed) {
+    group_run_mixed(grp, v, sigma, ricker, dt, nsteps, s);
+    return;
+  }
   g_rec = Recorder();
   const int32_t n = (int32_t)grp->meshes.size();
   std::vector<Params> prm(n);
@@ -727,6 +828,166 @@ void group_run(slt_group grp, double* const* v, double* const* sigma, const doub
     k_from_work<<<g, 256, 0, s>>>(prm[i].buf[B_S], 3 * m->Np, m->d_perm.p, m->nc, m->ncp, sigma[i]);
   }
   SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(s));
+  for (auto& part : grp->parts) {
+    int32_t herr = 0;
+    SLT_CUDA(cudaMemcpy(&herr, part.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr && nsteps > 0) fail(SLT_ERR_TIMEOUT, "a wait of the dataflow executor gave up");
+  }
+}
+
+// The batched form in one launch: every tiled member (any degree 1-3, one field or many shots)
+// runs from one ready queue in one persistent kernel.  The fields' conversion into the work
+// layout, the queue reset and seeding, the persistent kernel and the conversion back are
+// captured once as a CUDA graph and replayed while nsteps and the field pointers stay the same
+// (the parameter blocks, with the source series and time steps, are uploaded before each replay).
+// Untiled members run afterwards as in group_run.
+void group_run_mixed(slt_group grp, double* const* v, double* const* sigma, const double* const* ricker,
+                     const double* dt, int64_t nsteps, cudaStream_t s) {
+  g_rec = Recorder();
+  const int32_t n = (int32_t)grp->meshes.size();
+  std::vector<Params> prm(n);
+  for (int32_t i = 0; i < n; ++i) {
+    slt_mesh m = grp->meshes[i];
+    const int32_t S = grp->nshots[i];
+    Params& a = prm[i];
+    if (S > 1) {
+      const int64_t fs = m->ncp * S, need = 15 * m->Np * fs;
+      if (m->work_b.n < (size_t)need) {
+        m->work_b.alloc(need);
+        SLT_CUDA(cudaMemsetAsync(m->work_b.p, 0, need * sizeof(double), s));
+      }
+      a = make_params(m);
+      double* base = m->work_b.p;
+      const int64_t Np = m->Np;
+      a.buf[B_V] = base;
+      a.buf[B_S] = base + 2 * Np * fs;
+      a.buf[B_U1] = base + 5 * Np * fs;
+      a.buf[B_U2] = base + 7 * Np * fs;
+      a.buf[B_E] = base + 9 * Np * fs;
+      a.buf[B_S1] = base + 12 * Np * fs;
+      a.src = nullptr;
+      a.src_w = -1;
+      a.S = S;
+      a.s0 = 0;
+      a.sg = S;
+      a.fs = fs;
+      a.src_wb = grp->src_w[i].p;
+      a.src_b = grp->src[i].p;
+    } else {
+      a = make_params(m);
+    }
+    a.p = m->p;
+    a.dt = dt[i];
+    a.c24 = dt[i] * dt[i] / 24.0;
+    a.ricker = ricker[i];
+    if (slt_schedule sc = grp->scheds[i])
+      for (auto& sub : sc->subs)
+        for (int j = sub.first; j < sub.last; ++j) {
+          a.plan_ptr[j] = sub.plan_ptr[j - sub.first].p;
+          a.plan_items[j] = sub.plan_items[j - sub.first].p;
+        }
+  }
+  std::vector<int32_t> tiled;
+  for (auto& part : grp->parts) {
+    std::vector<Params> pp;
+    for (int32_t i : part.members) {
+      pp.push_back(prm[i]);
+      tiled.push_back(i);
+    }
+    SLT_CUDA(cudaMemcpyAsync(part.params.p, pp.data(), pp.size() * sizeof(Params), cudaMemcpyHostToDevice, s));
+    const long long total = (long long)nsteps * part.G;
+    if (total >= (1ll << 31)) fail(SLT_ERR_UNSUPPORTED, "steps x tiles must stay below 2^31");
+    if (part.pending.n < (size_t)total) {
+      part.pending.alloc(total);
+      part.queue.alloc(total);
+    }
+  }
+  auto convert = [&](cudaStream_t st, bool in) {
+    for (int32_t i : tiled) {
+      slt_mesh m = grp->meshes[i];
+      const int32_t S = grp->nshots[i];
+      const int Np = m->Np;
+      int g;
+      io_grid(m->nc * (S > 1 ? 5 * Np * S : 1), g);
+      if (S > 1) {
+        if (in) {
+          k_to_work_b<<<g, 256, 0, st>>>(v[i], 2 * Np, S, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_V]);
+          k_to_work_b<<<g, 256, 0, st>>>(sigma[i], 3 * Np, S, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_S]);
+        } else {
+          k_from_work_b<<<g, 256, 0, st>>>(prm[i].buf[B_V], 2 * Np, S, m->d_perm.p, m->nc, m->ncp, v[i]);
+          k_from_work_b<<<g, 256, 0, st>>>(prm[i].buf[B_S], 3 * Np, S, m->d_perm.p, m->nc, m->ncp, sigma[i]);
+        }
+      } else if (in) {
+        k_to_work<<<g, 256, 0, st>>>(v[i], 2 * Np, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_V]);
+        k_to_work<<<g, 256, 0, st>>>(sigma[i], 3 * Np, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_S]);
+      } else {
+        k_from_work<<<g, 256, 0, st>>>(prm[i].buf[B_V], 2 * Np, m->d_perm.p, m->nc, m->ncp, v[i]);
+        k_from_work<<<g, 256, 0, st>>>(prm[i].buf[B_S], 3 * Np, m->d_perm.p, m->nc, m->ncp, sigma[i]);
+      }
+    }
+  };
+  if (!tiled.empty()) {
+    std::vector<const void*> key = {reinterpret_cast<const void*>(nsteps)};
+    for (int32_t i : tiled) {
+      key.push_back(v[i]);
+      key.push_back(sigma[i]);
+    }
+    if (!grp->graph || key != grp->graph_key) {
+      if (grp->graph) {
+        cudaGraphExecDestroy(grp->graph);
+        grp->graph = nullptr;
+      }
+      if (!grp->capture) SLT_CUDA(cudaStreamCreateWithFlags(&grp->capture, cudaStreamNonBlocking));
+      SLT_CUDA(cudaStreamSynchronize(s));  // the parameter uploads are on s
+      cudaGraph_t graph = nullptr;
+      SLT_CUDA(cudaStreamBeginCapture(grp->capture, cudaStreamCaptureModeThreadLocal));
+      try {
+        convert(grp->capture, true);
+        for (auto& part : grp->parts) {
+          switch (part.p) {
+            case 0: launch_group_part<0>(part, nsteps, grp->capture); break;
+            case 1: launch_group_part<1>(part, nsteps, grp->capture); break;
+            case 2: launch_group_part<2>(part, nsteps, grp->capture); break;
+            case 3: launch_group_part<3>(part, nsteps, grp->capture); break;
+            default: launch_group_part<4>(part, nsteps, grp->capture); break;
+          }
+        }
+        convert(grp->capture, false);
+        SLT_CUDA(cudaGetLastError());
+      } catch (...) {
+        cudaStreamEndCapture(grp->capture, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      SLT_CUDA(cudaStreamEndCapture(grp->capture, &graph));
+      cudaError_t e = cudaGraphInstantiate(&grp->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      SLT_CUDA(e);
+      grp->graph_key = key;
+      grp->graph_launches = 0;
+    }
+    SLT_CUDA(cudaGraphLaunch(grp->graph, s));
+    ++grp->graph_launches;
+  }
+  if (!grp->untiled.empty()) {
+    for (int32_t i : grp->untiled) {
+      slt_mesh m = grp->meshes[i];
+      int g;
+      io_grid(m->nc, g);
+      k_to_work<<<g, 256, 0, s>>>(v[i], 2 * m->Np, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_V]);
+      k_to_work<<<g, 256, 0, s>>>(sigma[i], 3 * m->Np, m->d_perm.p, m->nc, m->ncp, prm[i].buf[B_S]);
+      switch (m->p) {
+        case 1: run_steps<1>(m, grp->scheds[i], prm[i], nsteps, s); break;
+        case 2: run_steps<2>(m, grp->scheds[i], prm[i], nsteps, s); break;
+        case 3: run_steps<3>(m, grp->scheds[i], prm[i], nsteps, s); break;
+        case 4: run_steps<4>(m, grp->scheds[i], prm[i], nsteps, s); break;
+      }
+      k_from_work<<<g, 256, 0, s>>>(prm[i].buf[B_V], 2 * m->Np, m->d_perm.p, m->nc, m->ncp, v[i]);
+      k_from_work<<<g, 256, 0, s>>>(prm[i].buf[B_S], 3 * m->Np, m->d_perm.p, m->nc, m->ncp, sigma[i]);
+    }
+    SLT_CUDA(cudaGetLastError());
+  }
   SLT_CUDA(cudaStreamSynchronize(s));
   for (auto& part : grp->parts) {
     int32_t herr = 0;

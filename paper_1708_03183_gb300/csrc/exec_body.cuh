@@ -75,6 +75,7 @@ struct Params {
   const int32_t* src_wb;            // [S] source cell of every shot
   const double* src_b;              // [S][Np] source coefficients of every shot
   double* e5;                       // if set, phase 5 accumulates its strain here instead of buf[B_E]
+  int32_t p;                        // degree (read by the kernels that serve meshes of several degrees)
 };
 
 // one (cell, shot) work item: c = cell work id, f = field column, s = shot

@@ -264,8 +264,10 @@ struct slt_mesh_s {
   slt::DevBuf<int32_t> bsrc_w;       // per-shot source cell (work id, -1 = none)
   slt::DevBuf<long long> step_dev;   // step counter read by graph-captured untiled steps
   cudaStream_t capture = nullptr;    // private stream the untiled step is captured on
+  cudaStream_t copy = nullptr;       // private stream of the host-field copies (slt_execute_host)
   ~slt_mesh_s() {
     if (capture) cudaStreamDestroy(capture);
+    if (copy) cudaStreamDestroy(copy);
   }
 };
 
@@ -287,6 +289,21 @@ struct slt_group_s {
   std::vector<slt_schedule> scheds;
   std::vector<Part> parts;
   std::vector<int32_t> untiled;
+  // one launch over all degrees (slt_group_create_batched): members with several shots (fields
+  // with the shots innermost) and their sources; the tiled part captured as a CUDA graph,
+  // replayed while the step count and the field pointers stay the same
+  bool mixed = false;
+  std::vector<int32_t> nshots;                 // per member (1 = one field)
+  std::vector<slt::DevBuf<int32_t>> src_w;     // per member: source cell of every shot (work id)
+  std::vector<slt::DevBuf<double>> src;        // per member: source coefficients [S][Np]
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> graph_key;
+  cudaStream_t capture = nullptr;
+  int64_t graph_launches = 0;                  // replays of the cached graph (for tests)
+  ~slt_group_s() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (capture) cudaStreamDestroy(capture);
+  }
 };
 
 struct slt_receivers_s {
@@ -303,6 +320,9 @@ void upload_constants(const RefElem& r);
 void build_pre(slt_mesh m, cudaStream_t s);
 void exec_run(slt_mesh m, slt_schedule sched, double* v, double* sigma, const double* ricker, double dt,
               int64_t nsteps, cudaStream_t s, double* profile = nullptr);
+// the same with host fields and source series: copies overlapped with the layout conversion
+void exec_run_host(slt_mesh m, slt_schedule sched, double* hv, double* hs, const double* hr, double dt,
+                   int64_t nsteps, cudaStream_t s);
 void group_build(slt_group g);
 void group_run(slt_group g, double* const* v, double* const* sigma, const double* const* ricker, const double* dt,
                int64_t nsteps, cudaStream_t s);
