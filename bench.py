@@ -86,7 +86,7 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "internal.h")
+KERNEL_SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "staged.cuh", "internal.h")
 
 
 def source_digest(texts):
@@ -542,6 +542,7 @@ def fp64_peak(slt, reps=20):
         for _ in range(reps):
             runs.append(slt.slt_fp64_peak())
     best = {k: max(r[k] for r in runs) for k in ("dfma_tflops", "dmma_tflops", "mixed_tflops")}
+    best["lanes"] = slt.slt_fp64_lane_probe()   # warp instructions per clock per SM
     best["clocks"] = clk.summary()
     best["nominal_dfma_tflops"] = FP64_PEAK_TFLOPS
     best["dfma_per_clk_per_sm"] = best["dfma_tflops"] * 1e12 / 2 / 152 / (best["clocks"]["sm_mhz"] or 2070.0) / 1e6
@@ -584,6 +585,7 @@ def main():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-p4", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
+    ap.add_argument("--no-staged", action="store_true")
     ap.add_argument("--p4-steps", type=int, default=200)
     ap.add_argument("--multi-steps", type=int, default=200)
     ap.add_argument("--shots", type=int, default=64)
@@ -641,6 +643,8 @@ def main():
                             block_threads=args.block, cluster_size=args.cluster_size)
     inspect_s = time.perf_counter() - t0
     subs = [slt.slt_schedule_info(sched, k) for k in range(2)]
+    insp_stages = slt.slt_schedule_inspection_times(sched)
+    lanes = slt.slt_schedule_lane_info(sched)
 
     ricker = torch.tensor(cfg["ricker"], device="cuda")
     units_per_step = 5 * Np * nc
@@ -686,6 +690,12 @@ def main():
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "tiles": [s["ntiles"] for s in subs], "colours": [s["ncolours"] for s in subs],
                       "restarts": [s["restarts"] for s in subs], "inspection_s": inspect_s,
+                      "inspection_stages_s": insp_stages,
+                      "fp64_lane_efficiency": {"tiled": lanes["dataflow_efficiency"],
+                                               "staged_passes": lanes["staged_efficiency"],
+                                               "untiled": lanes["untiled_efficiency"],
+                                               "how": "slt_schedule_lane_info: FP64 warp-lane instructions "
+                                                      "a step needs over those its warps issue"},
                       "executor": ["dataflow", "colour phases", "dataflow, tile clusters of %d CTAs" % args.cluster_size,
                                    "staged dataflow (tiles out of shared memory)"][args.executor],
                       "block_threads": args.block},
@@ -731,6 +741,21 @@ def main():
                           if args.scale == 1 else None,
                           "clocks": cclk}
         del csched
+
+    if not args.no_staged and args.executor == 0:
+        # the same workload with every tile run out of shared memory (executor 3): the DRAM bytes
+        # it saves, and what its one CTA per SM costs on this FP64-bound part
+        ssched = slt.slt_inspect(chain, tile_size=256, split=(9,), executor=3, block_threads=384)
+        sms, sprof, sclk = timed(ssched, k_untiled, args.warmup)
+        sk = sprof["chain_ms"] * 1e-3
+        out["staged"] = {"executor": "staged dataflow, tiles out of shared memory, ts 256, 384 threads",
+                         "value": whole_job_rate(units_per_step * k_untiled, world, sms * 1e-3),
+                         "ms_per_step": sms / k_untiled, "steps": k_untiled,
+                         "roofline_frac_fp64": flops * k_untiled / sk / 1e12 / FP64_PEAK_TFLOPS,
+                         "traffic": ncu_traffic("k_staged<2,384>", "large_ts256", k_untiled)
+                         if args.scale == 1 else None,
+                         "clocks": sclk}
+        del ssched
 
     if not args.no_untiled:
         K = k_untiled

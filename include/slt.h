@@ -147,6 +147,22 @@ int slt_schedule_info(slt_schedule sched, int32_t subchain, int64_t info[8]);
    [3] node times however many tiles are in flight; it reaches the work bound only when
    [0] / [5] is well above [3].  SLT_ERR_ARG for a schedule without an executor plan. */
 int slt_schedule_dataflow_info(slt_schedule sched, double info[6]);
+/* FP64 lane accounting of one time step of the schedule's plans (schedules inspected on
+   slt_mesh_chain), in warp-lane FP64 instructions, counted from the part functions' instruction
+   counts at the mesh's degree: info[0] what the step needs (every item's parts), info[1] what the
+   dataflow executors issue (warps of 32 consecutive plan items of a tile; a warp issues a part when
+   any of its lanes has it, so idle lanes count), info[2] what the staged executor's compacted
+   passes issue (each pass padded to whole warps), info[3] what the untiled chain issues (every
+   cell, warps of 32 consecutive cells).  info[0] / info[1] is the lane efficiency of the tiled
+   executors; the FP64 pipe spends a full issue slot on a warp instruction whatever its active
+   lanes.  Synchronises. */
+int slt_schedule_lane_info(slt_schedule sched, double info[4]);
+/* Wall seconds slt_inspect spent per stage, each ended by a stream synchronisation: [0] seed
+   partition (Hilbert ranks), [1] colouring, projections, tiling functions and conflict repair
+   (Algorithms 1-3, every restart included), [2] iteration lists and local maps, [3] the executor
+   plans, [4] the staged executor's plans, [5] the dataflow dependency graph, [6..7] zero.  Summed
+   over the sub-chains. */
+int slt_schedule_inspection_times(slt_schedule sched, double seconds[8]);
 /* Copy one integer array of the schedule to host memory.  Call with host_out = NULL to get
    the length in *n.  kind:
      0 rank of every seed element            (loop, desc ignored)
@@ -391,6 +407,11 @@ int slt_adjoint_batched(slt_mesh mesh, slt_schedule sched, slt_receivers rec, in
  * instruction; 4 independent accumulators per warp), out[2] = both issued at once (half the warps
  * each, equal flops), out[3] = total ms of the three timed launches.  Allocates nothing. */
 int slt_fp64_peak(void* stream, double out[4]);
+/* How the FP64 pipe treats partial and few warps (the paper has no counterpart; the executors'
+   design rests on these two facts): DFMA warp instructions per clock per SM (maximum clock) with
+   out[0] 32 active lanes per warp, out[1] 16 active lanes, out[2] one warp per SM, out[3] four
+   warps per SM.  Allocates nothing; synchronises. */
+int slt_fp64_lane_probe(void* stream, double out[4]);
 
 /* ------------------------------------------------------------------ allocation-free ranking
  * The paper has no counterpart to this entry point: it serves callers who cannot allocate

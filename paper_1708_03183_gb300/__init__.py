@@ -45,6 +45,8 @@ _SIGS = {
     "slt_schedule_destroy": (ctypes.c_int, [P]),
     "slt_schedule_info": (ctypes.c_int, [P, I32, P]),
     "slt_schedule_dataflow_info": (ctypes.c_int, [P, P]),
+    "slt_schedule_lane_info": (ctypes.c_int, [P, P]),
+    "slt_schedule_inspection_times": (ctypes.c_int, [P, P]),
     "slt_schedule_export": (ctypes.c_int, [P, I32, I32, I32, P, P]),
     "slt_mesh_create": (ctypes.c_int, [P, P, I64, I32, P, P, P, P, P, P]),
     "slt_mesh_destroy": (ctypes.c_int, [P]),
@@ -65,6 +67,7 @@ _SIGS = {
     "slt_apply_operator": (ctypes.c_int, [P, I32, P, P, P]),
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_fp64_peak": (ctypes.c_int, [P, P]),
+    "slt_fp64_lane_probe": (ctypes.c_int, [P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
     "slt_mesh_set_source": (ctypes.c_int, [P, P, P]),
     "slt_receivers_create": (ctypes.c_int, [P, I32, P, P]),
@@ -231,6 +234,24 @@ def slt_schedule_dataflow_info(sched):
     return dict(zip(keys, (float(x) for x in info)))
 
 
+def slt_schedule_lane_info(sched):
+    """FP64 warp-lane instructions of one step: needed, issued by the dataflow executors, by the
+    staged executor's passes, by the untiled chain."""
+    info = np.zeros(4, dtype=np.float64)
+    _check(lib.slt_schedule_lane_info(sched.ptr, ctypes.c_void_p(info.ctypes.data)))
+    return dict(needed=float(info[0]), dataflow=float(info[1]), staged=float(info[2]), untiled=float(info[3]),
+                dataflow_efficiency=float(info[0] / info[1]), staged_efficiency=float(info[0] / info[2]),
+                untiled_efficiency=float(info[0] / info[3]))
+
+
+def slt_schedule_inspection_times(sched):
+    """Seconds of slt_inspect per stage."""
+    t = np.zeros(8, dtype=np.float64)
+    _check(lib.slt_schedule_inspection_times(sched.ptr, ctypes.c_void_p(t.ctypes.data)))
+    return dict(partition=float(t[0]), colour_project_tile=float(t[1]), lists_local_maps=float(t[2]),
+                executor_plans=float(t[3]), staged_plans=float(t[4]), dataflow_graph=float(t[5]))
+
+
 EXPORT_KINDS = {"rank": 0, "colour": 1, "sigma": 2, "list_ptr": 3, "list": 4, "fp_ptr": 5, "fp": 6, "lmap": 7,
                 "succ_ptr": 8, "succ": 9, "indeg0": 10, "indeg": 11, "fp_stage_ptr": 12, "fp_stage": 13}
 
@@ -278,6 +299,14 @@ def slt_fp64_peak(stream=None):
     o = np.zeros(4, dtype=np.float64)
     _check(lib.slt_fp64_peak(_stream(stream), ctypes.c_void_p(o.ctypes.data)))
     return dict(dfma_tflops=float(o[0]), dmma_tflops=float(o[1]), mixed_tflops=float(o[2]), probe_ms=float(o[3]))
+
+
+def slt_fp64_lane_probe(stream=None):
+    """DFMA warp instructions per clock per SM: 32 lanes, 16 lanes, one warp per SM, four warps per SM."""
+    o = np.zeros(4, dtype=np.float64)
+    _check(lib.slt_fp64_lane_probe(_stream(stream), ctypes.c_void_p(o.ctypes.data)))
+    return dict(full_warps=float(o[0]), half_warps=float(o[1]), one_warp_per_sm=float(o[2]),
+                four_warps_per_sm=float(o[3]))
 
 
 def slt_mesh_chain(mesh):

@@ -296,6 +296,21 @@ int slt_schedule_dataflow_info(slt_schedule s, double info[6]) {
   API_END
 }
 
+int slt_schedule_inspection_times(slt_schedule s, double seconds[8]) {
+  API_BEGIN
+  REQUIRE(s && seconds, "null argument");
+  for (int k = 0; k < 8; ++k) seconds[k] = s->insp_s[k];
+  API_END
+}
+
+int slt_schedule_lane_info(slt_schedule s, double info[4]) {
+  API_BEGIN
+  REQUIRE(s && info, "null argument");
+  REQUIRE(s->mesh && !s->df.cum.empty(), "the schedule has no executor plan (not inspected on a mesh chain)");
+  lane_info(s, s->mesh, info);
+  API_END
+}
+
 int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc, int32_t* host_out, int64_t* n) {
   API_BEGIN
   REQUIRE(s && n, "null argument");

@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <map>
 #include <set>
 #include <utility>
@@ -592,6 +594,15 @@ void build_plan(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t s
 }
 
 void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out) {
+  // wall time of each stage (the stages end with a stream synchronisation)
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto lap = [&](std::chrono::steady_clock::time_point& t0, int k) {
+    SLT_CUDA(cudaStreamSynchronize(s));
+    const auto t1 = now();
+    out->insp_s[k] += std::chrono::duration<double>(t1 - t0).count();
+    t0 = t1;
+  };
+  auto t0 = now();
   Ctx X{c, &opt, s, {}, {}};
   X.dmaps.resize(c->maps.size());
   for (size_t k = 0; k < c->maps.size(); ++k) {
@@ -628,6 +639,7 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
       }
       seed_rank(xy.p, nseed, opt.renumber, sub.rank.p, s);
     }
+    lap(t0, 0);
     sub.sigma.resize(nl);
     for (int jj = 0; jj < nl; ++jj) sub.sigma[jj].alloc(std::max<int64_t>(c->set_size[c->loops[sub.first + jj].set], 1));
     k_div<<<grid_for(nseed), 256, 0, s>>>(sub.rank.p, nseed, ts, sub.sigma[sl].p);
@@ -720,6 +732,7 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
         fell_back = true;
     }
     sub.fell_back = fell_back;
+    lap(t0, 1);
     {
       std::vector<int32_t> hc = sub.colour.download(s, m);
       int32_t nc = 0;
@@ -738,7 +751,9 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
       for (size_t d = 0; d < L.descs.size(); ++d)
         if (L.descs[d].map >= 0) export_local_map(X, L.descs[d].map, sub.sigma[jj].p, n, m, sub.lmaps[jj][d]);
     }
+    lap(t0, 2);
     if (c->mesh) build_plan(out, c->mesh, sub, s);
+    lap(t0, 3);
     if (c->mesh && out->executor == 3) {
       stage_build(out, c->mesh, sub, s);
       const int32_t cap = stage_capacity(c->mesh->p);
@@ -747,8 +762,10 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
                                       " cells, more than the " + std::to_string(cap) +
                                       " its shared memory holds at this degree; use a smaller tile size");
     }
+    lap(t0, 4);
   }
   if (c->mesh) build_dataflow(out, c->mesh, s);
+  lap(t0, 5);
 }
 
 // Longest dependency chain per time step of the (step, tile) graph in the steady state: the
@@ -1246,6 +1263,109 @@ void stage_build(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t 
   SLT_CUDA(cudaMemcpyAsync(&hbad, bad.p, 4, cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaStreamSynchronize(s));
   if (hbad) fail(SLT_ERR_UNSUPPORTED, "staged plan: a facet iteration's cell is outside its tile's footprint");
+}
+
+}  // namespace slt
+
+namespace slt {
+
+// FP64 instructions per work item of each part of a phase (an instruction counts once whatever
+// its flops: the pipe takes one issue slot for each), as the part functions of the executors
+// issue them at degree p with nnz nonzeros of Dr plus Ds: [0] the first cell loop (volume part),
+// [1] an interior face, [2] a free-surface face, [3] the later cell loop.
+static void part_costs(int H, int Np, int Nfp, double nnz, double c[4]) {
+  const double volB = 8.0 * Np + 2 * nnz, volD = 2 * nnz + 8.0 * Np;
+  const double intB = 7.0 * Nfp + 2.0 * Np * Nfp, extB = 2 + 4.0 * Nfp + 2.0 * Np * Nfp;
+  const double intD = 2.0 * Nfp + 2.0 * Np * Nfp + 4.0 * Np;
+  const bool A = H == 0 || H == 2 || H == 4;
+  c[0] = H == 0 ? volB : (H == 1 || H == 3 || H == 5) ? volD : 0;
+  c[1] = A ? intB : intD;
+  c[2] = A ? extB : 0;
+  c[3] = (H == 1 || H == 3) ? 5.0 * Np + volB : H == 2 ? 4.0 * Np : H == 5 ? 11.0 * Np : 0;
+}
+
+void lane_info(slt_schedule sched, slt_mesh mesh, double out[4]) {
+  const int Np = mesh->Np, Nfp = mesh->Nfp;
+  double mx = 0, nnz = 0;
+  for (double x : mesh->ref.Dr) mx = std::max(mx, std::fabs(x));
+  for (double x : mesh->ref.Ds) mx = std::max(mx, std::fabs(x));
+  for (double x : mesh->ref.Dr) nnz += std::fabs(x) > 1e-12 * mx;
+  for (double x : mesh->ref.Ds) nnz += std::fabs(x) > 1e-12 * mx;
+  std::vector<int32_t> nbr = mesh->nbr.download(nullptr, 3 * mesh->ncp);
+  auto ext = [&](int64_t w, int f) { return nbr[f * mesh->ncp + w] < 0; };
+  double useful = 0, exec_df = 0, exec_st = 0, exec_un = 0;
+  // one item's parts, and the union over a warp of items (interior and free-surface faces apart)
+  auto item_cost = [&](int H, int64_t w, int fl, const double* c) {
+    double u = ((fl & 8) ? c[0] : 0) + ((fl & 16) ? c[3] : 0);
+    for (int f = 0; f < 3; ++f)
+      if ((fl >> f) & 1) u += ext(w, f) ? c[2] : c[1];
+    return u;
+  };
+  auto warp_cost = [&](int H, const std::vector<std::pair<int64_t, int>>& it, size_t a, size_t b, const double* c) {
+    int pa = 0, pb = 0, fi = 0, fe = 0;
+    for (size_t i = a; i < b; ++i) {
+      const int fl = it[i].second;
+      pa |= (fl >> 3) & 1;
+      pb |= (fl >> 4) & 1;
+      for (int f = 0; f < 3; ++f)
+        if ((fl >> f) & 1) {
+          if (ext(it[i].first, f)) fe |= 1 << f;
+          else fi |= 1 << f;
+        }
+    }
+    return 32.0 * (pa * c[0] + pb * c[3] + __builtin_popcount(fi) * c[1] + __builtin_popcount(fe) * c[2]);
+  };
+  for (const SubSched& sub : sched->subs) {
+    for (int J0 = sub.first; J0 < sub.last; J0 = seg_end(J0, sub.last)) {
+      const int H = phase_of(J0);
+      double c[4];
+      part_costs(H, Np, Nfp, nnz, c);
+      std::vector<int32_t> ptr = sub.plan_ptr[J0 - sub.first].download(nullptr, sub.m + 1);
+      std::vector<int32_t> items = sub.plan_items[J0 - sub.first].download(nullptr, std::max(ptr[sub.m], 1));
+      for (int32_t t = 0; t < sub.m; ++t) {
+        std::vector<std::pair<int64_t, int>> it;
+        for (int32_t i = ptr[t]; i < ptr[t + 1]; ++i) it.push_back({items[i] >> 5, items[i] & 31});
+        for (auto& x : it) useful += 32.0 * item_cost(H, x.first, x.second, c) / 32.0;
+        for (size_t a = 0; a < it.size(); a += 32) exec_df += warp_cost(H, it, a, std::min(it.size(), a + 32), c);
+        // staged passes: the first cell loop, each interior face index, the free surface, the
+        // later cell loop, each over its compacted list
+        int64_t npa = 0, npb = 0, nint[3] = {0, 0, 0}, next = 0;
+        double ext_work = 0;
+        for (auto& x : it) {
+          npa += (x.second >> 3) & 1;
+          npb += (x.second >> 4) & 1;
+          bool e = false;
+          for (int f = 0; f < 3; ++f)
+            if ((x.second >> f) & 1) {
+              if (ext(x.first, f)) e = true;
+              else ++nint[f];
+            }
+          next += e;
+        }
+        auto padded = [](int64_t n) { return (double)((n + 31) / 32 * 32); };
+        exec_st += padded(npa) * c[0] + padded(npb) * c[3] + padded(nint[0]) * c[1] + padded(nint[1]) * c[1] +
+                   padded(nint[2]) * c[1] + padded(next) * c[2] * 1.0;
+        (void)ext_work;
+      }
+    }
+  }
+  // the untiled chain: every phase over all cells, warps of 32 consecutive work ids, all parts
+  for (int H = 0; H < kPhases; ++H) {
+    double c[4];
+    part_costs(H, Np, Nfp, nnz, c);
+    for (int64_t w0 = 0; w0 < mesh->nc; w0 += 32) {
+      int fe = 0;
+      for (int64_t w = w0; w < std::min<int64_t>(mesh->nc, w0 + 32); ++w)
+        for (int f = 0; f < 3; ++f)
+          if (ext(w, f)) fe |= 1 << f;
+      const int fi = 7;  // every warp has cells with each interior face
+      exec_un += 32.0 * (c[0] + c[3] + __builtin_popcount(fi) * c[1] + __builtin_popcount(fe) * (H == 0 || H == 2 || H == 4 ? c[2] : 0));
+    }
+  }
+  out[0] = useful;
+  out[1] = exec_df;
+  out[2] = exec_st;
+  out[3] = exec_un;
 }
 
 }  // namespace slt

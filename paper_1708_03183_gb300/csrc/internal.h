@@ -216,6 +216,10 @@ struct slt_schedule_s {
   std::vector<int64_t> set_size;
   slt_mesh mesh = nullptr;
   std::vector<slt::SubSched> subs;
+  // seconds of slt_inspect per stage: seed partition, colouring with projections, tiling and
+  // conflict repair (Algorithms 1-3), iteration lists and local maps, executor plans, staged
+  // plans, dependency graph, (unused)
+  double insp_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace slt {
@@ -375,6 +379,8 @@ void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
 void stage_build(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 int32_t stage_capacity(int p);  // slots of shared memory the staged executor has per tile CTA
+// FP64 lane accounting of a schedule's plans (see slt_schedule_lane_info)
+void lane_info(slt_schedule sched, slt_mesh m, double out[4]);
 // inspect.cu
 void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_schedule out);
 }  // namespace slt

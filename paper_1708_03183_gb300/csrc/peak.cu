@@ -56,6 +56,14 @@ __device__ __forceinline__ void dmma_loop(int iters, double x, double* out) {
   *out = s;
 }
 
+// DFMA with only `lanes` active lanes per warp (the others return at once)
+__global__ void __launch_bounds__(256) k_fp64_lanes(int iters, int lanes, int flag, double* sink) {
+  if ((int)(threadIdx.x & 31) >= lanes) return;
+  double r;
+  dfma_loop(iters, threadIdx.x, &r);
+  if (flag) sink[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 // mode 0: DFMA, 1: DMMA, 2: even warps DFMA, odd warps DMMA (iters_mma for those)
 __global__ void __launch_bounds__(256) k_fp64_probe(int mode, int iters, int iters_mma, int flag, double* sink) {
   const int warp = threadIdx.x >> 5;
@@ -101,6 +109,49 @@ extern "C" int slt_fp64_peak(void* stream, double out[4]) {
     out[1] = f_mma / (t1 * 1e-3) / 1e12;
     out[2] = (0.5 * f_fma + 0.25 * f_mma) / (t2 * 1e-3) / 1e12;
     out[3] = t0 + t1 + t2;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  } catch (const slt::Error& e) {
+    slt::set_error(e.msg);
+    return e.code;
+  } catch (...) {
+    slt::set_error("unexpected exception");
+    return SLT_ERR_CUDA;
+  }
+  return SLT_OK;
+}
+
+// How the FP64 pipe treats partial warps and few warps (the two facts the executors' design rests
+// on): out[0] = DFMA warp instructions per clock per SM with 32 active lanes, out[1] = the same
+// with 16 active lanes, out[2] = with one 32-lane warp per SM, out[3] = with four warps per SM
+// (clock from cudaDevAttrClockRate, the maximum).  Each timed after a warm-up launch.
+extern "C" int slt_fp64_lane_probe(void* stream, double out[4]) {
+  try {
+    if (!out) slt::fail(SLT_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, nsm = 0, khz = 0;
+    SLT_CUDA(cudaGetDevice(&dev));
+    SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SLT_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    cudaEvent_t e0, e1;
+    SLT_CUDA(cudaEventCreate(&e0));
+    SLT_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](int blocks, int threads, int lanes, int iters) {
+      k_fp64_lanes<<<blocks, threads, 0, s>>>(iters, lanes, 0, nullptr);
+      SLT_CUDA(cudaEventRecord(e0, s));
+      k_fp64_lanes<<<blocks, threads, 0, s>>>(iters, lanes, 0, nullptr);
+      SLT_CUDA(cudaEventRecord(e1, s));
+      SLT_CUDA(cudaEventSynchronize(e1));
+      SLT_CUDA(cudaGetLastError());
+      float ms = 0;
+      SLT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      const double warp_instr = (double)blocks * threads / 32 * iters * kChains;
+      return warp_instr / (ms * 1e-3) / ((double)khz * 1e3) / nsm;
+    };
+    out[0] = timed(nsm * 8, 256, 32, 2048);
+    out[1] = timed(nsm * 8, 256, 16, 2048);
+    out[2] = timed(nsm, 32, 32, 8192);
+    out[3] = timed(nsm, 128, 32, 8192);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   } catch (const slt::Error& e) {

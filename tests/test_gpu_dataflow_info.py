@@ -101,3 +101,23 @@ def test_one_tile_per_subchain_is_a_chain_of_sub_chains(lib):
     info = lib.slt_schedule_dataflow_info(sched)
     assert info["nodes_per_step"] == 2 and info["critical_path_nodes"] == 2
     assert info["critical_path_items"] == pytest.approx(2.0)
+
+
+def test_lane_accounting_is_invariant_under_tiling(lib):
+    # sparse tiling reorders the iterations and splits cells' facet parts among tiles, but the
+    # work of a step stays the same: the FP64 lane instructions needed are equal for every tile
+    # size; the executors issue at least that much (idle lanes), small tiles waste more lanes than
+    # one tile holding the whole mesh, and the staged executor's compacted passes waste fewer
+    # than the item-per-thread warps on small tiles
+    cfg = workload("small_p2")
+    mesh = gpu_mesh(lib, cfg)
+    ch = lib.slt_mesh_chain(mesh)
+    infos = [lib.slt_schedule_lane_info(lib.slt_inspect(ch, tile_size=ts, split=(9,))) for ts in (24, 64, 200, 10 ** 6)]
+    need = infos[0]["needed"]
+    for inf in infos:
+        assert inf["needed"] == pytest.approx(need, rel=1e-12)
+        assert inf["dataflow"] >= need and inf["staged"] >= need and inf["untiled"] >= need
+    for inf in infos[:2]:
+        assert inf["staged"] < inf["dataflow"]
+    assert infos[0]["dataflow_efficiency"] < infos[-1]["dataflow_efficiency"]
+    assert infos[-1]["untiled"] == pytest.approx(infos[0]["untiled"], rel=1e-12)

@@ -1,9 +1,10 @@
 """Parity at the full sizes of the benchmarked workloads, in the launch configurations bench.py
 times: the large P2 mesh (1.0M cells; the whole schedule bit for bit against the oracle inspector,
-two tiled steps against the oracle's chain, and the discrete energy over a 100-step launch), the P4
-mesh, sampled shots of the 64-shot
-batched run, sampled members of the 16-mesh group, and the adjoint workload's gradient against
-central differences of its misfit.  Minutes of oracle time: marked slow."""
+two tiled steps against the oracle's chain, four steps in each launch form against it, and the
+discrete energy over a 100-step launch), the P4 mesh, sampled shots of the 64-shot batched run,
+sampled members of the 16-mesh group and of the whole batched configuration in one launch, and the
+adjoint workload's gradient against central differences of its misfit (one shot untiled; eight
+shots in one call on the tiles).  Minutes of oracle time: marked slow."""
 import numpy as np
 import pytest
 
@@ -68,7 +69,7 @@ def large_oracle4(large):
     return v0, s0, vo, so
 
 
-@pytest.mark.parametrize("form", ["untiled_graph", "tiled_ts256", "cluster_ts2048_c4"])
+@pytest.mark.parametrize("form", ["untiled_graph", "tiled_ts256", "cluster_ts2048_c4", "staged_ts256_bt384"])
 def test_fullsize_four_steps_in_each_timed_launch_form(lib, large, large_oracle4, form):
     # the other launch forms bench.py times at full size: the untiled chain replayed as a CUDA graph
     # (four or more steps), the default dataflow executor, and the cluster executor of its
@@ -80,8 +81,10 @@ def test_fullsize_four_steps_in_each_timed_launch_form(lib, large, large_oracle4
         sc = None
     elif form == "tiled_ts256":
         sc = sched
-    else:
+    elif form == "cluster_ts2048_c4":
         sc = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=2048, split=(9,), executor=2, cluster_size=4)
+    else:
+        sc = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=256, split=(9,), executor=3, block_threads=384)
     v, s = torch.tensor(v0, device="cuda"), torch.tensor(s0, device="cuda")
     lib.slt_execute(mesh, sc, v, s, torch.tensor(cfg["ricker"], device="cuda"), cfg["dt"], 4)
     assert rel_l2(v.cpu().numpy(), vo) < TOL and rel_l2(s.cpu().numpy(), so) < TOL
@@ -222,3 +225,80 @@ def test_fullsize_adjoint_gradient_matches_central_differences(lib):
         fd = (misfit([a + eps * b for a, b in zip(model, d)]) - misfit([a - eps * b for a, b in zip(model, d)])) / (2 * eps)
         ad = sum(g[k] @ d[k] for k in range(3))
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_fullsize_eight_shot_tiled_adjoint(lib):
+    # the bench's adjoint block: 8 top-row shots in one call, 1000 steps, checkpoints every 50, on
+    # the tiles of a ts 64 schedule: the same misfit and gradient as the untiled run, and the
+    # gradient along a seeded direction equal to central differences of the misfit
+    import torch
+    n = 1000
+    cfg = synth.build_config("adjoint", nsteps=n)
+    m = cfg["mesh"]
+    nc = m["cell2vert"].shape[0]
+    shots = np.array([((i + 0.5) * 300.0 / 8, (7 + 0.5) * 150.0 / 8) for i in range(8)])
+    rec = np.stack([(np.arange(50) + 0.5) * 6.0, np.full(50, 149.0)], 1)
+    mesh = lib.slt_mesh_create(m["cell2vert"], m["cellxy"], 2, *synth.layered(m))
+    r = lib.slt_receivers_create(mesh, rec)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    data = torch.zeros((n, 8, 50, 2), dtype=torch.float64, device="cuda")
+    lib.slt_record_batched(mesh, None, r, shots, rk, cfg["dt"], n, data)
+    model = (cfg["rho"], cfg["lam"], cfg["mu"])
+    lib.slt_mesh_set_material(mesh, *model)
+    sched = lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=64, split=(9,))
+    out = []
+    for sc in (sched, None):
+        g = torch.zeros((3, nc), dtype=torch.float64, device="cuda")
+        J = lib.slt_adjoint_batched(mesh, sc, r, shots, rk, cfg["dt"], n, data, 50, g)
+        out.append((J, g.cpu().numpy()))
+    (J, g), (J0, g0) = out
+    assert abs(J - J0) <= 1e-12 * J0 and rel_l2(g, g0) < 1e-10
+    tr = torch.zeros_like(data)
+
+    def misfit(mod):
+        lib.slt_mesh_set_material(mesh, *mod)
+        lib.slt_record_batched(mesh, sched, r, shots, rk, cfg["dt"], n, tr)
+        return 0.5 * cfg["dt"] * float(((tr - data) ** 2).sum())
+
+    assert abs(misfit(model) - J) <= 1e-12 * J
+    rng = np.random.default_rng(37)
+    d = [a * rng.uniform(-1, 1, a.shape) for a in model]
+    eps = 1e-5
+    fd = (misfit([a + eps * b for a, b in zip(model, d)]) - misfit([a - eps * b for a, b in zip(model, d)])) / (2 * eps)
+    ad = sum(g[k] @ d[k] for k in range(3))
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_fullsize_batched_configuration_in_one_launch(lib):
+    # the bench's one-launch block: the 64-shot 708x354 P2 mesh (ts 16) and the 16 uneven meshes
+    # (ts 256) from one queue, 2 steps: sampled members equal their own runs bit for bit
+    import torch
+    bcfg = synth.build_config("large", nx=708, ny=354, nsteps=2)
+    big = gpu_mesh(lib, bcfg)
+    bsched = lib.slt_inspect(lib.slt_mesh_chain(big), tile_size=16, split=(9,))
+    grid = np.array([((i + 0.5) * 300.0 / 8, (j + 0.5) * 150.0 / 8) for j in range(8) for i in range(8)])
+    cfgs = synth.multi_configs(16, nsteps=2)
+    meshes = [gpu_mesh(lib, c) for c in cfgs]
+    scheds = [lib.slt_inspect(lib.slt_mesh_chain(m), tile_size=256, split=(9,)) for m in meshes]
+    nc = bcfg["mesh"]["cell2vert"].shape[0]
+    rng = np.random.default_rng(41)
+    bv0 = 1e-3 * rng.standard_normal((nc, 2, 6, 64))
+    bs0 = 1e-3 * rng.standard_normal((nc, 3, 6, 64))
+    init = []
+    for c in cfgs:
+        n_, Np = c["mesh"]["cell2vert"].shape[0], (c["p"] + 1) * (c["p"] + 2) // 2
+        init.append((1e-3 * rng.standard_normal((n_, 2, Np)), 1e-3 * rng.standard_normal((n_, 3, Np))))
+    grp = lib.slt_group_create_batched([big] + meshes, [bsched] + scheds, [64] + [1] * 16, [grid] + [None] * 16)
+    vs = [torch.tensor(bv0, device="cuda")] + [torch.tensor(a, device="cuda") for a, _ in init]
+    ss = [torch.tensor(bs0, device="cuda")] + [torch.tensor(b, device="cuda") for _, b in init]
+    rs = [torch.tensor(bcfg["ricker"], device="cuda")] + [torch.tensor(c["ricker"], device="cuda") for c in cfgs]
+    dts = [bcfg["dt"]] + [c["dt"] for c in cfgs]
+    lib.slt_group_execute(grp, vs, ss, rs, dts, 2)
+    v2, s2 = torch.tensor(bv0, device="cuda"), torch.tensor(bs0, device="cuda")
+    lib.slt_execute_batched(big, bsched, grid, v2, s2, rs[0], bcfg["dt"], 2)
+    assert torch.equal(vs[0], v2) and torch.equal(ss[0], s2)
+    for k in (0, 5, 11):
+        v1, s1 = torch.tensor(init[k][0], device="cuda"), torch.tensor(init[k][1], device="cuda")
+        lib.slt_execute(meshes[k], scheds[k], v1, s1, rs[k + 1], cfgs[k]["dt"], 2)
+        assert torch.equal(vs[k + 1], v1) and torch.equal(ss[k + 1], s1), k
+
