@@ -86,7 +86,7 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "staged.cuh", "internal.h")
+KERNEL_SOURCES = ("exec.cu", "exec_body.cuh", "dataflow.cuh", "staged.cuh", "passes.cuh", "internal.h")
 
 
 def source_digest(texts):
@@ -558,7 +558,7 @@ def workload_name(args):
             "sparse-tiled ts=%d, fusion {velocity, stress}, %s executor" % (
                 args.config, nx, ny, c["Lx"], c["Ly"], 2 * nx * ny, c["p"], c["material"],
                 c["f0"], args.tile_size,
-                ["dataflow", "colour-phase", "cluster dataflow", "staged dataflow"][getattr(args, "executor", 0)]))
+                ["dataflow", "colour-phase", "cluster dataflow", "staged dataflow", "pass dataflow"][getattr(args, "executor", 0)]))
 
 
 def main():
@@ -571,7 +571,7 @@ def main():
     ap.add_argument("--tile-size", type=int, default=256)
     ap.add_argument("--executor", type=int, default=0,
                     help="0 dataflow (persistent), 1 colour phases, 2 dataflow with one CTA cluster per tile, "
-                         "3 staged dataflow (each tile out of shared memory)")
+                         "3 staged dataflow (each tile out of shared memory), 4 dataflow with compacted passes")
     ap.add_argument("--cluster-size", type=int, default=8, help="CTAs per tile cluster (executor 2)")
     ap.add_argument("--block", type=int, default=256, help="threads per tile CTA (128, 256 or 384)")
     ap.add_argument("--no-untiled", action="store_true")
@@ -676,7 +676,8 @@ def main():
     achieved = flops * args.steps / kern_s / 1e12
     hbm_peak, hbm_kind = peaks()
     probe = slt.slt_fp64_peak()
-    kname = ("k_dataflow<%d,%d>", "k_tiled<%d,%d>", "k_dataflow_cluster<%d,%d>", "k_staged<%d,%d>")[args.executor] % (
+    kname = ("k_dataflow<%d,%d>", "k_tiled<%d,%d>", "k_dataflow_cluster<%d,%d>", "k_staged<%d,%d>",
+             "k_passes<%d,%d>")[args.executor] % (
         p, args.block)
     traffic = ncu_traffic(kname, args.config, args.steps) if args.scale == 1 and args.block == 256 else None
     tiled_bytes = cost["tiled_bytes_per_step"]
@@ -697,7 +698,8 @@ def main():
                                                "how": "slt_schedule_lane_info: FP64 warp-lane instructions "
                                                       "a step needs over those its warps issue"},
                       "executor": ["dataflow", "colour phases", "dataflow, tile clusters of %d CTAs" % args.cluster_size,
-                                   "staged dataflow (tiles out of shared memory)"][args.executor],
+                                   "staged dataflow (tiles out of shared memory)",
+                                   "dataflow with compacted passes"][args.executor],
                       "block_threads": args.block},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP64_PEAK_TFLOPS,

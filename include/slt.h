@@ -100,7 +100,10 @@ typedef struct {
   int32_t executor;      /* elastic chains: 0 = dataflow (default), 1 = colour phases,
                             2 = dataflow with one thread-block cluster of 256-thread CTAs per tile
                             (for large tiles; single-field runs), 3 = staged dataflow (each
-                            tile's sub-chain out of shared memory; single-field runs) */
+                            tile's sub-chain out of shared memory; single-field runs),
+                            4 = dataflow with each segment of a tile run as compacted passes
+                            over the items that have each part (lists of executor 3, values
+                            in global memory; single-field runs) */
   int32_t wait_spins;    /* dataflow: polls of a dependency before giving up (0 = 2^24, ~1 s+) */
   int32_t block_threads; /* threads per tile CTA: 128, 256 or 384, and 512 or 768 for executors
                             0 and 3 (0 = 256) */
@@ -115,6 +118,11 @@ typedef struct {
                                 for the loops before it (Section 5.1.1): MIN projections from
                                 the seed towards the first loop, then MAX projections over the
                                 loops up to the seed and forward tiling after it */
+  int32_t queue_all;         /* dataflow executors (0, 2, 3, 4): 0 = a CTA that finishes a tile runs
+                                the first successor that tile released itself, the others go
+                                to the ready queue (default; the successor overlaps the tile, so
+                                its data is still in L2); 1 = every released tile goes through
+                                the queue, in release order */
 } slt_options;
 
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,

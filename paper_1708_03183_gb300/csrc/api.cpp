@@ -213,16 +213,18 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->renumber == 0 || opt->renumber == 1, "renumber must be 0 or 1");
   REQUIRE(opt->max_rounds >= 0, "max_rounds must be >= 0");
   REQUIRE(opt->nsplit >= 0 && opt->nsplit <= 15, "nsplit must be in 0..15");
-  REQUIRE(opt->executor >= 0 && opt->executor <= 3, "executor must be 0, 1, 2 or 3");
+  REQUIRE(opt->executor >= 0 && opt->executor <= 4, "executor must be 0 to 4");
   REQUIRE(opt->cluster_size >= 0 && opt->cluster_size <= 8, "cluster_size must be in 0..8");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
   REQUIRE(opt->shots_per_cta >= 0, "shots_per_cta must be >= 0");
+  REQUIRE(opt->queue_all == 0 || opt->queue_all == 1, "queue_all must be 0 or 1");
   REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
               opt->block_threads == 384 || opt->block_threads == 512 || opt->block_threads == 768,
           "block_threads must be 0, 128, 256, 384, 512 or 768");
   REQUIRE(opt->block_threads <= 384 || opt->executor == 0 || opt->executor == 3,
           "512- and 768-thread tiles are for the dataflow executors (executors 0 and 3)");
-  REQUIRE(opt->executor != 3 || c->mesh, "the staged executor runs the elastic chain of a mesh");
+  REQUIRE((opt->executor != 3 && opt->executor != 4) || c->mesh,
+          "the staged and pass executors run the elastic chain of a mesh");
   const int nl = (int)c->loops.size();
   int prev = 0;
   for (int k = 0; k < opt->nsplit; ++k) {
@@ -252,6 +254,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   // every temporary is then written out as well
   s->stage_cross = !(opt->nsplit == 0 || (opt->nsplit == 1 && opt->split[0] == 9));
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
+  s->keep = opt->queue_all ? 0 : 1;
   if (opt->block_threads) s->block = opt->block_threads;
   s->shots_per_cta = opt->shots_per_cta;
   if (opt->cluster_size) s->cluster = opt->cluster_size;

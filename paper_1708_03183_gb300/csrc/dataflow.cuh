@@ -38,7 +38,12 @@ struct DFQ {
   int32_t* err;                   // set when a wait gave up
   long long max_spins;
   int32_t g_lo, g_hi;             // nodes of this run: tiles g_lo .. g_hi - 1 (one sub-chain, or all)
+  int32_t keep;                   // 1: a CTA runs one of the nodes its tile released next itself
 };
+
+// Queue slot value of a node that its releasing CTA kept: the slot is filled so that every slot
+// is filled exactly once, and a CTA that takes it takes the next slot.
+constexpr int32_t kSkipSlot = -2;
 // one mesh: sub-chain table by value
 struct DF {
   DFQ q;
@@ -86,40 +91,63 @@ __global__ void k_df_seed(DFQ q, const int32_t* __restrict__ indeg0) {
     }
 }
 
-// Thread 0: claim the next slot and wait (bounded) until a node is published there.  Returns
-// the node, or -1 when the run is over or a wait gave up (the error flag is then set).
+// Thread 0: claim the next slot and wait (bounded) until a node is published there; a slot of a
+// kept node sends it to the next slot.  Returns the node, or -1 when the run is over or a wait
+// gave up (the error flag is then set).
 __device__ __forceinline__ long long df_take(const DFQ& q) {
-  const unsigned long long slot = atomicAdd(q.head, 1ull);
-  if ((long long)slot >= q.total || ld_acquire(q.err)) return -1;
-  long long node;
-  long long spins = 0;
-  while ((node = ld_acquire(&q.queue[slot])) < 0) {
-    if (++spins > q.max_spins || ld_acquire(q.err)) {
-      atomicExch(q.err, 1);
-      return -1;
+  for (;;) {
+    const unsigned long long slot = atomicAdd(q.head, 1ull);
+    if ((long long)slot >= q.total || ld_acquire(q.err)) return -1;
+    long long node;
+    long long spins = 0;
+    while ((node = ld_acquire(&q.queue[slot])) == -1) {
+      if (++spins > q.max_spins || ld_acquire(q.err)) {
+        atomicExch(q.err, 1);
+        return -1;
+      }
+      __nanosleep(64);
     }
-    __nanosleep(64);
+    if (node == kSkipSlot) continue;
+    __threadfence();
+    return node;
   }
-  __threadfence();
-  return node;
 }
 
 // The first warp, after the CTA (or cluster) finished node (st, g) and passed a barrier: release
 // its successors, one lane per successor (about ten per node), so that the decrements travel to L2
 // side by side instead of one after another.  Each lane's fence and acq_rel decrement order the
 // whole tile's writes, which the barrier made visible to it, before the successor can be taken.
-__device__ __forceinline__ void df_publish(const DFQ& q, int g, long long st) {
+// With q.keep, the first released successor is not queued: its slot gets kSkipSlot and the CTA
+// runs it next (returned on every lane; -1 when none).  A released successor overlaps the tile
+// just run, so its cells' data is still in L2 when it starts, where a node queued behind the
+// rest of the ready nodes may find it evicted.  The releasing lane's acquire reaches the CTA's
+// other threads through the barrier before the node's first load, as with df_take.
+__device__ __forceinline__ long long df_publish(const DFQ& q, int g, long long st) {
   __threadfence();
-  for (int i = q.succ_ptr[g] + (int)(threadIdx.x & 31); i < q.succ_ptr[g + 1]; i += 32) {
-    const int e = q.succ[i];
-    const long long s2 = st + (e & 1);
-    if (s2 >= q.nsteps || (e >> 1) < q.g_lo || (e >> 1) >= q.g_hi) continue;
-    const long long n2 = s2 * q.G + (e >> 1);
-    if (atom_add_acq_rel(&q.pending[n2], -1) == 1) {
-      const unsigned long long j = atomicAdd(q.tail, 1ull);
-      st_release(&q.queue[j], (int32_t)n2);
+  const int lane = (int)(threadIdx.x & 31);
+  const int i0 = q.succ_ptr[g], i1 = q.succ_ptr[g + 1];
+  long long kept = -1;
+  for (int base = i0; base < i1; base += 32) {  // the same trip count on every lane
+    const int i = base + lane;
+    long long n2 = -1;
+    if (i < i1) {
+      const int e = q.succ[i];
+      const long long s2 = st + (e & 1);
+      if (s2 < q.nsteps && (e >> 1) >= q.g_lo && (e >> 1) < q.g_hi) {
+        const long long c = s2 * q.G + (e >> 1);
+        if (atom_add_acq_rel(&q.pending[c], -1) == 1) n2 = c;
+      }
     }
+    const unsigned rel = __ballot_sync(0xffffffffu, n2 >= 0);
+    const int keeper = (q.keep && kept < 0 && rel) ? __ffs(rel) - 1 : -1;
+    if (n2 >= 0) {
+      const unsigned long long j = atomicAdd(q.tail, 1ull);
+      st_release(&q.queue[j], lane == keeper ? kSkipSlot : (int32_t)n2);
+    }
+    if (keeper >= 0) kept = __shfl_sync(0xffffffffu, n2, keeper);
   }
+  if (kept >= 0) __threadfence();
+  return kept;
 }
 
 // One tile's slice of the segments of [first, last) at step st, segments separated by CTA
@@ -146,8 +174,9 @@ __device__ __forceinline__ void run_tile(const Params& a, int first, int last, i
 template <int P, int BS, bool BATCH>
 __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Params a, DF df) {
   __shared__ long long s_node;
+  long long kept = -1;  // (thread 0's copy is the one used)
   for (;;) {
-    if (threadIdx.x == 0) s_node = df_take(df.q);
+    if (threadIdx.x == 0) s_node = kept >= 0 ? kept : df_take(df.q);
     __syncthreads();
     const long long node = s_node;
     if (node < 0) return;
@@ -156,7 +185,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow(Param
     int k = 0;
     while (g >= df.cum[k + 1]) ++k;
     run_tile<P, BS, BATCH>(a, df.first[k], df.last[k], g - df.cum[k], st);
-    if (threadIdx.x < 32) df_publish(df.q, g, st);
+    if (threadIdx.x < 32) kept = df_publish(df.q, g, st);
   }
 }
 
@@ -168,8 +197,9 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
   __shared__ long long s_node;
   __shared__ Params sp;
   static_assert(sizeof(Params) % 4 == 0, "Params is copied as 32-bit words");
+  long long kept = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_node = df_take(df.q);
+    if (threadIdx.x == 0) s_node = kept >= 0 ? kept : df_take(df.q);
     __syncthreads();
     const long long node = s_node;
     if (node < 0) return;
@@ -187,7 +217,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_group
     for (int i = threadIdx.x; i < (int)(sizeof(Params) / 4); i += BS) dst[i] = src[i];
     __syncthreads();
     run_tile<P, BS, false>(sp, df.first[k], df.last[k], g - df.cum[k], st);
-    if (threadIdx.x < 32) df_publish(df.q, g, st);
+    if (threadIdx.x < 32) kept = df_publish(df.q, g, st);
   }
 }
 
@@ -200,8 +230,9 @@ __global__ void __launch_bounds__(BS, 2) k_dataflow_mixed(DFM df) {
   __shared__ long long s_node;
   __shared__ Params sp;
   static_assert(sizeof(Params) % 4 == 0, "Params is copied as 32-bit words");
+  long long kept = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_node = df_take(df.q);
+    if (threadIdx.x == 0) s_node = kept >= 0 ? kept : df_take(df.q);
     __syncthreads();
     const long long node = s_node;
     if (node < 0) return;
@@ -227,7 +258,7 @@ __global__ void __launch_bounds__(BS, 2) k_dataflow_mixed(DFM df) {
       case 6: run_tile<3, BS, false>(sp, f, l, t, st); break;
       default: run_tile<3, BS, true>(sp, f, l, t, st); break;
     }
-    if (threadIdx.x < 32) df_publish(df.q, g, st);
+    if (threadIdx.x < 32) kept = df_publish(df.q, g, st);
   }
 }
 
@@ -242,8 +273,9 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_clust
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   const unsigned rank = cl.block_rank(), C = cl.num_blocks();
   const unsigned cid = blockIdx.x / C;
+  long long kept = -1;
   for (;;) {
-    if (rank == 0 && threadIdx.x == 0) slot[cid] = df_take(df.q);
+    if (rank == 0 && threadIdx.x == 0) slot[cid] = kept >= 0 ? kept : df_take(df.q);
     cl.sync();
     const long long node = *(volatile long long*)&slot[cid];
     if (node < 0) return;
@@ -261,7 +293,7 @@ __global__ void __launch_bounds__(BS, tile_min_blocks<P, BS>()) k_dataflow_clust
         run_seg<P, DF_L2_ONLY, false>(a, H, items[i], st);
       cl.sync();
     }
-    if (rank == 0 && threadIdx.x < 32) df_publish(df.q, g, st);
+    if (rank == 0 && threadIdx.x < 32) kept = df_publish(df.q, g, st);
   }
 }
 
@@ -310,6 +342,7 @@ bool prepare_dataflow(::slt_schedule_s* sched, Params& a, int64_t nsteps, cudaSt
   q.tail = D.head.p + 1;
   q.err = D.err.p;
   q.max_spins = sched->wait_spins;
+  q.keep = sched->keep;
   q.g_lo = 0;
   q.g_hi = q.G;
   SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
@@ -374,6 +407,7 @@ bool prepare_dataflow_sub(::slt_schedule_s* sched, Params& a, int k, cudaStream_
   q.tail = D.head.p + 1;
   q.err = D.err.p;
   q.max_spins = sched->wait_spins;
+  q.keep = sched->keep;
   SLT_CUDA(cudaMemsetAsync(D.head.p, 0, 2 * sizeof(unsigned long long), s));
   SLT_CUDA(cudaMemsetAsync(D.err.p, 0, sizeof(int32_t), s));
   rec_begin(2, 2);

@@ -54,6 +54,7 @@ __global__ void k_step_inc(long long* step) { *step += 1; }
 
 #include "dataflow.cuh"
 #include "staged.cuh"
+#include "passes.cuh"
 #include "layout.cuh"
 
 // Tiled chain: one CTA per tile of one colour; the tile runs its slice of every segment of the
@@ -307,6 +308,42 @@ void run_staged(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
   dataflow_check(sched, s);
 }
 
+// executor 4: the dataflow executor running each segment as compacted passes (k_passes)
+template <int P>
+void run_passes(slt_schedule sched, Params a, int64_t nsteps, cudaStream_t s) {
+  DF df;
+  if (!prepare_dataflow(sched, a, nsteps, s, df, [&](int c, int n) { g_rec.begin(c, s, n); },
+                        [&] { g_rec.end(s); }))
+    return;
+  StageArgs g{};
+  for (size_t k = 0; k < sched->subs.size(); ++k) {
+    const SubSched& sub = sched->subs[k];
+    g.fp_ptr[k] = sub.fp_ptr.p;
+    g.fp_cell[k] = sub.fp_cell.p;
+    g.fp_nsl[k] = sub.fp_nsl.p;
+    for (int j = sub.first; j < sub.last; ++j) {
+      g.off[j] = sub.st_off[j - sub.first].p;
+      g.ent[j] = sub.st_ent[j - sub.first].p;
+    }
+  }
+  int dev = 0, nsm = 0, per = 0;
+  SLT_CUDA(cudaGetDevice(&dev));
+  SLT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto launch = [&](auto kernel, int threads) {
+    SLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0));
+    const long long grid = std::min<long long>((long long)nsm * std::max(per, 1), df.q.total);
+    sched->df.last_grid = grid;
+    g_rec.begin(0, s, 1);
+    kernel<<<(unsigned)grid, threads, 0, s>>>(a, df, g);
+    g_rec.end(s);
+  };
+  if (sched->block == 128) launch(k_passes<P, 128>, 128);
+  else if (sched->block == 384) launch(k_passes<P, 384>, 384);
+  else launch(k_passes<P, 256>, 256);
+  SLT_CUDA(cudaGetLastError());
+  dataflow_check(sched, s);
+}
+
 // The untiled step as one CUDA graph (the 6 phase kernels and the step-counter increment), captured
 // on the mesh's private stream and launched nsteps times on s: the host issues one launch per
 // step instead of six.  The step index comes from a device counter the graph advances.
@@ -361,6 +398,10 @@ void run_steps(slt_mesh m, slt_schedule sched, Params a, int64_t nsteps, cudaStr
   }
   if (sched && sched->executor == 3) {
     run_staged<P>(sched, a, nsteps, s);
+    return;
+  }
+  if (sched && sched->executor == 4) {
+    run_passes<P>(sched, a, nsteps, s);
     return;
   }
   if (!sched && nsteps >= kGraphMinSteps) {
@@ -643,6 +684,7 @@ void group_build(slt_group grp) {
         fail(SLT_ERR_UNSUPPORTED, "one launch over all degrees takes degrees 1-3 and 256-thread tiles");
       if (sc->block > 384) fail(SLT_ERR_UNSUPPORTED, "group members take 128-384-thread tiles");
       part.wait_spins = std::max<int64_t>(part.wait_spins, sc->wait_spins);
+      part.keep = std::min(part.keep, sc->keep);
       const DataflowPlan& D = sc->df;
       const int32_t G = D.cum.back();
       for (size_t k = 0; k < sc->subs.size(); ++k) {
@@ -707,6 +749,7 @@ void launch_group_part(slt_group_s::Part& part, int64_t nsteps, cudaStream_t s) 
   q.tail = part.head.p + 1;
   q.err = part.err.p;
   q.max_spins = part.wait_spins;
+  q.keep = part.keep;
   q.g_lo = 0;
   q.g_hi = q.G;
   df.K = part.K;

@@ -754,6 +754,13 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     lap(t0, 2);
     if (c->mesh) build_plan(out, c->mesh, sub, s);
     lap(t0, 3);
+    if (c->mesh && out->executor == 4) {  // its pass lists, which name cells by footprint slot
+      stage_build(out, c->mesh, sub, s);
+      if (sub.max_fp > kNoSlot - 1)
+        fail(SLT_ERR_UNSUPPORTED, "pass executor: a tile touches " + std::to_string(sub.max_fp) +
+                                      " cells, more than the " + std::to_string(kNoSlot - 1) +
+                                      " its pass lists can name; use a smaller tile size");
+    }
     if (c->mesh && out->executor == 3) {
       stage_build(out, c->mesh, sub, s);
       const int32_t cap = stage_capacity(c->mesh->p);

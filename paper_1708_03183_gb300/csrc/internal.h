@@ -203,7 +203,9 @@ struct DataflowPlan {
 }  // namespace slt
 
 struct slt_schedule_s {
-  int32_t executor = 0;              // 0 dataflow, 1 colour phases, 2 dataflow with tile clusters, 3 staged
+  int32_t executor = 0;              // 0 dataflow, 1 colour phases, 2 dataflow with tile clusters, 3 staged,
+                                     // 4 dataflow with compacted passes
+  int32_t keep = 1;                  // dataflow: a CTA runs the first successor its tile released
   int32_t stage_cross = 0;           // staged: temporaries cross sub-chains, so every one is written out
   int32_t block = 256;               // threads per tile CTA (128, 256 or 384)
   int32_t shots_per_cta = 0;         // multi-shot dataflow runs: shots per queue pass (0 = all)
@@ -282,6 +284,7 @@ struct slt_group_s {
   struct Part {
     int p = 0, block = 256;
     int64_t wait_spins = 0;
+    int32_t keep = 1;
     std::vector<int32_t> members;            // indices into meshes
     int32_t G = 0, K = 0;
     slt::DevBuf<int32_t> cum, first, last, mesh_of;   // (mesh, sub-chain) table

@@ -304,8 +304,9 @@ __global__ void __launch_bounds__(BS, 1) k_staged(Params a, DF df, StageArgs g) 
   M.cell = s_cell;
   M.nsl = s_nsl;
   M.cap = cap;
+  long long kept = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_node = df_take(df.q);
+    if (threadIdx.x == 0) s_node = kept >= 0 ? kept : df_take(df.q);
     __syncthreads();
     const long long node = s_node;
     if (node < 0) return;
@@ -357,6 +358,6 @@ __global__ void __launch_bounds__(BS, 1) k_staged(Params a, DF df, StageArgs g) 
       }
     }
     __syncthreads();
-    if (threadIdx.x < 32) df_publish(df.q, gi, st);
+    if (threadIdx.x < 32) kept = df_publish(df.q, gi, st);
   }
 }

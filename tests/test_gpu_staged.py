@@ -1,9 +1,10 @@
-"""The staged executor (executor 3): each tile's sub-chain runs out of shared memory through the
-tile's footprint (its local map of the cell set), with temporaries written to global memory only
-where another tile reads them.  It must give the oracle's fields, and the same bits as the
-dataflow executor on the same schedule (the per-cell arithmetic and its order are shared); its
-footprints must be the cells the tile's iterations touch, recounted from the exported tiling
-functions."""
+"""The executors that run each segment as compacted passes over the staged plan's lists:
+executor 3 (staged: each tile's sub-chain out of shared memory through the tile's footprint, its
+local map of the cell set, temporaries written to global memory only where another tile reads
+them) and executor 4 (the same passes with every value in global memory).  Both must give the
+oracle's fields, and the same bits as the dataflow executor on the same schedule (the per-cell
+arithmetic and its order are shared); the footprints must be the cells the tile's iterations
+touch, recounted from the exported tiling functions."""
 import numpy as np
 import pytest
 
@@ -13,14 +14,14 @@ from tests.helpers import TOL, gpu_mesh, gpu_run, oracle_run, rel_l2, workload
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("block", [256, 512])
+@pytest.mark.parametrize("executor,block", [(3, 256), (3, 512), (4, 256), (4, 384)])
 @pytest.mark.parametrize("name,ts", [("tiny", 64), ("tiny", 7), ("tiny", 10 ** 6), ("small_p2", 64),
                                      ("small_p2", 200), ("small_p3", 48), ("small_p4", 40)])
-def test_staged_matches_oracle_and_dataflow_bitwise(lib, name, ts, block):
+def test_staged_matches_oracle_and_dataflow_bitwise(lib, name, ts, executor, block):
     cfg = workload(name)
     mesh = gpu_mesh(lib, cfg)
     ch = lib.slt_mesh_chain(mesh)
-    staged = lib.slt_inspect(ch, tile_size=ts, split=(9,), executor=3, block_threads=block)
+    staged = lib.slt_inspect(ch, tile_size=ts, split=(9,), executor=executor, block_threads=block)
     v, s = gpu_run(lib, cfg, sched=staged, mesh=mesh)
     vo, so = oracle_run(name)
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL, (rel_l2(v, vo), rel_l2(s, so))
@@ -28,25 +29,27 @@ def test_staged_matches_oracle_and_dataflow_bitwise(lib, name, ts, block):
     assert np.array_equal(v, v0) and np.array_equal(s, s0)
 
 
+@pytest.mark.parametrize("executor", [3, 4])
 @pytest.mark.parametrize("split", [(), (9,), (3, 9, 12), (4,), (2, 7, 13), tuple(range(1, 16))])
-def test_staged_fusion_schemes(lib, split):
+def test_staged_fusion_schemes(lib, split, executor):
     # other fusion schemes send temporaries across sub-chains (then every one is written out);
     # a split inside a phase leaves partial values for the next sub-chain
     cfg = workload("tiny")
     mesh = gpu_mesh(lib, cfg)
     ch = lib.slt_mesh_chain(mesh)
-    v, s = gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=32, split=split, executor=3), mesh=mesh)
+    v, s = gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=32, split=split, executor=executor), mesh=mesh)
     vo, so = oracle_run("tiny")
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL
     v0, s0 = gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=32, split=split), mesh=mesh)
     assert np.array_equal(v, v0) and np.array_equal(s, s0)
 
 
-def test_staged_backward_tiling(lib):
+@pytest.mark.parametrize("executor", [3, 4])
+def test_staged_backward_tiling(lib, executor):
     cfg = workload("small_p2")
     mesh = gpu_mesh(lib, cfg)
     ch = lib.slt_mesh_chain(mesh)
-    sched = lib.slt_inspect(ch, tile_size=48, split=(9,), seed_loop=(4, 5), executor=3)
+    sched = lib.slt_inspect(ch, tile_size=48, split=(9,), seed_loop=(4, 5), executor=executor)
     v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
     vo, so = oracle_run("small_p2")
     assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL
@@ -101,3 +104,29 @@ def test_staged_many_steps_one_launch(lib):
     v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
     v0, s0 = gpu_run(lib, cfg, sched=None, mesh=mesh)
     assert rel_l2(v, v0) < 1e-13 and rel_l2(s, s0) < 1e-13
+
+
+def test_passes_refuses_tiles_beyond_its_slot_range(lib):
+    # the pass lists name a cell by its slot in the tile's footprint (11 bits)
+    import synth
+    c0 = synth.CONFIGS["small_p2"]
+    cfg = synth.build_config("small_p2", nx=2 * c0["nx"], ny=c0["ny"])
+    assert cfg["mesh"]["cell2vert"].shape[0] > 2046
+    mesh = gpu_mesh(lib, cfg)
+    with pytest.raises(lib.SltError) as e:
+        lib.slt_inspect(lib.slt_mesh_chain(mesh), tile_size=10 ** 6, split=(9,), executor=4)
+    assert e.value.code == -6
+
+
+@pytest.mark.parametrize("executor", [0, 3, 4])
+def test_kept_successors_give_the_queued_order_bits(lib, executor):
+    # a CTA running a successor its tile released (instead of queueing it) changes only the order
+    # in which independent tiles run: the same bits, several steps in flight in one launch
+    cfg = workload("small_p2")
+    mesh = gpu_mesh(lib, cfg)
+    ch = lib.slt_mesh_chain(mesh)
+    runs = [gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=40, split=(9,), executor=executor,
+                                                    queue_all=qa), mesh=mesh) for qa in (0, 1)]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    vo, so = oracle_run("small_p2")
+    assert rel_l2(runs[0][0], vo) < TOL and rel_l2(runs[0][1], so) < TOL
