@@ -118,11 +118,13 @@ typedef struct {
                                 for the loops before it (Section 5.1.1): MIN projections from
                                 the seed towards the first loop, then MAX projections over the
                                 loops up to the seed and forward tiling after it */
-  int32_t queue_all;         /* dataflow executors (0, 2, 3, 4): 0 = a CTA that finishes a tile runs
-                                the first successor that tile released itself, the others go
-                                to the ready queue (default; the successor overlaps the tile, so
-                                its data is still in L2); 1 = every released tile goes through
-                                the queue, in release order */
+  int32_t release_order;     /* dataflow executors (0, 2, 3, 4), what a CTA does with the tiles its
+                                finished tile released: 1 = run the first one itself (its cells
+                                are still in L2) and queue the others, 2 = queue them all in
+                                release order, 0 = the executor's default: 1 for the staged
+                                executor (3), whose DRAM traffic it cuts by about a tenth, 2 for
+                                the others, which it slows (1 % at ts 256, 16 % for 4-CTA tile
+                                clusters at ts 2048: a kept tile runs ahead of older ready ones) */
 } slt_options;
 
 /* Default options: ts 1024, greedy colouring, Hilbert renumbering, 16 rounds, seed 0x5EED,
@@ -168,7 +170,7 @@ int slt_schedule_lane_info(slt_schedule sched, double info[4]);
 /* Wall seconds slt_inspect spent per stage, each ended by a stream synchronisation: [0] seed
    partition (Hilbert ranks), [1] colouring, projections, tiling functions and conflict repair
    (Algorithms 1-3, every restart included), [2] iteration lists and local maps, [3] the executor
-   plans, [4] the staged executor's plans, [5] the dataflow dependency graph, [6..7] zero.  Summed
+   plans, [4] the staged and pass executors' plans, [5] the dataflow dependency graph, [6..7] zero.  Summed
    over the sub-chains. */
 int slt_schedule_inspection_times(slt_schedule sched, double seconds[8]);
 /* Copy one integer array of the schedule to host memory.  Call with host_out = NULL to get

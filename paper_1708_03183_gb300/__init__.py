@@ -28,7 +28,7 @@ class slt_options(ctypes.Structure):
                 ("prio_seed", ctypes.c_uint64), ("nsplit", I32), ("split", I32 * 15), ("executor", I32),
                 ("wait_spins", I32), ("block_threads", I32), ("sub_tile_size", I32 * 16),
                 ("cluster_size", I32), ("shots_per_cta", I32), ("seed_loop", I32 * 16),
-                ("queue_all", I32)]
+                ("release_order", I32)]
 
 
 _SIGS = {

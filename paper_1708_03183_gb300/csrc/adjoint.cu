@@ -13,8 +13,10 @@
 //   velocity update (vt, forward sigma = sigma^n):
 //     g_rho += -dt (<vt, A~ sigma> + c <AB vt, A sigma>);  g_lam += -c dt <E(vt), C_lam E(A sigma)>
 // (mu likewise with C_mu).  Forward states are recomputed segment by segment from checkpoints
-// of (v, sigma) taken every k steps; the forward steps use the mesh's executor (tiled when a
-// schedule is given), the adjoint steps the untiled operator loops.
+// of (v, sigma) taken every k steps.  The single-field path below runs the forward steps on the
+// mesh's executor (tiled when a schedule is given) and the adjoint steps through the untiled
+// operator loops; the many-shot path further down runs forward, recompute and adjoint steps
+// alike as the chain's two sub-chains, untiled or on the schedule's tiles.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

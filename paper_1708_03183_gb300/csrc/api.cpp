@@ -217,7 +217,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   REQUIRE(opt->cluster_size >= 0 && opt->cluster_size <= 8, "cluster_size must be in 0..8");
   REQUIRE(opt->wait_spins >= 0, "wait_spins must be >= 0");
   REQUIRE(opt->shots_per_cta >= 0, "shots_per_cta must be >= 0");
-  REQUIRE(opt->queue_all == 0 || opt->queue_all == 1, "queue_all must be 0 or 1");
+  REQUIRE(opt->release_order >= 0 && opt->release_order <= 2, "release_order must be 0, 1 or 2");
   REQUIRE(opt->block_threads == 0 || opt->block_threads == 128 || opt->block_threads == 256 ||
               opt->block_threads == 384 || opt->block_threads == 512 || opt->block_threads == 768,
           "block_threads must be 0, 128, 256, 384, 512 or 768");
@@ -254,7 +254,7 @@ int slt_inspect(slt_chain c, const slt_options* opt, void* stream, slt_schedule*
   // every temporary is then written out as well
   s->stage_cross = !(opt->nsplit == 0 || (opt->nsplit == 1 && opt->split[0] == 9));
   if (opt->wait_spins > 0) s->wait_spins = opt->wait_spins;
-  s->keep = opt->queue_all ? 0 : 1;
+  s->keep = opt->release_order == 1 || (opt->release_order == 0 && opt->executor == 3);
   if (opt->block_threads) s->block = opt->block_threads;
   s->shots_per_cta = opt->shots_per_cta;
   if (opt->cluster_size) s->cluster = opt->cluster_size;

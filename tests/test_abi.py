@@ -49,7 +49,7 @@ def test_chain_validation_on_host(slt):
     assert slt.slt_chain_info(ch) == (2, 1, 1)
     for bad in (dict(tile_size=0), dict(colouring=2), dict(max_rounds=-1), dict(split=(0,)), dict(split=(1,)),
                 dict(sub_tile_size=(4, -1)), dict(seed_loop=(1,)), dict(seed_loop=(-1,)), dict(shots_per_cta=-1), dict(executor=3),
-                dict(executor=4), dict(executor=5), dict(cluster_size=9), dict(queue_all=2),
+                dict(executor=4), dict(executor=5), dict(cluster_size=9), dict(release_order=3), dict(release_order=-1),
                 dict(block_threads=512, executor=4)):
         with pytest.raises(slt.SltError) as e:
             slt.slt_inspect(ch, renumber=0, **bad)

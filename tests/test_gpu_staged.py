@@ -120,13 +120,14 @@ def test_passes_refuses_tiles_beyond_its_slot_range(lib):
 
 @pytest.mark.parametrize("executor", [0, 3, 4])
 def test_kept_successors_give_the_queued_order_bits(lib, executor):
-    # a CTA running a successor its tile released (instead of queueing it) changes only the order
-    # in which independent tiles run: the same bits, several steps in flight in one launch
+    # a CTA running a successor its tile released (release_order 1) instead of queueing it (2)
+    # changes only the order in which independent tiles run: the same bits, several steps in
+    # flight in one launch
     cfg = workload("small_p2")
     mesh = gpu_mesh(lib, cfg)
     ch = lib.slt_mesh_chain(mesh)
     runs = [gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=40, split=(9,), executor=executor,
-                                                    queue_all=qa), mesh=mesh) for qa in (0, 1)]
+                                                    release_order=r), mesh=mesh) for r in (1, 2)]
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
     vo, so = oracle_run("small_p2")
     assert rel_l2(runs[0][0], vo) < TOL and rel_l2(runs[0][1], so) < TOL
