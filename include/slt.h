@@ -192,6 +192,11 @@ int slt_schedule_inspection_times(slt_schedule sched, double seconds[8]);
     12 staged executor: footprint offsets [ntiles + 1] of sub-chain `loop`
     13 staged executor: footprints, per tile the cells (caller numbering) its segments touch, in
        slot order (the tile's local map of the cell set over the whole sub-chain)
+    14 export flags of loop `loop`, one per iteration: 1 when an element the iteration writes or
+       increments is also touched, in some loop of its sub-chain, by a tile other than its own
+       (a value the tile must write back for another tile rather than keep local; Algorithm 1,
+       compute_local_maps).  Computed on the device from the tiling functions and the local
+       maps at the call; synchronises
    The sub-chain is the one containing `loop` (kinds 0, 1: the sub-chain index in `loop`). */
 int slt_schedule_export(slt_schedule sched, int32_t kind, int32_t loop, int32_t desc,
                         int32_t* host_out, int64_t* n);

@@ -213,6 +213,47 @@ def local_maps(chain, sig, m):
     return out
 
 
+def export_flags(chain, sig):
+    """The export flag of every iteration of every loop (the per-tile data of Algorithm 1's
+    compute_local_maps): 1 when an element that the iteration writes or increments (mode 'w' or
+    'i') is also accessed, in some loop of the chain, by a tile other than the iteration's own,
+    i.e. a value its tile must hand to another tile rather than keep local.  sig: one tiling
+    function per loop.  Returns one int32 array per loop."""
+    # every access of the chain as (set, tile, element)
+    acc = {}
+    for j, (s, descs, _) in enumerate(chain.loops):
+        n = chain.set_size[s]
+        for (mid, mode) in descs:
+            if mid < 0:
+                tgt, tiles, elems = s, sig[j].astype(np.int64), np.arange(n, dtype=np.int64)
+            else:
+                frm, tgt, a, vals = chain.maps[mid]
+                tiles, elems = np.repeat(sig[j], a).astype(np.int64), vals.astype(np.int64)
+            acc.setdefault(tgt, []).append((tiles, elems))
+    # distinct tiles per element
+    ntiles = {}
+    for tgt, parts in acc.items():
+        tiles = np.concatenate([p[0] for p in parts])
+        elems = np.concatenate([p[1] for p in parts])
+        span = int(tiles.max()) + 1 if tiles.size else 1
+        pairs = np.unique(elems * span + tiles)          # each (element, tile) once
+        ntiles[tgt] = np.bincount(pairs // span, minlength=chain.set_size[tgt])
+    out = []
+    for j, (s, descs, _) in enumerate(chain.loops):
+        n = chain.set_size[s]
+        f = np.zeros(n, dtype=bool)
+        for (mid, mode) in descs:
+            if mode == "r":
+                continue
+            if mid < 0:
+                f |= ntiles[s] > 1
+            else:
+                frm, tgt, a, vals = chain.maps[mid]
+                f |= (ntiles[tgt][vals] > 1).reshape(n, a).any(axis=1)
+        out.append(f.astype(np.int32))
+    return out
+
+
 def map_invert(values, arity, ntgt):
     lib = _load()
     v = np.ascontiguousarray(values, dtype=np.int32)

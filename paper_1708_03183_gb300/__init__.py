@@ -254,7 +254,7 @@ def slt_schedule_inspection_times(sched):
 
 
 EXPORT_KINDS = {"rank": 0, "colour": 1, "sigma": 2, "list_ptr": 3, "list": 4, "fp_ptr": 5, "fp": 6, "lmap": 7,
-                "succ_ptr": 8, "succ": 9, "indeg0": 10, "indeg": 11, "fp_stage_ptr": 12, "fp_stage": 13}
+                "succ_ptr": 8, "succ": 9, "indeg0": 10, "indeg": 11, "fp_stage_ptr": 12, "fp_stage": 13, "export": 14}
 
 
 def slt_schedule_export(sched, kind, loop, desc=0):

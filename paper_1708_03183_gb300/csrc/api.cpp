@@ -317,7 +317,18 @@ int slt_schedule_lane_info(slt_schedule s, double info[4]) {
 int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc, int32_t* host_out, int64_t* n) {
   API_BEGIN
   REQUIRE(s && n, "null argument");
-  REQUIRE(kind >= 0 && kind <= 13, "unknown kind");
+  REQUIRE(kind >= 0 && kind <= 14, "unknown kind");
+  if (kind == 14) {  // export flags of loop `loop`
+    REQUIRE(loop >= 0 && loop < (int32_t)s->loops.size(), "unknown loop");
+    const int64_t len = s->set_size[s->loops[loop].set];
+    *n = len;
+    if (host_out && len) {
+      DevBuf<int32_t> f;
+      export_flags(s, loop, f, nullptr);
+      SLT_CUDA(cudaMemcpy(host_out, f.p, len * 4, cudaMemcpyDeviceToHost));
+    }
+    return SLT_OK;
+  }
   if (kind == 12 || kind == 13) {  // the staged executor's tile footprints of sub-chain `loop`
     REQUIRE(loop >= 0 && loop < (int32_t)s->subs.size(), "unknown sub-chain");
     const SubSched& S = s->subs[loop];

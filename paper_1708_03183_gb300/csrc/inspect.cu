@@ -1272,6 +1272,141 @@ void stage_build(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t 
   if (hbad) fail(SLT_ERR_UNSUPPORTED, "staged plan: a facet iteration's cell is outside its tile's footprint");
 }
 
+// ------------------------------------------------------------------ export flags (local maps)
+// Per iteration of one loop: 1 when an element the iteration writes or increments is also
+// touched, in some loop of its sub-chain, by a tile other than the iteration's own - the values
+// a tile must export (write back for another tile) rather than keep local.  The (tile, element)
+// pairs of every access of the sub-chain come from the tiling functions (direct accesses) and the
+// local-map footprints (indirect ones); a sort drops repeats, and an element touched by more than
+// one tile is shared.
+
+namespace {
+
+// (tile, element) of every entry of a footprint CSR: the tile by binary search in fp_ptr
+__global__ void k_csr_pairs(const int32_t* __restrict__ fp_ptr, int32_t m, const int32_t* __restrict__ fp,
+                            int64_t n, uint32_t* __restrict__ tile, uint32_t* __restrict__ elem) {
+  GRID_STRIDE(e, n) {
+    int32_t lo = 0, hi = m;  // the last t with fp_ptr[t] <= e
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (fp_ptr[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    tile[e] = (uint32_t)lo;
+    elem[e] = (uint32_t)fp[e];
+  }
+}
+__global__ void k_direct_pairs(const int32_t* __restrict__ sig, int64_t n, uint32_t* __restrict__ tile,
+                               uint32_t* __restrict__ elem) {
+  GRID_STRIDE(e, n) {
+    tile[e] = (uint32_t)sig[e];
+    elem[e] = (uint32_t)e;
+  }
+}
+
+constexpr int kMaxExpDesc = 8;
+struct ExpDescs {
+  int32_t n;
+  int32_t arity[kMaxExpDesc];              // 0: direct access (the iteration's own element)
+  const int32_t* fp_ptr[kMaxExpDesc];
+  const int32_t* fp[kMaxExpDesc];
+  const int32_t* lmap[kMaxExpDesc];
+  const int32_t* cnt[kMaxExpDesc];         // distinct tiles per element of the target set
+};
+__global__ void k_export_flags(ExpDescs d, const int32_t* __restrict__ sig, int64_t n, int32_t* __restrict__ out) {
+  GRID_STRIDE(i, n) {
+    int32_t f = 0;
+    for (int k = 0; k < d.n; ++k) {
+      if (d.arity[k] == 0) {
+        f |= d.cnt[k][i] > 1;
+        continue;
+      }
+      const int32_t base = d.fp_ptr[k][sig[i]];
+      for (int a = 0; a < d.arity[k]; ++a) f |= d.cnt[k][d.fp[k][base + d.lmap[k][i * d.arity[k] + a]]] > 1;
+    }
+    out[i] = f;
+  }
+}
+
+}  // namespace
+
+void export_flags(slt_schedule sched, int32_t J, DevBuf<int32_t>& out, cudaStream_t s) {
+  const SubSched* S = nullptr;
+  for (const SubSched& x : sched->subs)
+    if (J >= x.first && J < x.last) S = &x;
+  if (!S) fail(SLT_ERR_ARG, "loop not inspected");
+  const LoopH& L = sched->loops[J];
+  const int64_t n = sched->set_size[L.set];
+  // distinct tiles per element of a set, over every access of the sub-chain
+  std::vector<std::pair<int32_t, DevBuf<int32_t>>> counts;
+  auto count_for = [&](int32_t T) -> const int32_t* {
+    for (auto& c : counts)
+      if (c.first == T) return c.second.p;
+    int64_t tot = 0;
+    std::vector<std::pair<int, int>> parts;  // (loop, desc) accessing T
+    std::vector<int64_t> len;
+    for (int j = S->first; j < S->last; ++j)
+      for (int d = 0; d < (int)sched->loops[j].descs.size(); ++d) {
+        const DescH& D = sched->loops[j].descs[d];
+        int64_t k = 0;
+        if (D.map < 0 && sched->loops[j].set == T) k = sched->set_size[T];
+        if (D.map >= 0 && sched->maps_meta[D.map].to == T) {
+          int32_t e = 0;
+          SLT_CUDA(cudaMemcpy(&e, S->lmaps[j - S->first][d].fp_ptr.p + S->m, 4, cudaMemcpyDeviceToHost));
+          k = e;
+        }
+        if (k) {
+          parts.push_back({j, d});
+          len.push_back(k);
+          tot += k;
+        }
+      }
+    DevBuf<uint32_t> tile(std::max<int64_t>(tot, 1)), elem(std::max<int64_t>(tot, 1));
+    int64_t o = 0;
+    for (size_t q = 0; q < parts.size(); ++q) {
+      const int j = parts[q].first, d = parts[q].second;
+      if (sched->loops[j].descs[d].map < 0) {
+        k_direct_pairs<<<grid_for(len[q]), 256, 0, s>>>(S->sigma[j - S->first].p, len[q], tile.p + o, elem.p + o);
+      } else {
+        const LocalMap& lm = S->lmaps[j - S->first][d];
+        k_csr_pairs<<<grid_for(len[q]), 256, 0, s>>>(lm.fp_ptr.p, S->m, lm.fp.p, len[q], tile.p + o, elem.p + o);
+      }
+      o += len[q];
+    }
+    SLT_CUDA(cudaGetLastError());
+    const int64_t nu = sort_unique_pairs(tile, bits_for(std::max(S->m - 1, 1)), elem,
+                                         bits_for(std::max<int64_t>(sched->set_size[T] - 1, 1)), tot, s);
+    DevBuf<int32_t> cnt(std::max<int64_t>(sched->set_size[T], 1));
+    SLT_CUDA(cudaMemsetAsync(cnt.p, 0, std::max<int64_t>(sched->set_size[T], 1) * 4, s));
+    if (nu) k_cell_count<<<grid_for(nu), 256, 0, s>>>(elem.p, nu, cnt.p);
+    SLT_CUDA(cudaGetLastError());
+    counts.push_back({T, std::move(cnt)});
+    return counts.back().second.p;
+  };
+  ExpDescs ed{};
+  for (int d = 0; d < (int)L.descs.size(); ++d) {
+    const DescH& D = L.descs[d];
+    if (D.mode == 'r') continue;
+    if (ed.n == kMaxExpDesc) fail(SLT_ERR_UNSUPPORTED, "more than 8 written descriptors in one loop");
+    if (D.map < 0) {
+      ed.arity[ed.n] = 0;
+      ed.cnt[ed.n] = count_for(L.set);
+    } else {
+      const LocalMap& lm = S->lmaps[J - S->first][d];
+      ed.arity[ed.n] = sched->maps_meta[D.map].arity;
+      ed.fp_ptr[ed.n] = lm.fp_ptr.p;
+      ed.fp[ed.n] = lm.fp.p;
+      ed.lmap[ed.n] = lm.lmap.p;
+      ed.cnt[ed.n] = count_for(sched->maps_meta[D.map].to);
+    }
+    ++ed.n;
+  }
+  out.alloc(std::max<int64_t>(n, 1));
+  if (n) k_export_flags<<<grid_for(n), 256, 0, s>>>(ed, S->sigma[J - S->first].p, n, out.p);
+  SLT_CUDA(cudaGetLastError());
+  SLT_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace slt
 
 namespace slt {

@@ -382,6 +382,9 @@ void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
 void stage_build(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 int32_t stage_capacity(int p);  // slots of shared memory the staged executor has per tile CTA
+// export flags of loop J (1 per iteration: an element it writes is touched by another tile of
+// its sub-chain), into out (device); synchronises s
+void export_flags(slt_schedule sched, int32_t J, DevBuf<int32_t>& out, cudaStream_t s);
 // FP64 lane accounting of a schedule's plans (see slt_schedule_lane_info)
 void lane_info(slt_schedule sched, slt_mesh m, double out[4]);
 // inspect.cu

@@ -79,3 +79,5 @@ def compare_schedules(slt, gsched, chain_or, sub_bounds, ts, _offset=(0, 0), **o
                 assert np.array_equal(slt.slt_schedule_export(gsched, "fp_ptr", j, d), fp_ptr)
                 assert np.array_equal(slt.slt_schedule_export(gsched, "fp", j, d), fp)
                 assert np.array_equal(slt.slt_schedule_export(gsched, "lmap", j, d), lmap)
+        for jj, f in enumerate(OI.export_flags(chain_or.sub(lo0, hi0), o["sigma"])):
+            assert np.array_equal(slt.slt_schedule_export(gsched, "export", lo + jj), f), ("export", lo + jj)

@@ -40,6 +40,14 @@ def test_fullsize_schedule_bit_exact(lib, large):
             ptr, its = o["lists"][jj]
             assert np.array_equal(lib.slt_schedule_export(sched, "list_ptr", lo + jj), ptr)
             assert np.array_equal(lib.slt_schedule_export(sched, "list", lo + jj), its)
+        # the local maps of the sub-chain's first facet loop (its increment descriptor), and the
+        # export flags of every loop
+        fp_ptr, fp, lmap = o["local_maps"][1][1]
+        assert np.array_equal(lib.slt_schedule_export(sched, "fp_ptr", lo + 1, 1), fp_ptr)
+        assert np.array_equal(lib.slt_schedule_export(sched, "fp", lo + 1, 1), fp)
+        assert np.array_equal(lib.slt_schedule_export(sched, "lmap", lo + 1, 1), lmap)
+        for jj, f in enumerate(OI.export_flags(ch.sub(lo, hi), o["sigma"])):
+            assert np.array_equal(lib.slt_schedule_export(sched, "export", lo + jj), f), lo + jj
 
 
 def test_fullsize_tiled_steps_match_oracle(lib, large):

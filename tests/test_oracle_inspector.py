@@ -315,3 +315,68 @@ def test_backward_tiled_replay_equals_untiled_chain(seed):
     out = _replay(ch, order)
     for a, b in zip(ref, out):
         assert np.array_equal(a, b)
+
+
+def _export_brute(ch, sig):
+    # the definition, access by access: iteration i of loop j is flagged when some element it
+    # writes or increments is read or written by an iteration of another tile in any loop
+    acc = []   # (set, element, tile) of every access
+    for j, (s, descs, _) in enumerate(ch.loops):
+        for i in range(ch.set_size[s]):
+            for (mid, mode) in descs:
+                if mid < 0:
+                    acc.append((s, i, int(sig[j][i])))
+                else:
+                    frm, to, a, vals = ch.maps[mid]
+                    for k in range(a):
+                        acc.append((to, int(vals[i * a + k]), int(sig[j][i])))
+    out = []
+    for j, (s, descs, _) in enumerate(ch.loops):
+        f = np.zeros(ch.set_size[s], dtype=np.int32)
+        for i in range(ch.set_size[s]):
+            t = int(sig[j][i])
+            written = []
+            for (mid, mode) in descs:
+                if mode == "r":
+                    continue
+                if mid < 0:
+                    written.append((s, i))
+                else:
+                    frm, to, a, vals = ch.maps[mid]
+                    written += [(to, int(vals[i * a + k])) for k in range(a)]
+            f[i] = any((x[0], x[1]) == w and x[2] != t for w in written for x in acc)
+        out.append(f)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_export_flags_match_the_access_by_access_definition(seed):
+    rng = np.random.default_rng(100 + seed)
+    ch = _random_chain(rng, int(rng.integers(2, 5)))
+    ts = int(rng.integers(1, 8))
+    s = I.inspect(ch, ts, prio_seed=seed)
+    for a, b in zip(I.export_flags(ch, s["sigma"]), _export_brute(ch, s["sigma"])):
+        assert np.array_equal(a, b)
+
+
+def test_export_flags_worked_cases():
+    # one tile: nothing is exported
+    ch = _strip_chain()
+    s = I.inspect(ch, 100)
+    assert all(not f.any() for f in I.export_flags(ch, s["sigma"]))
+    # a strip of 8 edges in tiles of 4 edges (edges 0-3 and 4-7, every loop incrementing both end
+    # vertices): only the edges at vertex 4, where the tiles meet, write a vertex the other tile
+    # touches - edge 3 (vertices 3, 4) and edge 4 (vertices 4, 5)
+    ch = _strip_chain(8, 1)
+    sig = [np.array([0, 0, 0, 0, 1, 1, 1, 1], dtype=np.int32)]
+    assert list(I.export_flags(ch, sig)[0]) == [0, 0, 0, 1, 1, 0, 0, 0]
+    # a read-only loop exports nothing; a write through a direct access of a set touched by one
+    # tile per element exports nothing either
+    ch = I.Chain()
+    E, V = ch.set("edges", 4), ch.set("verts", 5)
+    e2v = ch.map(E, V, 2, np.array([(i, i + 1) for i in range(4)]))
+    ch.loop(E, [(-1, "w"), (e2v, "r")])
+    ch.loop(E, [(e2v, "r")])
+    sig = [np.array([0, 0, 1, 1], dtype=np.int32)] * 2
+    f = I.export_flags(ch, sig)
+    assert not f[0].any() and not f[1].any()
