@@ -405,12 +405,24 @@ def batched_timing(slt, synth, args, barrier, keep):
     pick = ("untiled" if not best.tile_size else
             "ts%d, %d shots per CTA" % (best.tile_size, best.shots_per_cta or S))
     keep.update(big_mesh=mesh, big_cfg=cfg, shots=pts, S=S, nc=nc, Np=Np)
+    # the volume contraction of this layout on the FP64 tensor instruction against DFMA, at this
+    # mesh's size (P2) and at the P4 workload's (250k cells), S shots each
+    tensor = {}
+    for deg, ncell in ((2, nc), (4, 250000)):
+        r = slt.slt_fp64_contraction_probe(deg, ncell, S - S % 8 or 8)
+        tensor["p%d" % deg] = {"cells": ncell, "dfma_ms": r["dfma_ms"], "dmma_ms": r["dmma_ms"],
+                               "dmma_over_dfma": r["dmma_ms"] / r["dfma_ms"],
+                               "useful_tflops_dfma": r["useful_flops"] / (r["dfma_ms"] * 1e-3) / 1e12,
+                               "useful_tflops_dmma": r["useful_flops"] / (r["dmma_ms"] * 1e-3) / 1e12,
+                               "dmma_useful_fraction": r["useful_flops"] / r["dmma_issued_flops"],
+                               "rel_diff": r["rel_diff"]}
     return {"workload": "708x354 squares on 300x150 (%d cells), P2 FP64, layered, %d shots on the 8x8 grid, "
                         "%d steps, fields [cell][comp][node][shot] (%.1f GB)" % (nc, S, K, 5 * Np * nc * S * 8 / 1e9),
             "value": units / (ms * 1e-3), "unit": "dof-updates/s", "best": pick, "ms_per_step": ms,
             "fp64_frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "clocks": clk.summary(),
             "autotune": {"seconds": tune_s, "rows": ["ts %d, renumber %d, %d threads, %d shots per CTA: %.2f ms" % tuple(r)
-                                                     for r in table]}}
+                                                     for r in table]},
+            "fp64_tensor_contraction": tensor}
 
 
 def multi_timing(slt, synth, args, barrier, keep):

@@ -427,6 +427,18 @@ int slt_fp64_peak(void* stream, double out[4]);
    out[0] 32 active lanes per warp, out[1] 16 active lanes, out[2] one warp per SM, out[3] four
    warps per SM.  Allocates nothing; synchronises. */
 int slt_fp64_lane_probe(void* stream, double out[4]);
+/* The volume contraction of the multi-shot form on the FP64 tensor instruction (the paper has no
+   counterpart: it measures whether the [dof][shot] layout's small dense products pay on the
+   warp-level FP64 tensor path, mma.sync.m8n8k4, which shares the pipe of DFMA).  For ncell cells
+   of degree `degree` and nshots shots (a multiple of 8), U[cell][Np][shot] = W X[cell] with
+   W = [Dr Ds] (Np x 2Np) and X[cell] a 2Np x nshots block of seeded values, computed twice on
+   `stream`: (a) one thread per (cell, shot) with DFMA, the structural zeros of Dr and Ds skipped
+   (as the executors do), (b) one warp per cell with m8n8k4 tiles (W zero-padded to multiples of
+   8 rows and 4 columns).  out[0], out[1] = ms of (a) and (b) (CUDA events, second of two runs),
+   out[2] = max |Ua - Ub| / max |Ua|, out[3] = useful flops (2 nnz ncell nshots), out[4] = flops
+   the tensor form issues, out[5] = nnz of [Dr Ds].  Allocates (4 Np doubles per cell and shot,
+   at most 32 GB; SLT_ERR_ARG beyond) and synchronises. */
+int slt_fp64_contraction_probe(int32_t degree, int64_t ncell, int32_t nshots, void* stream, double out[6]);
 
 /* ------------------------------------------------------------------ allocation-free ranking
  * The paper has no counterpart to this entry point: it serves callers who cannot allocate

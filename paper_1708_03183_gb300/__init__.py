@@ -69,6 +69,7 @@ _SIGS = {
     "slt_seed_rank_noalloc": (ctypes.c_int, [P, I64, P, P]),
     "slt_fp64_peak": (ctypes.c_int, [P, P]),
     "slt_fp64_lane_probe": (ctypes.c_int, [P, P]),
+    "slt_fp64_contraction_probe": (ctypes.c_int, [I32, I64, I32, P, P]),
     "slt_mesh_set_material": (ctypes.c_int, [P, P, P, P, P]),
     "slt_mesh_set_source": (ctypes.c_int, [P, P, P]),
     "slt_receivers_create": (ctypes.c_int, [P, I32, P, P]),
@@ -308,6 +309,14 @@ def slt_fp64_lane_probe(stream=None):
     _check(lib.slt_fp64_lane_probe(_stream(stream), ctypes.c_void_p(o.ctypes.data)))
     return dict(full_warps=float(o[0]), half_warps=float(o[1]), one_warp_per_sm=float(o[2]),
                 four_warps_per_sm=float(o[3]))
+
+
+def slt_fp64_contraction_probe(degree, ncell, nshots, stream=None):
+    o = np.zeros(6)
+    _check(lib.slt_fp64_contraction_probe(int(degree), int(ncell), int(nshots), _stream(stream),
+                                          ctypes.c_void_p(o.ctypes.data)))
+    return {"dfma_ms": o[0], "dmma_ms": o[1], "rel_diff": o[2], "useful_flops": o[3], "dmma_issued_flops": o[4],
+            "nnz": int(o[5])}
 
 
 def slt_mesh_chain(mesh):

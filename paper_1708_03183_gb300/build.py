@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libslt.so")
 SOURCES = ["api.cpp", "refelem.cpp", "tune.cpp", "sort.cu", "inspect.cu", "exec.cu", "exec_batched.cu",
-           "adjoint.cu", "noalloc.cu", "peak.cu"]
+           "adjoint.cu", "noalloc.cu", "peak.cu", "contract.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -58,6 +58,14 @@ def test_chain_validation_on_host(slt):
         slt.slt_inspect(ch, renumber=1)                       # no points on the seed set
 
 
+def test_probe_validation_on_host(slt):
+    # argument checks come before any device call
+    for bad in ((0, 100, 8), (5, 100, 8), (2, 0, 8), (2, 100, 12), (2, 100, 0), (2, 100, 264), (4, 1 << 24, 256)):
+        with pytest.raises(slt.SltError) as e:
+            slt.slt_fp64_contraction_probe(*bad)
+        assert e.value.code == -1
+
+
 def test_mesh_validation_on_host(slt):
     import synth
     m = synth.make_mesh(3, 3, seed=0)

@@ -135,3 +135,15 @@ def test_shots_per_cta_slices_give_the_same_bits(lib, groups):
     a = _run_batched(lib, cfg, mesh, whole, pts, v0, s0, 4)
     b = _run_batched(lib, cfg, mesh, sliced, pts, v0, s0, 4)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("degree,S", [(1, 8), (2, 64), (3, 16), (4, 64)])
+def test_tensor_core_volume_contraction_matches_dfma(lib, degree, S):
+    # the multi-shot form's volume contraction on mma.sync.m8n8k4 FP64 tiles gives the DFMA
+    # form's values (up to the order of the sums)
+    r = lib.slt_fp64_contraction_probe(degree, 3001, S)
+    np_ = (degree + 1) * (degree + 2) // 2
+    assert r["rel_diff"] < 1e-13, r
+    assert r["dfma_ms"] > 0 and r["dmma_ms"] > 0
+    assert r["useful_flops"] == 2 * r["nnz"] * 3001 * S
+    assert r["dmma_issued_flops"] == 512 * ((np_ + 7) // 8) * ((2 * np_ + 3) // 4) * 3001 * (S // 8)
