@@ -169,7 +169,7 @@ int slt_schedule_dataflow_info(slt_schedule sched, double info[6]);
 int slt_schedule_lane_info(slt_schedule sched, double info[4]);
 /* Wall seconds slt_inspect spent per stage, each ended by a stream synchronisation: [0] seed
    partition (Hilbert ranks), [1] colouring, projections, tiling functions and conflict repair
-   (Algorithms 1-3, every restart included), [2] iteration lists and local maps, [3] the executor
+   (Algorithms 1-3, every restart included), [2] iteration lists, [3] the executor
    plans, [4] the staged and pass executors' plans, [5] the dataflow dependency graph, [6..7] zero.  Summed
    over the sub-chains. */
 int slt_schedule_inspection_times(slt_schedule sched, double seconds[8]);
@@ -180,7 +180,8 @@ int slt_schedule_inspection_times(slt_schedule sched, double seconds[8]);
      2 tiling function sigma_j               (loop = j, chain-global index)
      3 iteration-list offsets [ntiles + 1]   (loop)
      4 iteration lists, ascending per tile   (loop)
-     5 local-map footprint offsets [ntiles+1](loop, desc = indirect descriptor index)
+     5 local-map footprint offsets [ntiles+1](loop, desc = indirect descriptor index; kinds 5-7 and
+       14 build the loop's local maps on the device at their first request, then keep them)
      6 local-map footprints (sorted targets per tile)
      7 local maps: position of map[i*arity+k] in the footprint of tile sigma_j[i]
      8 dataflow graph: successor offsets [G + 1] over the G tiles of all sub-chains (tile t of

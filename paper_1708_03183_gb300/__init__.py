@@ -250,7 +250,7 @@ def slt_schedule_inspection_times(sched):
     """Seconds of slt_inspect per stage."""
     t = np.zeros(8, dtype=np.float64)
     _check(lib.slt_schedule_inspection_times(sched.ptr, ctypes.c_void_p(t.ctypes.data)))
-    return dict(partition=float(t[0]), colour_project_tile=float(t[1]), lists_local_maps=float(t[2]),
+    return dict(partition=float(t[0]), colour_project_tile=float(t[1]), iteration_lists=float(t[2]),
                 executor_plans=float(t[3]), staged_plans=float(t[4]), dataflow_graph=float(t[5]))
 
 

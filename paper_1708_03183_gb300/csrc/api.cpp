@@ -380,6 +380,7 @@ int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc
     default: {
       REQUIRE(desc >= 0 && desc < (int32_t)L->descs.size() && L->descs[desc].map >= 0,
               "desc must name an indirect descriptor");
+      ensure_local_maps(s, const_cast<SubSched&>(*S), jj, nullptr);
       const LocalMap& lm = S->lmaps[jj][desc];
       if (kind == 5) { src = lm.fp_ptr.p; len = S->m + 1; }
       else if (kind == 6) {

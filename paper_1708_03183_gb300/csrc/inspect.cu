@@ -456,12 +456,9 @@ void export_lists(Ctx& X, const int32_t* sig, int64_t n, int32_t m, DevBuf<int32
   SLT_CUDA(cudaStreamSynchronize(s));
 }
 
-void export_local_map(Ctx& X, int mid, const int32_t* sig, int64_t n, int32_t m, LocalMap& L) {
-  cudaStream_t s = X.s;
-  const MapH& M = X.c->maps[mid];
-  const int a = M.arity;
+void build_local_map(const int32_t* dmap, int a, int64_t ntgt, const int32_t* sig, int64_t n, int32_t m,
+                     LocalMap& L, cudaStream_t s) {
   const int64_t ns = n * a;
-  const int64_t ntgt = X.c->set_size[M.to];
   L.fp_ptr.alloc(m + 1);
   L.lmap.alloc(std::max<int64_t>(ns, 1));
   if (ns == 0) {
@@ -473,17 +470,17 @@ void export_local_map(Ctx& X, int mid, const int32_t* sig, int64_t n, int32_t m,
   DevBuf<uint32_t> tile(ns), tgt(ns), order, slots(ns);
   k_iota_u<<<grid_for(ns), 256, 0, s>>>(slots.p, ns);
   k_gather_div<<<grid_for(ns), 256, 0, s>>>(sig, slots.p, ns, a, tile.p);
-  k_copy_i2u<<<grid_for(ns), 256, 0, s>>>(X.dmaps[mid].p, ns, tgt.p);
+  k_copy_i2u<<<grid_for(ns), 256, 0, s>>>(dmap, ns, tgt.p);
   sort_by_two(tile, bits_for(std::max(m - 1, 1)), tgt, bits_for(std::max<int64_t>(ntgt - 1, 1)), ns, order, s);
   DevBuf<int32_t> flag(ns), pos(ns + 1);
-  k_lm_flags<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, X.dmaps[mid].p, ns, flag.p);
+  k_lm_flags<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, dmap, ns, flag.p);
   exclusive_scan_i32(flag.p, pos.p, ns, s);
   int32_t nu = 0;
   SLT_CUDA(cudaMemcpyAsync(&nu, pos.p + ns, 4, cudaMemcpyDeviceToHost, s));
   SLT_CUDA(cudaStreamSynchronize(s));
   L.fp.alloc(std::max(nu, 1));
   DevBuf<uint32_t> utile(std::max(nu, 1));
-  k_lm_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, X.dmaps[mid].p, flag.p, pos.p, ns, L.fp.p, utile.p);
+  k_lm_emit<<<grid_for(ns), 256, 0, s>>>(tile.p, order.p, dmap, flag.p, pos.p, ns, L.fp.p, utile.p);
   lower_bound_offsets(utile.p, nu, m, L.fp_ptr.p, s);
   // lmap[slot] = (inclusive count of uniques up to p) - 1 - fp_ptr[tile]
   DevBuf<int32_t> incl(ns + 1);
@@ -739,7 +736,8 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
       for (int32_t v : hc) nc = std::max(nc, v + 1);
       sub.ncolours = nc;
     }
-    // assign: iteration lists; compute_local_maps
+    // assign: iteration lists (compute_local_maps runs when a local map is first asked for:
+    // no executor reads them, and they cost a sort per indirect descriptor)
     sub.list_ptr.resize(nl);
     sub.list.resize(nl);
     sub.lmaps.resize(nl);
@@ -748,8 +746,6 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
       int64_t n = c->set_size[L.set];
       export_lists(X, sub.sigma[jj].p, n, m, sub.list_ptr[jj], sub.list[jj]);
       sub.lmaps[jj].resize(L.descs.size());
-      for (size_t d = 0; d < L.descs.size(); ++d)
-        if (L.descs[d].map >= 0) export_local_map(X, L.descs[d].map, sub.sigma[jj].p, n, m, sub.lmaps[jj][d]);
     }
     lap(t0, 2);
     if (c->mesh) build_plan(out, c->mesh, sub, s);
@@ -773,6 +769,19 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
   }
   if (c->mesh) build_dataflow(out, c->mesh, s);
   lap(t0, 5);
+  out->dmaps = std::move(X.dmaps);  // the local maps are built from them on request
+}
+
+// compute_local_maps for loop jj of sub-chain S (each indirect descriptor not built yet)
+void ensure_local_maps(slt_schedule sched, SubSched& S, int jj, cudaStream_t s) {
+  const LoopH& L = sched->loops[S.first + jj];
+  const int64_t n = sched->set_size[L.set];
+  for (size_t d = 0; d < L.descs.size(); ++d) {
+    const int mid = L.descs[d].map;
+    if (mid < 0 || S.lmaps[jj][d].fp_ptr.p) continue;
+    const MapH& M = sched->maps_meta[mid];
+    build_local_map(sched->dmaps[mid].p, M.arity, sched->set_size[M.to], S.sigma[jj].p, n, S.m, S.lmaps[jj][d], s);
+  }
 }
 
 // Longest dependency chain per time step of the (step, tile) graph in the steady state: the
@@ -1331,10 +1340,11 @@ __global__ void k_export_flags(ExpDescs d, const int32_t* __restrict__ sig, int6
 }  // namespace
 
 void export_flags(slt_schedule sched, int32_t J, DevBuf<int32_t>& out, cudaStream_t s) {
-  const SubSched* S = nullptr;
-  for (const SubSched& x : sched->subs)
+  SubSched* S = nullptr;
+  for (SubSched& x : sched->subs)
     if (J >= x.first && J < x.last) S = &x;
   if (!S) fail(SLT_ERR_ARG, "loop not inspected");
+  for (int jj = 0; jj < S->last - S->first; ++jj) ensure_local_maps(sched, *S, jj, s);
   const LoopH& L = sched->loops[J];
   const int64_t n = sched->set_size[L.set];
   // distinct tiles per element of a set, over every access of the sub-chain

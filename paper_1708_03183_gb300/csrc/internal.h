@@ -211,6 +211,7 @@ struct slt_schedule_s {
   int32_t shots_per_cta = 0;         // multi-shot dataflow runs: shots per queue pass (0 = all)
   int32_t cluster = 8;               // executor 2: CTAs per tile cluster
   slt::DevBuf<long long> df_slot;    // executor 2: node handed from each cluster's leader
+  std::vector<slt::DevBuf<int32_t>> dmaps;  // device copies of the chain's maps (local maps on request)
   int64_t wait_spins = 1ll << 24;    // bounded dependency wait of the dataflow executor
   slt::DataflowPlan df;
   std::vector<slt::LoopH> loops;     // copy of the chain's loops
@@ -382,6 +383,8 @@ void build_plan(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 void build_dataflow(slt_schedule sched, slt_mesh m, cudaStream_t s);
 void stage_build(slt_schedule sched, slt_mesh m, SubSched& sub, cudaStream_t s);
 int32_t stage_capacity(int p);  // slots of shared memory the staged executor has per tile CTA
+// compute_local_maps of loop jj of sub-chain S, for the descriptors not built yet; synchronises s
+void ensure_local_maps(slt_schedule sched, SubSched& S, int jj, cudaStream_t s);
 // export flags of loop J (1 per iteration: an element it writes is touched by another tile of
 // its sub-chain), into out (device); synchronises s
 void export_flags(slt_schedule sched, int32_t J, DevBuf<int32_t>& out, cudaStream_t s);
