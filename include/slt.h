@@ -137,9 +137,12 @@ int slt_options_default(slt_options* opt);
    segment items) and the dataflow graph.  Errors: SLT_ERR_ARG for a null argument, a chain without
    loops, or invalid options (tile_size < 1, split points not strictly increasing inside
    (0, nloops), seed_loop outside its sub-chain, renumber = 1 without points on a seed set,
-   executor, cluster_size, block_threads or wait_spins out of range); SLT_ERR_UNSUPPORTED for 2^26
-   cells or more on a mesh chain, or a cell touched by more than 16 tiles of one sub-chain
-   (executor plans); SLT_ERR_OOM / SLT_ERR_CUDA from the device.  *out is NULL on error. */
+   executor, cluster_size, block_threads, wait_spins or release_order out of range, executors 3 and
+   4 on a chain not made by slt_mesh_chain); SLT_ERR_UNSUPPORTED for 2^26 cells or more on a mesh
+   chain, a cell touched by more than 16 tiles of one sub-chain (executor plans), or a tile whose
+   footprint exceeds the staged executor's shared memory (executor 3) or the 2046 slots the pass
+   lists can name (executor 4); SLT_ERR_OOM / SLT_ERR_CUDA from the device.  *out is NULL on
+   error. */
 int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
 int slt_schedule_destroy(slt_schedule sched);
 /* Per sub-chain statistics: info[0..7] = ntiles, ncolours, restarts, fell_back_to_sequential,
