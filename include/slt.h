@@ -140,8 +140,8 @@ int slt_options_default(slt_options* opt);
    executor, cluster_size, block_threads, wait_spins or release_order out of range, executors 3 and
    4 on a chain not made by slt_mesh_chain); SLT_ERR_UNSUPPORTED for 2^26 cells or more on a mesh
    chain, a cell touched by more than 16 tiles of one sub-chain (executor plans), or a tile whose
-   footprint exceeds the staged executor's shared memory (executor 3) or the 2046 slots the pass
-   lists can name (executor 4); SLT_ERR_OOM / SLT_ERR_CUDA from the device.  *out is NULL on
+   footprint exceeds the staged executor's shared memory (executor 3) or the 1022 slots the
+   staged and pass lists can name (executors 3 and 4); SLT_ERR_OOM / SLT_ERR_CUDA from the device.  *out is NULL on
    error. */
 int slt_inspect(slt_chain chain, const slt_options* opt, void* stream, slt_schedule* out);
 int slt_schedule_destroy(slt_schedule sched);

@@ -750,13 +750,7 @@ void inspect_chain(slt_chain c, const slt_options& opt, cudaStream_t s, slt_sche
     lap(t0, 2);
     if (c->mesh) build_plan(out, c->mesh, sub, s);
     lap(t0, 3);
-    if (c->mesh && out->executor == 4) {  // its pass lists, which name cells by footprint slot
-      stage_build(out, c->mesh, sub, s);
-      if (sub.max_fp > kNoSlot - 1)
-        fail(SLT_ERR_UNSUPPORTED, "pass executor: a tile touches " + std::to_string(sub.max_fp) +
-                                      " cells, more than the " + std::to_string(kNoSlot - 1) +
-                                      " its pass lists can name; use a smaller tile size");
-    }
+    if (c->mesh && out->executor == 4) stage_build(out, c->mesh, sub, s);  // its pass lists
     if (c->mesh && out->executor == 3) {
       stage_build(out, c->mesh, sub, s);
       const int32_t cap = stage_capacity(c->mesh->p);
@@ -1057,7 +1051,7 @@ __device__ __forceinline__ int32_t fp_find(const int32_t* __restrict__ fp, int32
 __global__ void k_cell_count(const uint32_t* __restrict__ cell, int64_t n, int32_t* __restrict__ cnt) {
   GRID_STRIDE(e, n) atomicAdd(&cnt[cell[e]], 1);
 }
-// footprint entries: work id | shared << 31, neighbour slots (11 bits per face)
+// footprint entries: work id | shared << 31, neighbour slots (kSlotBits per face)
 __global__ void k_fp_info(const uint32_t* __restrict__ tile, const uint32_t* __restrict__ cell, int64_t n,
                           const int32_t* __restrict__ cnt, const int32_t* __restrict__ fp_ptr,
                           const int32_t* __restrict__ nbr, int64_t ncp, int32_t* __restrict__ fp_cell,
@@ -1238,6 +1232,9 @@ void stage_build(slt_schedule sched, slt_mesh mesh, SubSched& sub, cudaStream_t 
     sub.max_fp = 0;
     for (int32_t t = 0; t < m; ++t) sub.max_fp = std::max(sub.max_fp, fp[t + 1] - fp[t]);
   }
+  if (sub.max_fp > kNoSlot - 1)  // the lists name cells by slot, kSlotBits bits each
+    fail(SLT_ERR_UNSUPPORTED, "staged plan: a tile touches " + std::to_string(sub.max_fp) + " cells, more than the " +
+                                  std::to_string(kNoSlot - 1) + " footprint slots its lists can name; use a smaller tile size");
   const int nl = sub.last - sub.first;
   sub.st_off.clear();
   sub.st_ent.clear();

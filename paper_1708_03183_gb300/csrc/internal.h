@@ -177,7 +177,9 @@ struct SubSched {
 };
 // the seven lists of a segment of a tile, in the order the staged executor runs them
 enum StageList : int32_t { SL_GATHER = 0, SL_INIT, SL_INT0, SL_INT1, SL_INT2, SL_EXT, SL_PB, SL_N };
-constexpr int32_t kSlotBits = 11, kNoSlot = (1 << kSlotBits) - 1;  // at most 2047 slots per tile
+// footprint slots: 0 .. kNoSlot - 2 a cell of the tile's footprint, kNoSlot - 1 a neighbour outside
+// it, kNoSlot a free surface; three of them (a cell's face neighbours) share one 32-bit word
+constexpr int32_t kSlotBits = 10, kNoSlot = (1 << kSlotBits) - 1;
 // item flags of the staged lists: faces (3 bits), first cell loop (8), later cell loop (16), and
 // 32 = the accumulated value starts from global memory (contributions made by another tile)
 constexpr int32_t kLoadBit = 32;

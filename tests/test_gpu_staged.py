@@ -107,7 +107,7 @@ def test_staged_many_steps_one_launch(lib):
 
 
 def test_passes_refuses_tiles_beyond_its_slot_range(lib):
-    # the pass lists name a cell by its slot in the tile's footprint (11 bits)
+    # the pass lists name a cell by its slot in the tile's footprint (10 bits)
     import synth
     c0 = synth.CONFIGS["small_p2"]
     cfg = synth.build_config("small_p2", nx=2 * c0["nx"], ny=c0["ny"])
@@ -131,3 +131,21 @@ def test_kept_successors_give_the_queued_order_bits(lib, executor):
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
     vo, so = oracle_run("small_p2")
     assert rel_l2(runs[0][0], vo) < TOL and rel_l2(runs[0][1], so) < TOL
+
+
+@pytest.mark.parametrize("executor", [3, 4])
+def test_footprints_of_many_slots(lib, executor):
+    # P1 tiles whose footprints use slots 512 and above (three neighbour slots share one word per
+    # cell, so the upper slot bits of the third face must survive): the dataflow executor's bits
+    # and the oracle's fields
+    cfg = workload("small_p2", p=1)
+    mesh = gpu_mesh(lib, cfg)
+    ch = lib.slt_mesh_chain(mesh)
+    sched = lib.slt_inspect(ch, tile_size=650, split=(9,), executor=executor, block_threads=384)
+    fp_ptr = lib.slt_schedule_export(sched, "fp_stage_ptr", 0)
+    assert np.diff(fp_ptr).max() > 600
+    v, s = gpu_run(lib, cfg, sched=sched, mesh=mesh)
+    v0, s0 = gpu_run(lib, cfg, sched=lib.slt_inspect(ch, tile_size=650, split=(9,)), mesh=mesh)
+    assert np.array_equal(v, v0) and np.array_equal(s, s0)
+    vo, so = oracle_run("small_p2", p=1)
+    assert rel_l2(v, vo) < TOL and rel_l2(s, so) < TOL
