@@ -573,6 +573,47 @@ def workload_name(args):
                 ["dataflow", "colour-phase", "cluster dataflow", "staged dataflow", "pass dataflow"][getattr(args, "executor", 0)]))
 
 
+def sweep(slt, synth, args):
+    """Time executor configurations on one workload: for each entry of --sweep, a warm-up launch
+    of 3 steps, then the best of two --steps-step launches (kernel time from
+    slt_execute_profiled), with the schedule's dependency-graph figures."""
+    import torch
+    c0 = synth.CONFIGS[args.config]
+    over = {"p": args.degree} if args.degree else {}
+    K = args.steps
+    cfg = synth.build_config(args.config, nsteps=2 * K + 3, nx=c0["nx"] // args.scale, ny=c0["ny"] // args.scale,
+                             **over)
+    m = cfg["mesh"]
+    nc, p = m["cell2vert"].shape[0], cfg["p"]
+    Np = (p + 1) * (p + 2) // 2
+    mesh = slt.slt_mesh_create(m["cell2vert"], m["cellxy"], p, cfg["rho"], cfg["lam"], cfg["mu"], cfg["src"])
+    chain = slt.slt_mesh_chain(mesh)
+    rk = torch.tensor(cfg["ricker"], device="cuda")
+    flops = slt.slt_mesh_cost(mesh)["flops_per_step"]
+    split = tuple(int(x) for x in args.split.split(":") if x)
+    for entry in args.sweep.split(","):
+        out = {"workload": "%s, %d cells, P%d" % (args.config, nc, p), "config": entry}
+        try:
+            sched = None
+            if entry != "untiled":
+                f = [int(x) for x in entry.split(":")] + [0, 0]
+                sched = slt.slt_inspect(chain, tile_size=f[0], split=split, block_threads=f[1], executor=f[2],
+                                        release_order=f[3], cluster_size=f[4])
+            v = torch.zeros((nc, 2, Np), dtype=torch.float64, device="cuda")
+            s = torch.zeros((nc, 3, Np), dtype=torch.float64, device="cuda")
+            slt.slt_execute(mesh, sched, v, s, rk, cfg["dt"], 3)
+            best = min(slt.slt_execute_profiled(mesh, sched, v, s, rk[3 + r * K:], cfg["dt"], K)["chain_ms"] / K
+                       for r in range(2))
+            out.update(ms_per_step=best, fp64_tflops=flops / (best * 1e-3) / 1e12)
+            if sched is not None:
+                d = slt.slt_schedule_dataflow_info(sched)
+                out.update(node_rounds_per_step=d["nodes_per_step"] / max(d["tiles_in_flight"], 1),
+                           critical_path_work_weighted=d["critical_path_items"], tiles_in_flight=d["tiles_in_flight"])
+        except slt.SltError as e:
+            out["error"] = str(e)
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,6 +646,12 @@ def main():
     ap.add_argument("--batched-ts", type=lambda t: [int(x) for x in t.split(",")], default=[16, 32, 64])
     ap.add_argument("--shots-per-cta", type=lambda t: [int(x) for x in t.split(",")], default=[16, 64])
     ap.add_argument("--fp64-peak", action="store_true", help="only measure the FP64 roof (probe + clocks)")
+    ap.add_argument("--sweep", default=None,
+                    help="only time executor configurations on --config (with --degree): comma-separated "
+                         "ts:block:executor[:release_order[:cluster_size]], 'untiled' for the untiled chain; "
+                         "--steps steps each, --split for the fusion scheme; one JSON line per configuration")
+    ap.add_argument("--degree", type=int, default=0, help="--sweep: override the workload's degree")
+    ap.add_argument("--split", default="9", help="--sweep: split points of the fusion scheme, ':'-separated")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -635,6 +682,11 @@ def main():
     if args.fp64_peak:
         if rank == 0:
             print(json.dumps(fp64_peak(slt)))
+        return
+
+    if args.sweep:
+        if rank == 0:
+            sweep(slt, synth, args)
         return
 
     c0 = synth.CONFIGS[args.config]
