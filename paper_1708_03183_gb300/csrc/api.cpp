@@ -357,14 +357,14 @@ int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc
     if (host_out && len) SLT_CUDA(cudaMemcpy(host_out, src, len * 4, cudaMemcpyDeviceToHost));
     return SLT_OK;
   }
-  const SubSched* S = nullptr;
+  SubSched* S = nullptr;
   int jj = 0;
   if (kind <= 1) {
     REQUIRE(loop >= 0 && loop < (int32_t)s->subs.size(), "unknown sub-chain");
     S = &s->subs[loop];
   } else {
     REQUIRE(loop >= 0 && loop < (int32_t)s->loops.size(), "unknown loop");
-    for (const SubSched& x : s->subs)
+    for (SubSched& x : s->subs)
       if (loop >= x.first && loop < x.last) { S = &x; jj = loop - x.first; }
     REQUIRE(S, "loop not inspected");
   }
@@ -380,7 +380,7 @@ int slt_schedule_export(slt_schedule s, int32_t kind, int32_t loop, int32_t desc
     default: {
       REQUIRE(desc >= 0 && desc < (int32_t)L->descs.size() && L->descs[desc].map >= 0,
               "desc must name an indirect descriptor");
-      ensure_local_maps(s, const_cast<SubSched&>(*S), jj, nullptr);
+      ensure_local_maps(s, *S, jj, nullptr);
       const LocalMap& lm = S->lmaps[jj][desc];
       if (kind == 5) { src = lm.fp_ptr.p; len = S->m + 1; }
       else if (kind == 6) {
