@@ -136,11 +136,12 @@ def _midpoints(X, cells, faces):
     return np.ascontiguousarray((a + b) * 0.5)
 
 
-def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=None, max_rounds=16, seed=0):
+def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=None, max_rounds=16, seed=0,
+            with_local_maps=True):
     """Run Algorithm 1 on `chain` with seed loop `seed` (0: forward tiling from the first loop;
     > 0: backward tiling, MIN projections, for the loops before it).  Returns a dict with
-    rank, colour, sigma (list, one tiling function per loop), stats, lists and local maps.
-    xy: points of the seed loop's set (renumber)."""
+    rank, colour, sigma (list, one tiling function per loop), stats, lists and (unless
+    with_local_maps is false) local maps.  xy: points of the seed loop's set (renumber)."""
     lib = _load()
     nsets = len(chain.set_size)
     set_size = np.array(chain.set_size, dtype=np.int64)
@@ -176,7 +177,8 @@ def inspect(chain, ts, sequential=False, prio_seed=0x5EED, renumber=False, xy=No
     out = dict(rank=rank, colour=colour[:m], sigma=sig, ntiles=int(stats[0]), ncolours=int(stats[1]),
                restarts=int(stats[2]), fell_back=bool(stats[3]), conflicts=int(stats[4]), unprojected=int(stats[5]))
     out["lists"] = [iteration_lists(s, m) for s in sig]
-    out["local_maps"] = local_maps(chain, sig, m)
+    if with_local_maps:
+        out["local_maps"] = local_maps(chain, sig, m)
     return out
 
 
